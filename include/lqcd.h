@@ -1,0 +1,216 @@
+/*
+ * lqcd.h -- C ABI of the GB300 Wilson-clover / overlap fermion library.
+ *
+ * The operators are the ones whose GPU kernels the paper ports and measures
+ * (Bi et al., "Lattice QCD package GWU-code and QUDA with HIP", Lattice
+ * 2019): the Wilson and clover Dirac operators (Table 1, QUDA_DIRAC_WILSON
+ * and QUDA_DIRAC_CLOVER), the D-slash kernel with SU(3) links compressed to
+ * 12 reals (Table 2 and its caption), the Krylov inverter built on them, and
+ * the overlap inverter of GWU-code (abstract, Sec. 3, Sec. 4).  The paper
+ * prints no formula; each call states the standard definition it follows.
+ *
+ * Conventions shared by every call
+ *   lattice   dims[4] = (L0, L1, L2, L3) = (x, y, z, t), every Lmu even
+ *             and >= 2; lexicographic site s = x0 + L0 (x1 + L1 (x2 + L2 x3));
+ *             parity (x0 + x1 + x2 + x3) mod 2, even = 0.  Periodic in x, y,
+ *             z; in t periodic or antiperiodic (t_antiperiodic = 1: a hop
+ *             across the t boundary carries a factor -1).
+ *   gamma     DeGrand-Rossi chiral basis, gamma5 = diag(1, 1, -1, -1).
+ *   hopping   (D psi)(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu).
+ *   clover    A(x) = 1 - c_sw kappa sum_{mu<nu} sigma_munu F_munu(x),
+ *             F_munu = [(Q - Q^dag)/(8i)] minus trace/3, Q the four
+ *             plaquette leaves at x, sigma_munu = (i/2)[g_mu, g_nu].
+ *   operator  M = A - kappa D;  Schur complement on odd sites
+ *             Mhat = A_oo - kappa^2 D_oe A_ee^-1 D_eo,  Mhat^dag = g5 Mhat g5.
+ *   canonical FP64 arrays, complex as (re, im) pairs, x fastest:
+ *             links  [t][z][y][x][mu 4][row 3][col 3]       (36 complex/site)
+ *             spinor [rhs][t][z][y][x][spin 4][colour 3]    (12 complex/site)
+ *
+ * Memory and ownership
+ *   Pointers marked "host or device" are device pointers when on_device = 1
+ *   (for example torch.Tensor.data_ptr() of a CUDA tensor) and host pointers
+ *   otherwise; the library copies what it needs during the call, on the
+ *   context's stream, and never keeps or frees a caller's pointer.  The
+ *   library owns everything it allocates; lqcd_destroy releases it.
+ *   Calls on one context are not thread-safe; different contexts are
+ *   independent.  Every call is asynchronous on the context's stream unless
+ *   it returns data to host memory or says otherwise.
+ *
+ * Errors
+ *   Every call returns an lqcd_status; 0 is success.  Arguments are checked
+ *   before any launch.  lqcd_last_error() returns a thread-local message for
+ *   the most recent failure.  The library never calls exit() or abort() and
+ *   never traps the GPU.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQCD_OK = 0,
+  LQCD_ERR_ARG = -1,      /* invalid argument (NULL pointer, bad size, bad enum) */
+  LQCD_ERR_CUDA = -2,     /* a CUDA runtime call or kernel launch failed */
+  LQCD_ERR_OOM = -3,      /* device or pinned host allocation failed */
+  LQCD_ERR_NOCONV = -4,   /* solver stopped without reaching the tolerance */
+  LQCD_ERR_TIMEOUT = -5,  /* a bounded device-side wait ran out */
+  LQCD_ERR_STATE = -6,    /* call needs state not set yet (gauge, kappa) */
+  LQCD_ERR_NOT_SU3 = -7,  /* a loaded link is not unitary with det 1 */
+  LQCD_ERR_SINGULAR = -8  /* a clover block has a zero pivot */
+} lqcd_status;
+
+/* Storage precision of a field.  Arithmetic is FP64 for LQCD_F64 and FP32
+ * for the others; FP16 and BF16 spinors and clover terms carry one FP32
+ * scale per site, links are stored unscaled. */
+typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3 } lqcd_prec;
+
+/* Link storage: all 18 reals, or rows 0 and 1 only (12 reals) with row 2
+ * rebuilt as conj(row0 x row1) in registers (Table 2's caption). */
+typedef enum { LQCD_RECON_18 = 18, LQCD_RECON_12 = 12 } lqcd_recon;
+
+/* Which sites a device-resident field holds. */
+typedef enum { LQCD_EVEN = 0, LQCD_ODD = 1, LQCD_FULL = 2 } lqcd_subset;
+
+typedef enum {
+  LQCD_OP_M = 0,            /* full lattice: out = M in                               */
+  LQCD_OP_MHAT = 1,         /* odd sites:    out_o = Mhat in_o                          */
+  LQCD_OP_MHAT_DAG = 2,     /* odd sites:    out_o = Mhat^dag in_o                      */
+  LQCD_OP_MHAT_NORMAL = 3,  /* odd sites:    out_o = Mhat^dag Mhat in_o                 */
+  LQCD_OP_HOP_EO = 4,       /* even sites:   out_e = D_eo in_o                          */
+  LQCD_OP_HOP_OE = 5,       /* odd sites:    out_o = D_oe in_e                          */
+  LQCD_OP_HW = 6,           /* full lattice: out = g5 [(4 - rho) in - D in / 2]         */
+  LQCD_OP_K2A = 7,          /* even sites:   out_e = A_ee^-1 D_eo in_o (c_sw = 0: D_eo) */
+  LQCD_OP_M_DAG = 8         /* full lattice: out = M^dag in = g5 M g5 in                */
+} lqcd_op;
+
+typedef struct lqcd_ctx lqcd_ctx;     /* one lattice geometry, gauge field and clover term */
+typedef struct lqcd_field lqcd_field; /* a device-resident spinor field (one or more RHS) */
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context for one lattice.  dims: four even extents >= 2.
+ * cuda_stream: a cudaStream_t to run on, or NULL for the legacy default
+ * stream.  Errors: LQCD_ERR_ARG (bad dims, NULL ctx), LQCD_ERR_CUDA. */
+lqcd_status lqcd_create(lqcd_ctx **ctx, const int dims[4], int t_antiperiodic, void *cuda_stream);
+
+/* Release the context and everything the library allocated for it.
+ * Fields created on it must be destroyed first.  NULL is accepted. */
+lqcd_status lqcd_destroy(lqcd_ctx *ctx);
+
+/* Replace the stream the context launches on (NULL: default stream). */
+lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *cuda_stream);
+
+/* Block until all work queued on the context's stream has finished. */
+lqcd_status lqcd_synchronize(lqcd_ctx *ctx);
+
+/* Thread-local message describing the last failure on this thread. */
+const char *lqcd_last_error(void);
+
+/* ---- gauge field and clover term -------------------------------------- */
+
+/* Load the links U_mu(x) (canonical layout, host or device).  The library
+ * keeps an FP64 copy and packs the site-blocked FP64/FP32/FP16/BF16 and
+ * 18/12-real forms on first use.  Every link is checked: unitarity
+ * max|U U^dag - 1| and |det U - 1| must be below 1e-10, else
+ * LQCD_ERR_NOT_SU3 (12-real storage relies on det U = 1).  Loading a new
+ * field drops the clover term.  Blocks until the check has finished. */
+lqcd_status lqcd_load_gauge(lqcd_ctx *ctx, const double *U, int on_device);
+
+/* Set kappa and c_sw and build the clover term A and A^-1 on the GPU in
+ * FP64: clover-leaf field strength, two 6x6 Hermitian blocks per site (the
+ * chiral basis makes sigma_munu block diagonal), inverted by an LDL^dag
+ * factorisation.  c_sw = 0 selects the plain Wilson operator (A = 1, no
+ * clover storage).  Needs a gauge field (else LQCD_ERR_STATE); a zero pivot
+ * gives LQCD_ERR_SINGULAR.  Blocks until the build has finished. */
+lqcd_status lqcd_clover(lqcd_ctx *ctx, double kappa, double c_sw);
+
+/* Set rho of the overlap kernel H_W = g5 D_W(-rho), D_W(m) = 4 + m - D/2. */
+lqcd_status lqcd_set_rho(lqcd_ctx *ctx, double rho);
+
+/* ---- operator application on canonical arrays -------------------------- */
+
+/* out = op(in) for nrhs right-hand sides stored back to back in canonical
+ * order (host or device; both nrhs * V * 24 doubles).  The arithmetic runs
+ * in `prec` with links in `recon` form: the input is converted to that
+ * precision on the GPU, the result converted back to FP64.  Sites outside
+ * the op's output subset are set to zero.  Needs the gauge field, and
+ * kappa for every op but HOP_EO/HOP_OE/HW (rho for HW).  Host buffers are
+ * read and written inside the call, which then blocks. */
+lqcd_status lqcd_dslash(lqcd_ctx *ctx, double *out, const double *in, int nrhs, lqcd_op op, lqcd_prec prec,
+                        lqcd_recon recon, int on_device);
+
+/* ---- device-resident fields -------------------------------------------- */
+
+/* Allocate a spinor field of nrhs right-hand sides on `subset` in storage
+ * precision `prec`.  Contents are undefined until imported or written. */
+lqcd_status lqcd_field_create(lqcd_ctx *ctx, lqcd_prec prec, lqcd_subset subset, int nrhs, lqcd_field **field);
+lqcd_status lqcd_field_destroy(lqcd_field *field);
+
+/* Convert canonical FP64 spinors (nrhs back to back, host or device) into
+ * the field, taking the sites of the field's subset.  Export converts back
+ * and writes only the sites of the field's subset. */
+lqcd_status lqcd_field_import(lqcd_ctx *ctx, lqcd_field *field, const double *canon, int on_device);
+lqcd_status lqcd_field_export(lqcd_ctx *ctx, const lqcd_field *field, double *canon, int on_device);
+
+/* out = op(in) on device-resident fields of one precision (the arithmetic
+ * precision follows the fields).  Subsets must match the op: EVEN/ODD
+ * parities for the Schur and hopping ops, FULL for M, M_DAG and HW.  The
+ * intermediate of MHAT-type ops lives in context-owned scratch.  Nothing is
+ * copied to or from the host and nothing synchronises. */
+lqcd_status lqcd_apply(lqcd_ctx *ctx, lqcd_op op, lqcd_recon recon, lqcd_field *out, const lqcd_field *in);
+
+/* The second half of Mhat on its own: out_o = A_oo x_o - kappa^2 D_oe y_e
+ * (dagger = 1: A_oo x_o - kappa^2 g5 D_oe y_e, the form used inside
+ * Mhat^dag = g5 Mhat g5 once y_e was built from g5 x_o).  Together with
+ * LQCD_OP_K2A this is one Mhat application split into its two kernels. */
+lqcd_status lqcd_apply_schur(lqcd_ctx *ctx, lqcd_recon recon, int dagger, lqcd_field *out, const lqcd_field *x_odd,
+                             const lqcd_field *y_even);
+
+/* Sum over all sites and right-hand sides of |component|^2, reduced in FP64
+ * in a fixed order (bitwise reproducible).  Blocks; result in host memory. */
+lqcd_status lqcd_field_norm2(lqcd_ctx *ctx, const lqcd_field *field, double *result);
+
+/* ---- solvers ----------------------------------------------------------- */
+
+typedef struct {
+  double tol;          /* target ||b - M x|| / ||b|| on the full lattice, > 0     */
+  int max_iter;        /* cap on CG iterations (inner iterations when mixed)       */
+  lqcd_prec inner;     /* LQCD_F64: plain FP64 CG; else mixed with this storage    */
+  double delta;        /* reliable-update trigger: inner ||r|| < delta * ||r_0||   */
+  int nrhs;            /* right-hand sides stored back to back in x and b          */
+  int use_x0;          /* 1: x holds an initial guess on entry                     */
+  lqcd_recon recon;    /* link storage of the FP64 operator                        */
+  lqcd_recon inner_recon; /* link storage of the inner low-precision operator      */
+  int check_every;     /* iterations between host convergence checks (0: 8)        */
+} lqcd_solve_params;
+
+typedef struct {
+  int iters;              /* CG iterations done (the largest over right-hand sides) */
+  int reliable_updates;   /* FP64 residual recomputations (mixed solver)            */
+  int nrhs;
+  double true_resid[64];  /* ||b - M x|| / ||b|| per RHS, recomputed in FP64 on GPU */
+  double seconds;         /* wall time of the solve                                 */
+  double mhat_applies;    /* Mhat (or Mhat^dag) applications, all precisions        */
+} lqcd_solve_info;
+
+/* Solve M x = b (canonical arrays, nrhs right-hand sides, host or device)
+ * by even-odd preconditioning: bhat_o = b_o + kappa D_oe A_ee^-1 b_e,
+ * CG on the normal equations of Mhat x_o = bhat_o (CGLS form, one
+ * independent recursion per right-hand side), then
+ * x_e = A_ee^-1 (b_e + kappa D_eo x_o).  With params->inner != LQCD_F64 the
+ * CG runs with low-precision storage and FP32 arithmetic, and the solution
+ * is accumulated, and the residual recomputed, in FP64 whenever the inner
+ * residual fell by `delta` (reliable updates).  Returns LQCD_OK only after
+ * the FP64 full-lattice residual of every RHS is <= tol; LQCD_ERR_NOCONV
+ * with info filled and x the last iterate otherwise.  Blocks. */
+lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device, const lqcd_solve_params *params,
+                       lqcd_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,0 +1,272 @@
+"""Python binding of the GB300 Wilson-clover / overlap library (liblqcd.so).
+
+Argument marshalling only: every operation runs in the CUDA kernels behind
+the C ABI declared in ``include/lqcd.h``; this module converts numpy arrays
+(host memory) and torch CUDA tensors (device memory) to plain pointers and
+raises ``LqcdError`` for a non-zero status.  Importing it without the built
+library raises ImportError: there is no CPU fallback.
+
+Functions keep the C names (``lqcd_create``, ``lqcd_load_gauge``,
+``lqcd_clover``, ``lqcd_dslash``, ``lqcd_solve``, ...).  ``Lattice`` bundles a
+context with those calls for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(
+        f"{_build.LIB} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()' or python -m paper_2001_05706_gb300.build)")
+_lib = ctypes.CDLL(_build.LIB)
+
+# enums (include/lqcd.h)
+LQCD_OK = 0
+LQCD_ERR_ARG, LQCD_ERR_CUDA, LQCD_ERR_OOM, LQCD_ERR_NOCONV = -1, -2, -3, -4
+LQCD_ERR_TIMEOUT, LQCD_ERR_STATE, LQCD_ERR_NOT_SU3, LQCD_ERR_SINGULAR = -5, -6, -7, -8
+LQCD_F64, LQCD_F32, LQCD_F16, LQCD_BF16 = 0, 1, 2, 3
+LQCD_RECON_18, LQCD_RECON_12 = 18, 12
+LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
+(LQCD_OP_M, LQCD_OP_MHAT, LQCD_OP_MHAT_DAG, LQCD_OP_MHAT_NORMAL, LQCD_OP_HOP_EO, LQCD_OP_HOP_OE, LQCD_OP_HW,
+ LQCD_OP_K2A, LQCD_OP_M_DAG) = range(9)
+
+PREC = {"f64": LQCD_F64, "f32": LQCD_F32, "f16": LQCD_F16, "bf16": LQCD_BF16}
+OPS = {"M": LQCD_OP_M, "MHAT": LQCD_OP_MHAT, "MHAT_DAG": LQCD_OP_MHAT_DAG, "MHAT_NORMAL": LQCD_OP_MHAT_NORMAL,
+       "HOP_EO": LQCD_OP_HOP_EO, "HOP_OE": LQCD_OP_HOP_OE, "HW": LQCD_OP_HW, "K2A": LQCD_OP_K2A,
+       "M_DAG": LQCD_OP_M_DAG}
+
+
+class lqcd_solve_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
+                ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("use_x0", ctypes.c_int),
+                ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class lqcd_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("true_resid", ctypes.c_double * 64), ("seconds", ctypes.c_double),
+                ("mhat_applies", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_ip = ctypes.c_int
+_sig = {
+    "lqcd_create": [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), _ip, _vp],
+    "lqcd_destroy": [_vp],
+    "lqcd_set_stream": [_vp, _vp],
+    "lqcd_synchronize": [_vp],
+    "lqcd_load_gauge": [_vp, _vp, _ip],
+    "lqcd_clover": [_vp, ctypes.c_double, ctypes.c_double],
+    "lqcd_set_rho": [_vp, ctypes.c_double],
+    "lqcd_dslash": [_vp, _vp, _vp, _ip, _ip, _ip, _ip, _ip],
+    "lqcd_field_create": [_vp, _ip, _ip, _ip, ctypes.POINTER(_vp)],
+    "lqcd_field_destroy": [_vp],
+    "lqcd_field_import": [_vp, _vp, _vp, _ip],
+    "lqcd_field_export": [_vp, _vp, _vp, _ip],
+    "lqcd_apply": [_vp, _ip, _ip, _vp, _vp],
+    "lqcd_apply_schur": [_vp, _ip, _ip, _vp, _vp, _vp],
+    "lqcd_field_norm2": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
+    "lqcd_solve": [_vp, _vp, _vp, _ip, ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.lqcd_last_error.argtypes = []
+_lib.lqcd_last_error.restype = ctypes.c_char_p
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def lqcd_last_error() -> str:
+    return _lib.lqcd_last_error().decode()
+
+
+def _check(status):
+    if status != LQCD_OK:
+        raise LqcdError(status, lqcd_last_error())
+    return status
+
+
+def _buf(a):
+    """(pointer, on_device) of a numpy array or a torch tensor (C-contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return _vp(a.ctypes.data), 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return _vp(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+# ---- the C calls, same names ------------------------------------------------
+
+def lqcd_create(dims, t_antiperiodic=1, stream=None):
+    ctx = _vp()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    _check(_lib.lqcd_create(ctypes.byref(ctx), d, int(t_antiperiodic), _stream_ptr(stream)))
+    return ctx
+
+
+def lqcd_destroy(ctx):
+    _check(_lib.lqcd_destroy(ctx))
+
+
+def lqcd_set_stream(ctx, stream):
+    _check(_lib.lqcd_set_stream(ctx, _stream_ptr(stream)))
+
+
+def lqcd_synchronize(ctx):
+    _check(_lib.lqcd_synchronize(ctx))
+
+
+def lqcd_load_gauge(ctx, U):
+    p, dev = _buf(U)
+    _check(_lib.lqcd_load_gauge(ctx, p, dev))
+
+
+def lqcd_clover(ctx, kappa, c_sw):
+    _check(_lib.lqcd_clover(ctx, float(kappa), float(c_sw)))
+
+
+def lqcd_set_rho(ctx, rho):
+    _check(_lib.lqcd_set_rho(ctx, float(rho)))
+
+
+def lqcd_dslash(ctx, out, inp, nrhs, op, prec, recon=LQCD_RECON_18):
+    po, do = _buf(out)
+    pi, di = _buf(inp)
+    if do != di:
+        raise ValueError("out and in must both be host or both be device buffers")
+    _check(_lib.lqcd_dslash(ctx, po, pi, int(nrhs), int(op), int(prec), int(recon), do))
+
+
+def lqcd_field_create(ctx, prec, subset, nrhs=1):
+    f = _vp()
+    _check(_lib.lqcd_field_create(ctx, int(prec), int(subset), int(nrhs), ctypes.byref(f)))
+    return f
+
+
+def lqcd_field_destroy(field):
+    _check(_lib.lqcd_field_destroy(field))
+
+
+def lqcd_field_import(ctx, field, canon):
+    p, dev = _buf(canon)
+    _check(_lib.lqcd_field_import(ctx, field, p, dev))
+
+
+def lqcd_field_export(ctx, field, canon):
+    p, dev = _buf(canon)
+    _check(_lib.lqcd_field_export(ctx, field, p, dev))
+
+
+def lqcd_apply(ctx, op, recon, out, inp):
+    _check(_lib.lqcd_apply(ctx, int(op), int(recon), out, inp))
+
+
+def lqcd_apply_schur(ctx, recon, dagger, out, x_odd, y_even):
+    _check(_lib.lqcd_apply_schur(ctx, int(recon), int(dagger), out, x_odd, y_even))
+
+
+def lqcd_field_norm2(ctx, field):
+    r = ctypes.c_double(0)
+    _check(_lib.lqcd_field_norm2(ctx, field, ctypes.byref(r)))
+    return r.value
+
+
+def lqcd_solve(ctx, x, b, params: lqcd_solve_params, raise_on_noconv=True):
+    """Returns (status, info).  x holds the solution on return."""
+    px, dx = _buf(x)
+    pb, db = _buf(b)
+    if dx != db:
+        raise ValueError("x and b must both be host or both be device buffers")
+    info = lqcd_solve_info()
+    st = _lib.lqcd_solve(ctx, px, pb, dx, ctypes.byref(params), ctypes.byref(info))
+    if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
+        raise LqcdError(st, lqcd_last_error())
+    return st, info
+
+
+def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,
+                 inner_recon=LQCD_RECON_12, check_every=8):
+    return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every)
+
+
+# ---- convenience ------------------------------------------------------------
+
+class Lattice:
+    """One context: geometry, gauge field, clover term (thin wrapper)."""
+
+    def __init__(self, dims, t_antiperiodic=1, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.ctx = lqcd_create(self.dims, t_antiperiodic, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            lqcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_gauge(self, U):
+        lqcd_load_gauge(self.ctx, U)
+
+    def clover(self, kappa, c_sw):
+        lqcd_clover(self.ctx, kappa, c_sw)
+
+    def set_rho(self, rho):
+        lqcd_set_rho(self.ctx, rho)
+
+    def dslash(self, psi, op="MHAT", prec="f64", recon=18):
+        """op(psi) on canonical complex128 arrays (numpy: host path; torch: device path)."""
+        nrhs = psi.size // (12 * self.V) if isinstance(psi, np.ndarray) else psi.numel() // (24 * self.V)
+        if isinstance(psi, np.ndarray):
+            psi = np.ascontiguousarray(psi, dtype=np.complex128)
+            out = np.empty_like(psi)
+        else:
+            out = psi.new_empty(psi.shape)
+        lqcd_dslash(self.ctx, out, psi, nrhs, OPS[op] if isinstance(op, str) else op,
+                    PREC[prec] if isinstance(prec, str) else prec, recon)
+        return out
+
+    def solve(self, b, tol=1e-10, inner="f64", nrhs=None, **kw):
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        if nrhs is None:
+            nrhs = b.size // (12 * self.V)
+        x = np.zeros_like(b)
+        prm = solve_params(tol=tol, inner=PREC[inner] if isinstance(inner, str) else inner, nrhs=nrhs, **kw)
+        st, info = lqcd_solve(self.ctx, x, b, prm, raise_on_noconv=False)
+        return x, st, info

@@ -1,0 +1,208 @@
+// Fused BLAS-1 kernels of the CG solvers with deterministic FP64 norms.
+//
+// The paper's QUDA port passes the multi-blas coefficients and kernel
+// arguments through device memory (Sec. 2, items 3.4 and 3.5) and notes
+// that Thrust reductions in double can be slow (Sec. 3); here the scalar
+// state of every right-hand side (gamma, ||q||^2, ...) lives in device
+// memory (SolverScalars) and each kernel derives its coefficient from it, so
+// a CG iteration needs no host round trip, and every norm is a fixed-order
+// tree reduction fused into the kernel that produces the vector.
+#include "internal.h"
+
+namespace lqcd {
+
+constexpr int kBlasThreads = 256;
+
+// CG step: alpha = gamma[cur] / qq;  x += alpha p;  r -= alpha q;  rr = ||r||^2
+template <typename SX, typename SV>
+__global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x, FieldRef p, MutField r,
+                                                             FieldRef q, SolverScalars *sc, int cur, double *partials,
+                                                             unsigned *counter, int nrhs) {
+  using TV = typename Math<SV>::T;
+  using TX = typename Math<SX>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  double nrm[1] = {0.0};
+  const SolverScalars s = sc[k];
+  const bool on = s.active != 0.0 && s.qq > 0.0;
+  const double alpha = on ? s.gamma[cur] / s.qq : 0.0;
+  if (h < Vh && on) {
+    cx<TV> pv[4][3], qv[4][3], rv[4][3];
+    cx<TX> xv[4][3];
+    load_spinor<SV>(p, Vh, k, h, pv);
+    load_spinor<SV>(q, Vh, k, h, qv);
+    load_spinor<SV>(r.ref(), Vh, k, h, rv);
+    load_spinor<SX>(x.ref(), Vh, k, h, xv);
+    const TV a = (TV)alpha;
+    const TX ax = (TX)alpha;
+    double n2 = 0.0;
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        xv[sp][c] = mk<TX>(xv[sp][c].r + ax * (TX)pv[sp][c].r, xv[sp][c].i + ax * (TX)pv[sp][c].i);
+        rv[sp][c] = mk<TV>(rv[sp][c].r - a * qv[sp][c].r, rv[sp][c].i - a * qv[sp][c].i);
+        n2 += (double)rv[sp][c].r * rv[sp][c].r + (double)rv[sp][c].i * rv[sp][c].i;
+      }
+    store_spinor<SX>(x.data, x.scale, x.rhs_words, Vh, k, h, xv);
+    store_spinor<SV>(r.data, r.scale, r.rhs_words, Vh, k, h, rv);
+    nrm[0] = n2;
+  }
+  // an inactive right-hand side reduces zeros: its rr reads 0 from then on
+  grid_reduce<1>(nrm, partials, counter, &sc[0].rr, k, nrhs, (int)(sizeof(SolverScalars) / 8));
+}
+
+// p = s + beta p with beta = gamma[1-cur] / gamma[cur]
+template <typename SV>
+__global__ void __launch_bounds__(kBlasThreads) cg_p_kernel(long Vh, MutField p, FieldRef sv, SolverScalars *sc,
+                                                            int cur) {
+  using TV = typename Math<SV>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  const SolverScalars s = sc[k];
+  if (h >= Vh || s.active == 0.0) return;
+  const TV beta = s.gamma[cur] > 0.0 ? (TV)(s.gamma[1 - cur] / s.gamma[cur]) : (TV)0;
+  cx<TV> pv[4][3], ss[4][3];
+  load_spinor<SV>(p.ref(), Vh, k, h, pv);
+  load_spinor<SV>(sv, Vh, k, h, ss);
+#pragma unroll
+  for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) pv[sp][c] = mk<TV>(ss[sp][c].r + beta * pv[sp][c].r, ss[sp][c].i + beta * pv[sp][c].i);
+  store_spinor<SV>(p.data, p.scale, p.rhs_words, Vh, k, h, pv);
+}
+
+// ||v||^2 per right-hand side into result[k * stride]
+template <typename S>
+__global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v, double *partials, unsigned *counter,
+                                                             double *result, int stride, int nrhs) {
+  using T = typename Math<S>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  double nrm[1] = {0.0};
+  if (h < Vh) {
+    cx<T> a[4][3];
+    load_spinor<S>(v, Vh, k, h, a);
+    double n2 = 0.0;
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) n2 += (double)a[sp][c].r * a[sp][c].r + (double)a[sp][c].i * a[sp][c].i;
+    nrm[0] = n2;
+  }
+  grid_reduce<1>(nrm, partials, counter, result, k, nrhs, stride);
+}
+
+// y += f_k x  (per right-hand side factor f[k], in FP64; y may be FP64 and x lower)
+template <typename SY, typename SX>
+__global__ void __launch_bounds__(kBlasThreads) axpy_kernel(long Vh, MutField y, FieldRef x, const double *f) {
+  using TY = typename Math<SY>::T;
+  using TX = typename Math<SX>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (h >= Vh) return;
+  const double a = f[k];
+  if (a == 0.0) return;
+  cx<TY> yv[4][3];
+  cx<TX> xv[4][3];
+  load_spinor<SY>(y.ref(), Vh, k, h, yv);
+  load_spinor<SX>(x, Vh, k, h, xv);
+#pragma unroll
+  for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      yv[sp][c] = mk<TY>((TY)((double)yv[sp][c].r + a * (double)xv[sp][c].r),
+                         (TY)((double)yv[sp][c].i + a * (double)xv[sp][c].i));
+  store_spinor<SY>(y.data, y.scale, y.rhs_words, Vh, k, h, yv);
+}
+
+// y = f_k x with per-RHS factors (precision conversion included)
+template <typename SY, typename SX>
+__global__ void __launch_bounds__(kBlasThreads) scale_kernel(long Vh, MutField y, FieldRef x, const double *f) {
+  using TY = typename Math<SY>::T;
+  using TX = typename Math<SX>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (h >= Vh) return;
+  const double a = f[k];
+  cx<TX> xv[4][3];
+  cx<TY> yv[4][3];
+  load_spinor<SX>(x, Vh, k, h, xv);
+#pragma unroll
+  for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) yv[sp][c] = mk<TY>((TY)(a * (double)xv[sp][c].r), (TY)(a * (double)xv[sp][c].i));
+  store_spinor<SY>(y.data, y.scale, y.rhs_words, Vh, k, h, yv);
+}
+
+static dim3 bgrid(long Vh, int nrhs) { return dim3((unsigned)((Vh + kBlasThreads - 1) / kBlasThreads), (unsigned)nrhs); }
+
+long blas_blocks(long Vh) { return (Vh + kBlasThreads - 1) / kBlasThreads; }
+
+#define LQ_DISPATCH_V(prec, CALL)                                  \
+  switch (prec) {                                                  \
+    case LQCD_F64: { using SV = double; CALL; } break;             \
+    case LQCD_F32: { using SV = float; CALL; } break;              \
+    case LQCD_F16: { using SV = __half; CALL; } break;             \
+    case LQCD_BF16: { using SV = __nv_bfloat16; CALL; } break;     \
+  }
+
+cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, MutField r, FieldRef q,
+                       SolverScalars *sc, int cur, double *partials, unsigned *counter, cudaStream_t st) {
+  dim3 g = bgrid(Vh, nrhs);
+  if (px == LQCD_F64 && pv == LQCD_F64) {
+    cg_xr_kernel<double, double><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs);
+  } else if (px == LQCD_F32) {
+    LQ_DISPATCH_V(pv, (cg_xr_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs)));
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t blas_cg_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef s, SolverScalars *sc, int cur,
+                      cudaStream_t st) {
+  dim3 g = bgrid(Vh, nrhs);
+  LQ_DISPATCH_V(pv, (cg_p_kernel<SV><<<g, kBlasThreads, 0, st>>>(Vh, p, s, sc, cur)));
+  return cudaGetLastError();
+}
+
+cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, unsigned *counter,
+                       double *result, int stride, cudaStream_t st) {
+  dim3 g = bgrid(Vh, nrhs);
+  LQ_DISPATCH_V(pv, (norm2_kernel<SV><<<g, kBlasThreads, 0, st>>>(Vh, v, partials, counter, result, stride, nrhs)));
+  return cudaGetLastError();
+}
+
+cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
+                      cudaStream_t st) {
+  dim3 g = bgrid(Vh, nrhs);
+  if (py == LQCD_F64) {
+    LQ_DISPATCH_V(px, (axpy_kernel<double, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
+  } else if (py == LQCD_F32) {
+    LQ_DISPATCH_V(px, (axpy_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
+  } else if (py == LQCD_F16 && px == LQCD_F16) {
+    axpy_kernel<__half, __half><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f);
+  } else if (py == LQCD_BF16 && px == LQCD_BF16) {
+    axpy_kernel<__nv_bfloat16, __nv_bfloat16><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
+                       cudaStream_t st) {
+  dim3 g = bgrid(Vh, nrhs);
+  switch (py) {
+    case LQCD_F64: LQ_DISPATCH_V(px, (scale_kernel<double, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f))); break;
+    case LQCD_F32: LQ_DISPATCH_V(px, (scale_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f))); break;
+    case LQCD_F16: LQ_DISPATCH_V(px, (scale_kernel<__half, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f))); break;
+    case LQCD_BF16:
+      LQ_DISPATCH_V(px, (scale_kernel<__nv_bfloat16, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lqcd

@@ -1,0 +1,397 @@
+// The even-odd Wilson-clover hopping kernel and its fused epilogues.
+//
+// One thread owns one output site of one parity (and NR right-hand sides).
+// For each of the 8 directions it loads the neighbour spinor, projects it
+// onto a half-spinor with (1 -+ g_mu) (DeGrand-Rossi basis: g_mu =
+// [[0, B_mu], [B_mu^dag, 0]], so (1 + s g_mu) psi = (h, s B_mu^dag h) with
+// h = u + s B_mu l for psi = (u, l)), multiplies the two colour vectors by
+// U_mu(x) or U_mu(x-mu)^dag (the 12-real form rebuilt in registers), and
+// accumulates the reconstructed spinor.  The epilogue then applies, per
+// MODE, the inverse clover block (K2a: y = A^-1 D x), the local clover term
+// and an xpay (K2b: z = A x - kappa^2 D y), the folded reconstruction
+// A^-1 (b + kappa D x), gamma5 and an optional "z + c * result", and
+// accumulates ||result||^2 into a deterministic grid reduction.
+//
+// Link times spinor is a 3x3 complex matrix-vector product: no dense
+// contraction, so this runs on the CUDA cores; it is HBM-bound for FP32 and
+// half storage and FP64-ALU-bound for FP64 on GB300.
+#pragma once
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace lqcd {
+
+enum DslashMode {
+  MODE_HOP = 0,          // out = beta * hop
+  MODE_HOP_AINV = 1,     // out = Ainv (beta * hop)
+  MODE_LOCAL_IDENT = 2,  // out = alpha * x + beta * hop
+  MODE_LOCAL_A = 3,      // out = alpha * A x + beta * hop
+  MODE_FOLDED_AINV = 4   // out = Ainv (alpha * x + beta * hop)
+};
+
+struct FieldRef {
+  const void *data;  // [rhs][words][Vh]
+  const float *scale;  // [rhs][Vh] for FP16/BF16, else nullptr
+  long rhs_words;      // words of one RHS of one parity (stride between RHS, in words of that field)
+};
+
+struct DslashParams {
+  Geom g;
+  int out_parity;
+  int nrhs;
+  void *out;
+  float *out_scale;
+  FieldRef in;    // hop input (other parity); data == nullptr or beta == 0: no hop
+  FieldRef xloc;  // local term input (output parity)
+  FieldRef z;     // optional xpay input (output parity)
+  const void *links[4][2];  // [mu][parity]
+  const void *cmat;         // A^-1 of the output parity (packed blocks)
+  const float *cmat_scale;
+  const void *lmat;         // A of the output parity
+  const float *lmat_scale;
+  double alpha, beta, gz;
+  int g5_in, g5_hop, g5_total;
+  double *norm_partials;  // nullptr: no norm
+  unsigned int *norm_counter;
+  double *norm_result;    // result of RHS r at norm_result[r * norm_stride]
+  int norm_stride;
+};
+
+// ---------------------------------------------------------------------------
+// field access
+// ---------------------------------------------------------------------------
+template <typename S> __device__ __forceinline__ const void *rhs_base(const void *base, long rhs_words, int r) {
+  using Wd = Words<S, 24>;
+  return reinterpret_cast<const char *>(base) + (long)r * rhs_words * Wd::W;
+}
+
+template <typename S, bool STREAM = false>
+__device__ __forceinline__ void load_spinor(const FieldRef &f, long Vh, int r, long i,
+                                            cx<typename Math<S>::T> (&psi)[4][3]) {
+  using T = typename Math<S>::T;
+  S raw[24];
+  load_reals<S, 24, STREAM>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
+  T sc = (T)1;
+  if (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) psi[a][c] = mk<T>(sc * (T)to_f(raw[6 * a + 2 * c]), sc * (T)to_f(raw[6 * a + 2 * c + 1]));
+}
+
+template <typename S>
+__device__ __forceinline__ void store_spinor(void *base, float *scale, long rhs_words, long Vh, int r, long i,
+                                             const cx<typename Math<S>::T> (&psi)[4][3]) {
+  using T = typename Math<S>::T;
+  S raw[24];
+  T inv = (T)1;
+  if (IsHalf<S>::value) {
+    T m = (T)0;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) m = fmax(m, fmax(fabs(psi[a][c].r), fabs(psi[a][c].i)));
+    scale[(long)r * Vh + i] = (float)m;
+    inv = m > (T)0 ? (T)1 / m : (T)0;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      raw[6 * a + 2 * c] = from_f<S>(psi[a][c].r * inv);
+      raw[6 * a + 2 * c + 1] = from_f<S>(psi[a][c].i * inv);
+    }
+  void *b = reinterpret_cast<char *>(base) + (long)r * rhs_words * Words<S, 24>::W;
+  store_reals<S, 24>(b, Vh, i, raw);
+}
+
+template <> __device__ __forceinline__ void store_spinor<double>(void *base, float *, long rhs_words, long Vh, int r,
+                                                                 long i, const cx<double> (&psi)[4][3]) {
+  double raw[24];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      raw[6 * a + 2 * c] = psi[a][c].r;
+      raw[6 * a + 2 * c + 1] = psi[a][c].i;
+    }
+  void *b = reinterpret_cast<char *>(base) + (long)r * rhs_words * Words<double, 24>::W;
+  store_reals<double, 24>(b, Vh, i, raw);
+}
+
+// Link U_mu at site i of one parity; 12-real form rebuilds row 2 = conj(row0 x row1).
+template <typename S, int R>
+__device__ __forceinline__ void load_link(const void *base, long Vh, long i, cx<typename Math<S>::T> (&U)[3][3]) {
+  using T = typename Math<S>::T;
+  S raw[R];
+  load_reals<S, R, true>(base, Vh, i, raw);
+#pragma unroll
+  for (int k = 0; k < R / 6; k++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) U[k][c] = mk<T>((T)to_f(raw[6 * k + 2 * c]), (T)to_f(raw[6 * k + 2 * c + 1]));
+  if (R == 12) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const int a = (j + 1) % 3, b = (j + 2) % 3;
+      cx<T> t = U[0][a] * U[1][b] - U[0][b] * U[1][a];
+      U[2][j] = conjg(t);
+    }
+  }
+}
+
+// Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 complex
+// entries below the diagonal in row order (1,0),(2,0),(2,1),(3,0),...,(5,4).
+template <typename T>
+__device__ __forceinline__ void herm6_mul(const T (&m)[36], const cx<T> (&v)[6], cx<T> (&o)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) o[i] = m[i] * v[i];
+#pragma unroll
+  for (int i = 1; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      const int k = 6 + 2 * (i * (i - 1) / 2 + j);
+      cx<T> l = mk<T>(m[k], m[k + 1]);
+      o[i] = cmadd(l, v[j], o[i]);   // L_ij v_j
+      o[j] = cjmadd(l, v[i], o[j]);  // conj(L_ij) v_i
+    }
+}
+
+// Clover storage of one parity: two blocks of 36 reals, block-major,
+// [blk][words][Vh], plus one FP32 scale per site for FP16/BF16.
+template <typename S>
+__device__ __forceinline__ void load_clover_block(const void *base, const float *scale, long Vh, long i, int blk,
+                                                  typename Math<S>::T (&m)[36]) {
+  using T = typename Math<S>::T;
+  using Wd = Words<S, 36>;
+  S raw[36];
+  const void *b = reinterpret_cast<const char *>(base) + (long)blk * Wd::NW * Vh * Wd::W;
+  load_reals<S, 36, true>(b, Vh, i, raw);
+  T sc = (T)1;
+  if (IsHalf<S>::value) sc = (T)__ldg(scale + i);
+#pragma unroll
+  for (int k = 0; k < 36; k++) m[k] = sc * (T)to_f(raw[k]);
+}
+
+// out = M psi with M = diag(block+, block-) acting on (spins 0,1) and (2,3).
+template <typename S, int NR>
+__device__ __forceinline__ void clover_apply(const void *base, const float *scale, long Vh, long i,
+                                             cx<typename Math<S>::T> (&psi)[NR][4][3]) {
+  using T = typename Math<S>::T;
+#pragma unroll
+  for (int blk = 0; blk < 2; blk++) {
+    T m[36];
+    load_clover_block<S>(base, scale, Vh, i, blk, m);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      cx<T> v[6], o[6];
+#pragma unroll
+      for (int k = 0; k < 6; k++) v[k] = psi[r][2 * blk + k / 3][k % 3];
+      herm6_mul<T>(m, v, o);
+#pragma unroll
+      for (int k = 0; k < 6; k++) psi[r][2 * blk + k / 3][k % 3] = o[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spin projection and reconstruction, (1 + s g_mu), s = +-1
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void project(int mu, T s, const cx<T> (&p)[4][3], cx<T> (&h)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    switch (mu) {
+      case 0:  // B = [[0, i], [i, 0]]
+        h[0][c] = p[0][c] + s * times_i(p[3][c]);
+        h[1][c] = p[1][c] + s * times_i(p[2][c]);
+        break;
+      case 1:  // B = [[0, -1], [1, 0]]
+        h[0][c] = p[0][c] - s * p[3][c];
+        h[1][c] = p[1][c] + s * p[2][c];
+        break;
+      case 2:  // B = [[i, 0], [0, -i]]
+        h[0][c] = p[0][c] + s * times_i(p[2][c]);
+        h[1][c] = p[1][c] - s * times_i(p[3][c]);
+        break;
+      default:  // B = 1
+        h[0][c] = p[0][c] + s * p[2][c];
+        h[1][c] = p[1][c] + s * p[3][c];
+        break;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void reconstruct(int mu, T s, const cx<T> (&h)[2][3], cx<T> (&acc)[4][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[0][c] = acc[0][c] + h[0][c];
+    acc[1][c] = acc[1][c] + h[1][c];
+    switch (mu) {
+      case 0:  // s B^dag h, B^dag = [[0, -i], [-i, 0]]
+        acc[2][c] = acc[2][c] - s * times_i(h[1][c]);
+        acc[3][c] = acc[3][c] - s * times_i(h[0][c]);
+        break;
+      case 1:  // B^dag = [[0, 1], [-1, 0]]
+        acc[2][c] = acc[2][c] + s * h[1][c];
+        acc[3][c] = acc[3][c] - s * h[0][c];
+        break;
+      case 2:  // B^dag = [[-i, 0], [0, i]]
+        acc[2][c] = acc[2][c] - s * times_i(h[0][c]);
+        acc[3][c] = acc[3][c] + s * times_i(h[1][c]);
+        break;
+      default:
+        acc[2][c] = acc[2][c] + s * h[0][c];
+        acc[3][c] = acc[3][c] + s * h[1][c];
+        break;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void link_mul(const cx<T> (&U)[3][3], bool dag, const cx<T> (&h)[2][3],
+                                         cx<T> (&o)[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      cx<T> t = mk<T>(0, 0);
+#pragma unroll
+      for (int c = 0; c < 3; c++) t = dag ? cjmadd(U[c][r], h[a][c], t) : cmadd(U[r][c], h[a][c], t);
+      o[a][r] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <typename S, int R, int MODE, int NR>
+__global__ void __launch_bounds__(128) dslash_kernel(const __grid_constant__ DslashParams P) {
+  using T = typename Math<S>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rg = blockIdx.y;  // right-hand-side group
+  const bool valid = h < P.g.Vh;
+  const int p = P.out_parity;
+  double nrm[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) nrm[r] = 0.0;
+
+  if (valid) {
+    cx<T> acc[NR][4][3];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[r][a][c] = mk<T>(0, 0);
+
+    const bool hop = P.in.data != nullptr && P.beta != 0.0;
+    if (hop) {
+      const Coords xc = site_coords(P.g, h, p);
+#pragma unroll
+      for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+          const int dir = d == 0 ? +1 : -1;
+          const long n = neighbour(P.g, xc, h, mu, dir);
+          const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
+          const T s = dir > 0 ? (T)-1 : (T)1;  // forward (1 - g_mu), backward (1 + g_mu)
+          cx<T> U[3][3];
+          if (dir > 0)
+            load_link<S, R>(P.links[mu][p], P.g.Vh, h, U);
+          else
+            load_link<S, R>(P.links[mu][1 - p], P.g.Vh, n, U);
+#pragma unroll
+          for (int r = 0; r < NR; r++) {
+            cx<T> psi[4][3];
+            load_spinor<S>(P.in, P.g.Vh, rg * NR + r, n, psi);
+            if (P.g5_in) {
+#pragma unroll
+              for (int c = 0; c < 3; c++) {
+                psi[2][c] = (T)-1 * psi[2][c];
+                psi[3][c] = (T)-1 * psi[3][c];
+              }
+            }
+            cx<T> hh[2][3], uh[2][3];
+            project<T>(mu, s, psi, hh);
+            link_mul<T>(U, dir < 0, hh, uh);
+            if (wrap) {
+#pragma unroll
+              for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) uh[a][c] = (T)-1 * uh[a][c];
+            }
+            reconstruct<T>(mu, s, uh, acc[r]);
+          }
+        }
+      }
+      const T beta = (T)P.beta;
+#pragma unroll
+      for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const T sg = (P.g5_hop && a >= 2) ? -beta : beta;
+            acc[r][a][c] = sg * acc[r][a][c];
+          }
+    }
+
+    // ---- epilogue -------------------------------------------------------
+    if (MODE == MODE_LOCAL_IDENT || MODE == MODE_FOLDED_AINV || MODE == MODE_LOCAL_A) {
+      const T alpha = (T)P.alpha;
+      cx<T> x[NR][4][3];
+#pragma unroll
+      for (int r = 0; r < NR; r++) load_spinor<S>(P.xloc, P.g.Vh, rg * NR + r, h, x[r]);
+      if (MODE == MODE_LOCAL_A) clover_apply<S, NR>(P.lmat, P.lmat_scale, P.g.Vh, h, x);
+#pragma unroll
+      for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) acc[r][a][c] = acc[r][a][c] + alpha * x[r][a][c];
+    }
+    if (MODE == MODE_HOP_AINV || MODE == MODE_FOLDED_AINV) clover_apply<S, NR>(P.cmat, P.cmat_scale, P.g.Vh, h, acc);
+    if (P.g5_total) {
+#pragma unroll
+      for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          acc[r][2][c] = (T)-1 * acc[r][2][c];
+          acc[r][3][c] = (T)-1 * acc[r][3][c];
+        }
+    }
+    if (P.z.data != nullptr) {
+      const T gz = (T)P.gz;
+#pragma unroll
+      for (int r = 0; r < NR; r++) {
+        cx<T> zz[4][3];
+        load_spinor<S>(P.z, P.g.Vh, rg * NR + r, h, zz);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) acc[r][a][c] = zz[a][c] + gz * acc[r][a][c];
+      }
+    }
+    const long out_words = Words<S, 24>::NW * P.g.Vh;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      store_spinor<S>(P.out, P.out_scale, out_words, P.g.Vh, rg * NR + r, h, acc[r]);
+      if (P.norm_partials) {
+        double s2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) s2 += (double)acc[r][a][c].r * acc[r][a][c].r + (double)acc[r][a][c].i * acc[r][a][c].i;
+        nrm[r] = s2;
+      }
+    }
+  }
+  if (P.norm_partials) grid_reduce<NR>(nrm, P.norm_partials, P.norm_counter, P.norm_result, rg * NR, P.nrhs, P.norm_stride);
+}
+
+// Host-side launcher, instantiated per storage type in dslash_<type>.cu.
+template <typename S>
+cudaError_t launch_dslash(const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);
+
+}  // namespace lqcd

@@ -1,0 +1,50 @@
+// Launch-shape selection for the dslash kernel; included once per storage
+// type by dslash_f64.cu, dslash_f32.cu, dslash_f16.cu and dslash_bf16.cu so
+// the instantiations compile in parallel.
+#pragma once
+#include "dslash.cuh"
+
+namespace lqcd {
+
+constexpr int kDslashThreads = 128;
+
+template <typename S, int R, int MODE, int NR>
+static cudaError_t launch_one(const DslashParams &P, cudaStream_t st) {
+  dim3 grid((unsigned)((P.g.Vh + kDslashThreads - 1) / kDslashThreads), (unsigned)(P.nrhs / NR));
+  dslash_kernel<S, R, MODE, NR><<<grid, kDslashThreads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename S, int R, int MODE>
+static cudaError_t launch_nr(const DslashParams &P, int nr, cudaStream_t st) {
+  if (nr == 1) return launch_one<S, R, MODE, 1>(P, st);
+  if constexpr (MODE != MODE_FOLDED_AINV) {
+    if (nr == 2) return launch_one<S, R, MODE, 2>(P, st);
+    if (nr == 4) return launch_one<S, R, MODE, 4>(P, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S, int R>
+static cudaError_t launch_mode(const DslashParams &P, int mode, int nr, cudaStream_t st) {
+  switch (mode) {
+    case MODE_HOP: return launch_nr<S, R, MODE_HOP>(P, nr, st);
+    case MODE_HOP_AINV: return launch_nr<S, R, MODE_HOP_AINV>(P, nr, st);
+    case MODE_LOCAL_IDENT: return launch_nr<S, R, MODE_LOCAL_IDENT>(P, nr, st);
+    case MODE_LOCAL_A: return launch_nr<S, R, MODE_LOCAL_A>(P, nr, st);
+    case MODE_FOLDED_AINV: return launch_nr<S, R, MODE_FOLDED_AINV>(P, nr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S, bool WITH18>
+static cudaError_t launch_dslash_impl(const DslashParams &P, int recon, int mode, int nr, cudaStream_t st) {
+  if (P.nrhs % nr != 0) return cudaErrorInvalidValue;
+  if (recon == 12) return launch_mode<S, 12>(P, mode, nr, st);
+  if constexpr (WITH18) {
+    if (recon == 18) return launch_mode<S, 18>(P, mode, nr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lqcd

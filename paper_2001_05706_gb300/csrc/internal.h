@@ -1,0 +1,171 @@
+// Library-internal declarations shared by the .cu files: the context and
+// field objects behind the opaque C handles, and the host-side launchers.
+#pragma once
+#include <cstddef>
+#include <map>
+#include <string>
+
+#include "common.cuh"
+#include "dslash.cuh"
+
+namespace lqcd {
+
+struct MutField {
+  void *data;
+  float *scale;
+  long rhs_words;
+  __host__ __device__ FieldRef ref() const { return FieldRef{data, scale, rhs_words}; }
+};
+
+// ---- layout.cu
+cudaError_t pack_spinor(lqcd_prec prec, const Geom &g, int p, const double *canon, int nrhs, void *out, float *scale,
+                        long rhs_words, cudaStream_t st);
+cudaError_t unpack_spinor(lqcd_prec prec, const Geom &g, int p, const void *in, const float *scale, long rhs_words,
+                          int nrhs, double *canon, cudaStream_t st);
+cudaError_t zero_parity(const Geom &g, int p, double *canon, int nrhs, cudaStream_t st);
+cudaError_t convert_spinor(lqcd_prec pi, lqcd_prec po, long Vh, int nrhs, const void *in, const float *is, long irw,
+                           void *out, float *os, long orw, double factor, cudaStream_t st);
+size_t link_bytes(lqcd_prec prec, int recon, long Vh);
+cudaError_t pack_links(lqcd_prec prec, const Geom &g, const double *U, int recon, void *out, cudaStream_t st);
+const void *link_ptr(const void *base, lqcd_prec prec, int recon, long Vh, int mu, int p);
+cudaError_t su3_check(const double *U, long nlinks, unsigned long long *worst, cudaStream_t st);
+size_t clover_bytes(lqcd_prec prec, long Vh);
+cudaError_t pack_clover(lqcd_prec prec, long Vh, const double *in, void *out, float *scale, cudaStream_t st);
+
+// ---- clover.cu
+cudaError_t clover_build(const Geom &g, const double *U, double kappa, double csw, double *A[2], double *Ainv[2],
+                         int *singular, cudaStream_t st);
+
+// ---- blas.cu
+long blas_blocks(long Vh);
+cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, MutField r, FieldRef q,
+                       SolverScalars *sc, int cur, double *partials, unsigned *counter, cudaStream_t st);
+cudaError_t blas_cg_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef s, SolverScalars *sc, int cur,
+                      cudaStream_t st);
+cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, unsigned *counter,
+                       double *result, int stride, cudaStream_t st);
+cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
+                      cudaStream_t st);
+cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
+                       cudaStream_t st);
+
+// ---- dslash_<type>.cu
+cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);
+
+inline int prec_bytes(lqcd_prec p) { return p == LQCD_F64 ? 8 : p == LQCD_F32 ? 4 : 2; }
+inline bool prec_half(lqcd_prec p) { return p == LQCD_F16 || p == LQCD_BF16; }
+// 16-byte words of one spinor site (24 reals) in precision p
+inline long spinor_words(lqcd_prec p) { return 24L * prec_bytes(p) / 16; }
+
+}  // namespace lqcd
+
+// ---- the objects behind the opaque handles
+struct lqcd_field {
+  lqcd_ctx *ctx;
+  lqcd_prec prec;
+  lqcd_subset subset;
+  int nrhs;
+  long Vh;
+  void *data[2];    // per parity: [rhs][words][Vh]
+  float *scale[2];  // per parity: [rhs][Vh] (FP16/BF16), else nullptr
+  void *alloc;
+  float *scale_alloc;
+  long rhs_words() const { return lqcd::spinor_words(prec) * Vh; }
+  lqcd::FieldRef ref(int p) const { return lqcd::FieldRef{data[p], scale[p], rhs_words()}; }
+  lqcd::MutField mut(int p) const { return lqcd::MutField{data[p], scale[p], rhs_words()}; }
+  bool has(int p) const { return subset == LQCD_FULL || (int)subset == p; }
+};
+
+struct CloverStore {
+  void *A[2] = {nullptr, nullptr};
+  void *Ainv[2] = {nullptr, nullptr};
+  float *As[2] = {nullptr, nullptr};
+  float *Ais[2] = {nullptr, nullptr};
+  void *alloc = nullptr;
+};
+
+struct lqcd_ctx {
+  int dims[4];
+  int tbc;
+  cudaStream_t stream;
+  lqcd::Geom geom;
+  long V, Vh;
+  double *U64 = nullptr;  // canonical FP64 links on the device
+  bool have_gauge = false;
+  std::map<int, void *> links;  // key 100*prec + recon
+  double kappa = 0, csw = 0;
+  bool have_kappa = false;
+  bool clover_on = false;  // csw != 0 and built
+  CloverStore clov[4];
+  double rho = 0;
+  bool have_rho = false;
+  // reduction scratch
+  double *partials = nullptr;
+  size_t partials_n = 0;
+  unsigned *counter = nullptr;
+  double *results = nullptr;  // 256 doubles
+  double *h_results = nullptr;  // pinned mirror
+  // canonical staging for host <-> device transfers
+  double *canon[2] = {nullptr, nullptr};
+  size_t canon_n[2] = {0, 0};
+  // cached intermediate fields (key: 10*prec + nrhs*1000 + slot)
+  std::map<long, lqcd_field *> temps;
+};
+
+// ---- errors (abi.cu)
+namespace lqcd {
+lqcd_status set_error(lqcd_status s, const char *fmt, ...);
+}
+#define LQ_CU(call)                                                                                      \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return ::lqcd::set_error(LQCD_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                               __LINE__);                                                                \
+  } while (0)
+#define LQ_TRY(call)                       \
+  do {                                     \
+    lqcd_status s_ = (call);               \
+    if (s_ != LQCD_OK) return s_;          \
+  } while (0)
+
+// ---- operator layer (ops.cu)
+namespace lqcd {
+struct Term {  // an optional field operand of the dslash epilogue
+  FieldRef f{nullptr, nullptr, 0};
+};
+lqcd_status get_links(lqcd_ctx *c, lqcd_prec prec, int recon, const void **base);
+lqcd_status get_clover(lqcd_ctx *c, lqcd_prec prec, CloverStore **cs);
+lqcd_status ensure_partials(lqcd_ctx *c, int nrhs);
+// one launch of the generic dslash kernel on output parity out_p
+lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
+                       FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
+                       int g5_total, double *norm_result, int norm_stride);
+// y_e = A_ee^-1 D_eo x_o (g5 on the input if dagger)
+lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o);
+// z_o = [zf +gz*] (A_oo x_o - kappa^2 [g5] D_oe y_e), optional norm
+lqcd_status op_k2b(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride);
+// out_o = Mhat x_o or Mhat^dag x_o, y_e scratch
+lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                    MutField y_e, FieldRef zf, double gz, double *norm_result, int norm_stride);
+// full-lattice out = [zf + gz*] M x (dagger: M^dag), per parity
+lqcd_status op_M(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out[2], FieldRef x[2],
+                 FieldRef zf[2], double gz, double *norm_result, int norm_stride);
+// bhat_o = b_o + kappa D_oe A_ee^-1 b_e  (tmp_e scratch)
+lqcd_status op_prepare(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField bhat_o, FieldRef b_e, FieldRef b_o,
+                       MutField tmp_e);
+// x_e = A_ee^-1 (b_e + kappa D_eo x_o)
+lqcd_status op_reconstruct(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField x_e, FieldRef b_e,
+                           FieldRef x_o);
+// out_p = g5 [(4 - rho) x_p - D x_{1-p} / 2] on both parities
+lqcd_status op_hw(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double *norm_result,
+                  int norm_stride);
+}  // namespace lqcd
+
+namespace lqcd {
+// context-cached temporary field for (prec, subset, nrhs, slot); owned by the context
+lqcd_status temp_field(lqcd_ctx *c, lqcd_prec prec, lqcd_subset subset, int nrhs, int slot, lqcd_field **out);
+// device staging buffer `slot` (0 or 1) of at least n doubles
+lqcd_status staging(lqcd_ctx *c, int slot, size_t n, double **out);
+}  // namespace lqcd

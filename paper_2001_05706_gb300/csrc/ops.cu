@@ -1,0 +1,191 @@
+// Operator layer: the even-odd Wilson-clover operators built from launches
+// of the generic dslash kernel, and the lazily packed link and clover forms
+// they read.
+#include "internal.h"
+
+namespace lqcd {
+
+lqcd_status get_links(lqcd_ctx *c, lqcd_prec prec, int recon, const void **base) {
+  if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
+  if (recon != 12 && recon != 18) return set_error(LQCD_ERR_ARG, "recon must be 12 or 18");
+  if (prec_half(prec) && recon != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 links are stored in 12-real form only");
+  const int key = 100 * (int)prec + recon;
+  auto it = c->links.find(key);
+  if (it != c->links.end()) {
+    *base = it->second;
+    return LQCD_OK;
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, link_bytes(prec, recon, c->Vh)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ERR_OOM, "cannot allocate packed links");
+  }
+  LQ_CU(pack_links(prec, c->geom, c->U64, recon, p, c->stream));
+  c->links[key] = p;
+  *base = p;
+  return LQCD_OK;
+}
+
+lqcd_status get_clover(lqcd_ctx *c, lqcd_prec prec, CloverStore **cs) {
+  if (!c->clover_on) return set_error(LQCD_ERR_STATE, "no clover term (c_sw = 0 or lqcd_clover not called)");
+  CloverStore &s = c->clov[prec];
+  if (!s.alloc) {
+    const size_t nb = clover_bytes(prec, c->Vh);
+    const size_t ns = prec_half(prec) ? sizeof(float) * c->Vh : 0;
+    char *p = nullptr;
+    if (cudaMalloc(&p, 4 * (nb + ns)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(LQCD_ERR_OOM, "cannot allocate clover storage");
+    }
+    s.alloc = p;
+    for (int q = 0; q < 2; q++) {
+      s.A[q] = p + (2 * q) * nb;
+      s.Ainv[q] = p + (2 * q + 1) * nb;
+      if (ns) {
+        s.As[q] = reinterpret_cast<float *>(p + 4 * nb + (2 * q) * ns);
+        s.Ais[q] = reinterpret_cast<float *>(p + 4 * nb + (2 * q + 1) * ns);
+      }
+    }
+    const CloverStore &m = c->clov[LQCD_F64];
+    for (int q = 0; q < 2; q++) {
+      LQ_CU(pack_clover(prec, c->Vh, (const double *)m.A[q], s.A[q], s.As[q], c->stream));
+      LQ_CU(pack_clover(prec, c->Vh, (const double *)m.Ainv[q], s.Ainv[q], s.Ais[q], c->stream));
+    }
+  }
+  *cs = &s;
+  return LQCD_OK;
+}
+
+lqcd_status ensure_partials(lqcd_ctx *c, int nrhs) {
+  const size_t need = (size_t)((c->Vh + 127) / 128 + 1) * (size_t)(nrhs < 1 ? 1 : nrhs);
+  if (need <= c->partials_n) return LQCD_OK;
+  if (c->partials) {
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->partials);
+    c->partials = nullptr;
+  }
+  if (cudaMalloc(&c->partials, need * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->partials_n = 0;
+    return set_error(LQCD_ERR_OOM, "cannot allocate reduction scratch");
+  }
+  c->partials_n = need;
+  return LQCD_OK;
+}
+
+static int pick_nr(lqcd_prec prec, int mode, int nrhs) {
+  if (mode == MODE_FOLDED_AINV) return 1;
+  if (prec == LQCD_F64) return nrhs % 2 == 0 ? 2 : 1;
+  if (nrhs % 4 == 0) return 4;
+  if (nrhs % 2 == 0) return 2;
+  return 1;
+}
+
+lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
+                       FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
+                       int g5_total, double *norm_result, int norm_stride) {
+  DslashParams P{};
+  P.g = c->geom;
+  P.out_parity = out_p;
+  P.nrhs = nrhs;
+  P.out = out.data;
+  P.out_scale = out.scale;
+  P.in = in;
+  P.xloc = xloc;
+  P.z = z;
+  const bool hop = in.data != nullptr && beta != 0.0;
+  if (hop) {
+    const void *base = nullptr;
+    LQ_TRY(get_links(c, prec, recon, &base));
+    for (int mu = 0; mu < 4; mu++)
+      for (int q = 0; q < 2; q++) P.links[mu][q] = link_ptr(base, prec, recon, c->Vh, mu, q);
+  }
+  if (mode == MODE_HOP_AINV || mode == MODE_FOLDED_AINV || mode == MODE_LOCAL_A) {
+    CloverStore *cs = nullptr;
+    LQ_TRY(get_clover(c, prec, &cs));
+    P.cmat = cs->Ainv[out_p];
+    P.cmat_scale = cs->Ais[out_p];
+    P.lmat = cs->A[out_p];
+    P.lmat_scale = cs->As[out_p];
+  }
+  P.alpha = alpha;
+  P.beta = beta;
+  P.gz = gz;
+  P.g5_in = g5_in;
+  P.g5_hop = g5_hop;
+  P.g5_total = g5_total;
+  if (norm_result) {
+    LQ_TRY(ensure_partials(c, nrhs));
+    P.norm_partials = c->partials;
+    P.norm_counter = c->counter;
+    P.norm_result = norm_result;
+    P.norm_stride = norm_stride;
+  }
+  const int nr = pick_nr(prec, mode, nrhs);
+  LQ_CU(launch_dslash_prec(prec, P, recon, mode, nr, c->stream));
+  return LQCD_OK;
+}
+
+static const FieldRef kNone{nullptr, nullptr, 0};
+
+lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  const int mode = c->clover_on ? MODE_HOP_AINV : MODE_HOP;
+  return run_dslash(c, prec, recon, mode, 0, nrhs, y_e, x_o, kNone, kNone, 0.0, 1.0, 0.0, dagger, 0, 0, nullptr, 0);
+}
+
+lqcd_status op_k2b(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  const int mode = c->clover_on ? MODE_LOCAL_A : MODE_LOCAL_IDENT;
+  return run_dslash(c, prec, recon, mode, 1, nrhs, out_o, y_e, x_o, zf, 1.0, -c->kappa * c->kappa, gz, 0, dagger, 0,
+                    norm_result, norm_stride);
+}
+
+lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                    MutField y_e, FieldRef zf, double gz, double *norm_result, int norm_stride) {
+  LQ_TRY(op_k2a(c, prec, recon, dagger, nrhs, y_e, x_o));
+  return op_k2b(c, prec, recon, dagger, nrhs, out_o, x_o, y_e.ref(), zf, gz, norm_result, norm_stride);
+}
+
+lqcd_status op_M(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out[2], FieldRef x[2],
+                 FieldRef zf[2], double gz, double *norm_result, int norm_stride) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  const int mode = c->clover_on ? MODE_LOCAL_A : MODE_LOCAL_IDENT;
+  for (int p = 0; p < 2; p++) {
+    // M^dag = g5 M g5 = A - kappa g5 D g5 (A commutes with g5)
+    LQ_TRY(run_dslash(c, prec, recon, mode, p, nrhs, out[p], x[1 - p], x[p], zf[p], 1.0, -c->kappa, gz, dagger, dagger,
+                      0, norm_result ? norm_result + p : nullptr, norm_stride));
+  }
+  return LQCD_OK;
+}
+
+lqcd_status op_prepare(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField bhat_o, FieldRef b_e, FieldRef b_o,
+                       MutField tmp_e) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  FieldRef src = b_e;
+  if (c->clover_on) {  // tmp_e = A_ee^-1 b_e (site-local: no hop)
+    LQ_TRY(run_dslash(c, prec, recon, MODE_FOLDED_AINV, 0, nrhs, tmp_e, kNone, b_e, kNone, 1.0, 0.0, 0.0, 0, 0, 0,
+                      nullptr, 0));
+    src = tmp_e.ref();
+  }
+  return run_dslash(c, prec, recon, MODE_HOP, 1, nrhs, bhat_o, src, kNone, b_o, 0.0, c->kappa, 1.0, 0, 0, 0, nullptr, 0);
+}
+
+lqcd_status op_reconstruct(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField x_e, FieldRef b_e,
+                           FieldRef x_o) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  const int mode = c->clover_on ? MODE_FOLDED_AINV : MODE_LOCAL_IDENT;
+  return run_dslash(c, prec, recon, mode, 0, nrhs, x_e, x_o, b_e, kNone, 1.0, c->kappa, 0.0, 0, 0, 0, nullptr, 0);
+}
+
+lqcd_status op_hw(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double *norm_result,
+                  int norm_stride) {
+  if (!c->have_rho) return set_error(LQCD_ERR_STATE, "rho not set (call lqcd_set_rho)");
+  for (int p = 0; p < 2; p++)
+    LQ_TRY(run_dslash(c, prec, recon, MODE_LOCAL_IDENT, p, nrhs, out[p], x[1 - p], x[p], kNone, 4.0 - c->rho, -0.5, 0.0,
+                      0, 0, 1, norm_result ? norm_result + p : nullptr, norm_stride));
+  return LQCD_OK;
+}
+
+}  // namespace lqcd

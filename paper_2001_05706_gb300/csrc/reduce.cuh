@@ -1,0 +1,67 @@
+// Deterministic FP64 grid reductions without floating-point atomics.
+//
+// Each block reduces its threads' values with a fixed shuffle tree and
+// writes one partial per reduced quantity; the block that finishes last
+// (found with an integer atomic counter) adds the partials in a fixed order
+// and writes the result.  Same grid, same inputs: bitwise-identical result,
+// independent of block scheduling.  The counter is reset by that last block,
+// so a launch sequence can be replayed (or captured in a CUDA graph).
+#pragma once
+#include "common.cuh"
+
+namespace lqcd {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce NV values per thread over the blocks of one grid row.  Block
+// (x, y) contributes to quantities kbase .. kbase+NV-1 (callers use
+// kbase = y * NV, so the rows of a 2-D grid hold different quantities);
+// partials must hold nk_total * gridDim.x doubles and result[k] receives the
+// sum of quantity k (at result[k * rstride]) for k < nk_total.  All threads of the block must call
+// this (no early return before it).
+template <int NV>
+__device__ __forceinline__ void grid_reduce(const double (&v)[NV], double *partials, unsigned int *counter,
+                                            double *result, int kbase, int nk_total, int rstride = 1) {
+  __shared__ double sh[NV][32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  const unsigned nblk_x = gridDim.x;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double s = lane < nwarp ? sh[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) partials[(long)(kbase + k) * nblk_x + blockIdx.x] = s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned total = gridDim.x * gridDim.y;
+    unsigned done = atomicAdd(counter, 1u);
+    last = (done == total - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    // warp w sums quantities k = w, w + nwarp, ...; lane-strided then tree
+    for (int k = warp; k < nk_total; k += nwarp) {
+      double s = 0.0;
+      for (unsigned b = lane; b < nblk_x; b += 32) s += __ldcg(partials + (long)k * nblk_x + b);
+      s = warp_sum(s);
+      if (lane == 0) result[(long)k * rstride] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+}  // namespace lqcd

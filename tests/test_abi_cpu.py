@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU and
+exports every function include/lqcd.h declares."""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2001_05706_gb300 import build
+    lib = build.build()
+    names = _declared()
+    assert "lqcd_dslash" in names and "lqcd_solve" in names and len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lqcd_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    dll = ctypes.CDLL(lib)
+    for n in names:
+        getattr(dll, n)
+
+
+def test_binding_reports_errors_without_gpu():
+    import paper_2001_05706_gb300 as L
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return
+    except ImportError:
+        pass
+    try:
+        L.lqcd_create((4, 4, 4, 4))
+    except L.LqcdError as e:
+        assert e.status in (L.LQCD_ERR_OOM, L.LQCD_ERR_CUDA)
+    else:
+        raise AssertionError("context creation succeeded without a GPU")
+    try:
+        L.lqcd_create((4, 3, 4, 4))
+    except L.LqcdError as e:
+        assert e.status == L.LQCD_ERR_ARG and "even" in str(e)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the parameter structs match the C compiler's layout."""
+    import paper_2001_05706_gb300 as L
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lqcd_solve_params), sizeof(lqcd_solve_info),'
+        ' offsetof(lqcd_solve_params, check_every), offsetof(lqcd_solve_info, true_resid),'
+        ' offsetof(lqcd_solve_info, mhat_applies)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    P, I = L.lqcd_solve_params, L.lqcd_solve_info
+    assert got == [ctypes.sizeof(P), ctypes.sizeof(I), P.check_every.offset, I.true_resid.offset,
+                   I.mhat_applies.offset]

@@ -1,0 +1,254 @@
+"""GPU parity of the operator kernels against the FP64 oracle, through the C ABI.
+
+Tolerances (relative 2-norm over the output sites): 1e-12 for FP64 storage,
+1e-5 for FP32, 1e-2 for FP16/BF16 storage with FP32 arithmetic."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-2, "bf16": 1e-2}
+KAPPA, CSW, RHO = 0.12, 1.0, 1.5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_05706_gb300 as L
+    return L
+
+
+def _setup(L, dims, eps, seed, csw=CSW, tbc=1):
+    U = gen.gauge_field(dims, eps, seed)
+    lat = L.Lattice(dims, tbc)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(KAPPA, csw)
+    lat.set_rho(RHO)
+    A = oracle.clover(dims, U, KAPPA, csw) if csw != 0 else None
+    Ai = oracle.clover_inverse(A) if A is not None else None
+    return lat, U, A, Ai
+
+
+def _oracle_op(op, dims, U, A, Ai, psi, tbc=1):
+    e = lambda v: oracle.keep_parity(dims, v, 0)
+    o = lambda v: oracle.keep_parity(dims, v, 1)
+    if op == "HOP_EO":
+        return e(oracle.hop(dims, U, o(psi), tbc))
+    if op == "HOP_OE":
+        return o(oracle.hop(dims, U, e(psi), tbc))
+    if op == "K2A":
+        return e(oracle.site_mul(Ai, oracle.hop(dims, U, o(psi), tbc)))
+    if op == "M":
+        return oracle.apply_M(dims, U, A, KAPPA, psi, tbc)
+    if op == "M_DAG":
+        return oracle.apply_M(dims, U, A, KAPPA, psi, tbc, dagger=True)
+    if op == "MHAT":
+        return oracle.apply_Mhat(dims, U, A, Ai, KAPPA, o(psi), tbc)
+    if op == "MHAT_DAG":
+        return oracle.apply_Mhat(dims, U, A, Ai, KAPPA, o(psi), tbc, dagger=True)
+    if op == "MHAT_NORMAL":
+        t = oracle.apply_Mhat(dims, U, A, Ai, KAPPA, o(psi), tbc)
+        return oracle.apply_Mhat(dims, U, A, Ai, KAPPA, t, tbc, dagger=True)
+    if op == "HW":
+        return oracle.apply_HW(dims, U, RHO, psi, tbc)
+    raise ValueError(op)
+
+
+OPS = ["HOP_EO", "HOP_OE", "K2A", "M", "M_DAG", "MHAT", "MHAT_DAG", "MHAT_NORMAL", "HW"]
+# (8,6,4,10): 960 sites per parity = 7.5 blocks of 128 threads (ragged tail)
+DIMS = (8, 6, 4, 10)
+
+
+@pytest.fixture(scope="module")
+def clover_lattice(lib):
+    lat, U, A, Ai = _setup(lib, DIMS, 0.3, 1001)
+    yield lat, U, A, Ai
+    lat.close()
+
+
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12)])
+def test_ops_clover(clover_lattice, op, prec, recon):
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 2001)[0]
+    out = lat.dslash(psi, op, prec, recon)
+    expect = _oracle_op(op, DIMS, U, A, Ai, psi)
+    assert rel(out, expect) < TOL[prec], f"{op} {prec} r{recon}"
+
+
+@pytest.mark.parametrize("op", ["K2A", "MHAT", "MHAT_DAG", "M"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_ops_wilson(lib, op, prec):
+    dims = (4, 4, 6, 8)
+    lat, U, A, Ai = _setup(lib, dims, 0.3, 7, csw=0.0)
+    psi = gen.gaussian_spinor(dims, 8)[0]
+    recon = 12
+    out = lat.dslash(psi, op, prec, recon)
+    assert rel(out, _oracle_op(op, dims, U, None, None, psi)) < TOL[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("nrhs", [2, 3, 4, 12])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_multi_rhs(clover_lattice, nrhs, prec):
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 3000 + nrhs, nrhs=nrhs)
+    out = lat.dslash(psi, "MHAT", prec, 12)
+    for k in range(nrhs):
+        assert rel(out[k], _oracle_op("MHAT", DIMS, U, A, Ai, psi[k])) < TOL[prec]
+
+
+def test_periodic_time_and_2x4(lib):
+    """Periodic t, and the 2^4 lattice where x+mu and x-mu coincide."""
+    for dims, tbc in [((2, 2, 2, 2), 1), ((4, 2, 2, 4), 0)]:
+        lat, U, A, Ai = _setup(lib, dims, 0.5, 5, tbc=tbc)
+        psi = gen.gaussian_spinor(dims, 6)[0]
+        for op in ("M", "MHAT"):
+            out = lat.dslash(psi, op, "f64", 18)
+            assert rel(out, _oracle_op(op, dims, U, A, Ai, psi, tbc)) < 1e-12
+        lat.close()
+
+
+def test_device_buffers_match_host(clover_lattice):
+    import torch
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 44, nrhs=2)
+    host = lat.dslash(psi, "MHAT", "f32", 12)
+    t = torch.from_numpy(psi.view(np.float64).copy()).cuda()
+    dev = lat.dslash(t, "MHAT", "f32", 12)
+    assert np.array_equal(dev.cpu().numpy().view(np.complex128).reshape(host.shape), host)
+
+
+def test_field_api_and_schur_split(clover_lattice, lib):
+    L = lib
+    lat, U, A, Ai = clover_lattice
+    ctx = lat.ctx
+    psi = gen.gaussian_spinor(DIMS, 91)[0]
+    xo = oracle.keep_parity(DIMS, psi, 1)
+    fx = L.lqcd_field_create(ctx, L.LQCD_F64, L.LQCD_ODD, 1)
+    fy = L.lqcd_field_create(ctx, L.LQCD_F64, L.LQCD_EVEN, 1)
+    fz = L.lqcd_field_create(ctx, L.LQCD_F64, L.LQCD_ODD, 1)
+    try:
+        L.lqcd_field_import(ctx, fx, np.ascontiguousarray(psi))
+        back = np.zeros_like(psi)
+        L.lqcd_field_export(ctx, fx, back)
+        assert np.array_equal(back, xo)  # exact round trip of the odd sites
+        L.lqcd_apply(ctx, L.LQCD_OP_K2A, 18, fy, fx)
+        L.lqcd_apply_schur(ctx, 18, 0, fz, fx, fy)
+        z = np.zeros_like(psi)
+        L.lqcd_field_export(ctx, fz, z)
+        assert rel(z, _oracle_op("MHAT", DIMS, U, A, Ai, psi)) < 1e-12
+        # dagger split: y from g5 x, then the g5 on the hop result
+        fg = L.lqcd_field_create(ctx, L.LQCD_F64, L.LQCD_ODD, 1)
+        L.lqcd_field_import(ctx, fg, np.ascontiguousarray(oracle.gamma5(psi)))
+        L.lqcd_apply(ctx, L.LQCD_OP_K2A, 18, fy, fg)
+        L.lqcd_apply_schur(ctx, 18, 1, fz, fx, fy)
+        L.lqcd_field_export(ctx, fz, z)
+        assert rel(z, _oracle_op("MHAT_DAG", DIMS, U, A, Ai, psi)) < 1e-12
+        L.lqcd_field_destroy(fg)
+        # deterministic FP64 norm
+        n1 = L.lqcd_field_norm2(ctx, fz)
+        n2 = L.lqcd_field_norm2(ctx, fz)
+        assert n1 == n2
+        assert abs(n1 - oracle.norm2(z)) < 1e-12 * n1
+    finally:
+        for f in (fx, fy, fz):
+            L.lqcd_field_destroy(f)
+
+
+def test_rejects_non_su3_and_bad_args(lib):
+    L = lib
+    dims = (4, 4, 4, 4)
+    U = gen.gauge_field(dims, 0.3, 1)
+    U[1, 2, 3, 0, 2] *= 1.001
+    lat = L.Lattice(dims)
+    with pytest.raises(L.LqcdError) as e:
+        lat.load_gauge(U.view(np.float64))
+    assert e.value.status == L.LQCD_ERR_NOT_SU3
+    psi = gen.gaussian_spinor(dims, 1)[0]
+    with pytest.raises(L.LqcdError) as e:
+        lat.dslash(psi, "MHAT", "f64", 18)
+    assert e.value.status == L.LQCD_ERR_STATE
+    lat.load_gauge(gen.gauge_field(dims, 0.3, 1).view(np.float64))
+    with pytest.raises(L.LqcdError) as e:
+        lat.dslash(psi, "MHAT", "f64", 18)  # kappa not set yet
+    assert e.value.status == L.LQCD_ERR_STATE
+    lat.clover(0.12, 1.0)
+    with pytest.raises(L.LqcdError) as e:
+        lat.dslash(psi, "MHAT", "f16", 18)  # half links are 12-real only
+    assert e.value.status == L.LQCD_ERR_ARG
+    with pytest.raises(L.LqcdError):
+        L.lqcd_create((4, 3, 4, 4))
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# full size: 32^3 x 64, the configuration the benchmark times, sampled sites
+# ---------------------------------------------------------------------------
+
+def _mhat_at_sites(dims, U, kappa, csw, x, sites):
+    """Mhat x at the given odd sites, from per-site oracle evaluations only."""
+    V = int(np.prod(dims))
+    xo = oracle.keep_parity(dims, x, 1)
+    # the even neighbours of each sample, and y = A^-1 D x there
+    L0, L1, L2, L3 = dims
+    x0, x1, x2, x3 = oracle.site_coords(dims, np.asarray(sites))
+    nb = set()
+    for mu, Lm in enumerate(dims):
+        for d in (1, -1):
+            c = [x0.copy(), x1.copy(), x2.copy(), x3.copy()]
+            c[mu] = (c[mu] + d) % Lm
+            nb.update((c[0] + L0 * (c[1] + L1 * (c[2] + L2 * c[3]))).tolist())
+    nb = np.array(sorted(nb))
+    Dx = oracle.hop_sites(dims, U, xo, nb)
+    An = oracle.clover_sites(dims, U, kappa, csw, nb)
+    y = np.zeros((V, 12), dtype=np.complex128)
+    for k, s in enumerate(nb):
+        y[s] = np.linalg.solve(An[k], Dx[k].reshape(12))
+    Dy = oracle.hop_sites(dims, U, y.reshape(oracle.spinor_shape(dims)), sites)
+    As = oracle.clover_sites(dims, U, kappa, csw, sites)
+    xf = xo.reshape(V, 12)
+    return np.stack([As[k] @ xf[s] - kappa**2 * Dy[k].reshape(12) for k, s in enumerate(sites)])
+
+
+@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f64", 18), ("f16", 12)])
+def test_full_size_sampled(lib, prec, recon):
+    L = lib
+    dims = (32, 32, 32, 64)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1002)
+    lat = L.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    psi = gen.gaussian_spinor(dims, 2002)[0]
+    ctx = lat.ctx
+    P = L.PREC[prec]
+    fx = L.lqcd_field_create(ctx, P, L.LQCD_ODD, 1)
+    fz = L.lqcd_field_create(ctx, P, L.LQCD_ODD, 1)
+    L.lqcd_field_import(ctx, fx, psi)
+    L.lqcd_apply(ctx, L.LQCD_OP_MHAT, recon, fz, fx)  # the call the benchmark times
+    z = np.zeros_like(psi)
+    L.lqcd_field_export(ctx, fz, z)
+    L.lqcd_field_destroy(fx)
+    L.lqcd_field_destroy(fz)
+    lat.close()
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(0)
+    cand = rng.choice(V, 400, replace=False)
+    par = np.array([sum(c) % 2 for c in zip(*oracle.site_coords(dims, cand))])
+    # odd sites on the t boundaries and the x, y, z wraps, plus random ones
+    edge = []
+    for c in [(31, 0, 0, 0), (0, 31, 0, 0), (0, 0, 31, 0), (0, 0, 0, 63), (31, 31, 31, 63), (1, 0, 0, 0),
+              (30, 0, 0, 63), (31, 0, 1, 0), (0, 0, 0, 1)]:
+        if sum(c) % 2 == 1:
+            edge.append(c[0] + 32 * (c[1] + 32 * (c[2] + 32 * c[3])))
+    sites = np.array(sorted(set(edge) | set(cand[par == 1][:64].tolist())))
+    expect = _mhat_at_sites(dims, U, kappa, csw, psi, sites)
+    got = z.reshape(V, 12)[sites]
+    assert rel(got, expect) < TOL[prec]

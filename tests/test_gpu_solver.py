@@ -1,0 +1,104 @@
+"""GPU solves checked by the FP64 oracle: true residual ||b - M x|| / ||b||
+recomputed on the CPU from the returned x, and x against the oracle's own
+solution."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_05706_gb300 as L
+    return L
+
+
+def test_fp64_cg_wilson_8x4(lib):
+    """Plain Wilson (c_sw = 0) even-odd CG in FP64 on 8^4, kappa = 0.12, eps = 0.3."""
+    dims = (8, 8, 8, 8)
+    U = gen.gauge_field(dims, 0.3, 1001)
+    b = gen.gaussian_spinor(dims, 2001)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(0.12, 0.0)
+    x, st, info = lat.solve(b, tol=1e-10, inner="f64", recon=18)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    r = oracle.true_residual(dims, U, None, 0.12, x, b)
+    assert r <= 1e-10
+    assert info.true_resid[0] <= 1e-10
+    xo, it, _ = oracle.solve(dims, U, None, None, 0.12, b, tol=1e-12)
+    assert rel(x, xo) < 1e-9
+    lat.close()
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16", "bf16"])
+def test_mixed_clover(lib, inner):
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner=inner, delta=0.1, recon=18, inner_recon=12)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    assert oracle.true_residual(dims, U, A, kappa, x, b) <= 1e-10
+    assert info.reliable_updates >= 1
+    lat.close()
+
+
+def test_multi_rhs_point_sources(lib):
+    """12 point sources, mixed FP16 inner solver, every one to 1e-10."""
+    dims = (8, 8, 8, 8)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1004)
+    b = gen.point_sources(dims)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner="f16", nrhs=12)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(12):
+        assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+    lat.close()
+
+
+def test_solve_deterministic_and_x0(lib):
+    dims = (4, 4, 4, 8)
+    U = gen.gauge_field(dims, 0.3, 9)
+    b = gen.gaussian_spinor(dims, 10)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(0.12, 1.0)
+    x1, st1, i1 = lat.solve(b, inner="f32")
+    x2, st2, i2 = lat.solve(b, inner="f32")
+    assert st1 == st2 == lib.LQCD_OK
+    assert np.array_equal(x1, x2) and i1.iters == i2.iters
+    # restart from the solution: converges immediately
+    prm = lib.solve_params(tol=1e-10, inner=lib.LQCD_F64, use_x0=1)
+    x3 = x1.copy()
+    st, info = lib.lqcd_solve(lat.ctx, x3, b, prm)
+    assert info.iters == 0
+    lat.close()
+
+
+def test_noconv_reports(lib):
+    dims = (4, 4, 4, 8)
+    U = gen.gauge_field(dims, 0.3, 9)
+    b = gen.gaussian_spinor(dims, 10)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(0.12, 1.0)
+    x, st, info = lat.solve(b, max_iter=3, inner="f64")
+    assert st == lib.LQCD_ERR_NOCONV
+    assert info.iters == 3 and info.true_resid[0] > 1e-10
+    lat.close()
