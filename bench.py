@@ -1,0 +1,480 @@
+"""Benchmark: Wilson-clover even-odd dslash HBM throughput on GB300, and
+mixed-precision vs FP64 solve time to a true residual of 1e-10.
+
+Workload (one "step"): one application of the Schur complement
+Mhat = A_oo - kappa^2 D_oe A_ee^-1 D_eo (kernels K2a: y = A^-1 D x and
+K2b: z = A x - kappa^2 D y) on a 32^3 x 64 lattice, c_sw = 1.0,
+kappa = 0.125, links exp(i 0.2 A) (seeded synthetic), FP32 storage and
+arithmetic, 12-real links, one right-hand side, fields resident in HBM.
+Throughput uses the compulsory byte model: per output site 8 links, the
+input spinor, the output spinor, the clover block pair (and the local
+spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
+                  [--no-solve] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded
+time-slab samples per step).  --kernel-only runs just that kernel (for ncu).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 64)
+KAPPA, CSW, EPS = 0.125, 1.0, 0.2
+GAUGE_SEED, SRC_SEED = 1002, 2002
+METRIC = "Wilson-clover dslash HBM GB/s (% of peak); mixed vs FP64 solve time to 1e-10"
+WORKLOAD = ("Wilson-clover even-odd Mhat = K2a (A^-1 D) + K2b (A x - kappa^2 D y), 32^3x64, c_sw=1.0, "
+            "kappa=0.125, links exp(i*0.2*A) seeded, FP32 storage+math, 12-real links, 1 RHS")
+FLOPS = {"k2a": 1824, "k2b": 1872}
+PB = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def site_bytes(prec: str, recon: int, kernel: str) -> int:
+    """Compulsory bytes per output site: 8 links, input spinor, output spinor,
+    clover block pair (+ the local spinor for K2b); FP16/BF16 add a 4-byte
+    scale per spinor and clover site."""
+    b = PB[prec]
+    half = prec in ("f16", "bf16")
+    link = 8 * recon * b
+    sp = 24 * b + (4 if half else 0)
+    cl = 72 * b + (4 if half else 0)
+    k2a = link + 2 * sp + cl
+    return k2a if kernel == "k2a" else k2a + sp
+
+
+def mhat_bytes(prec, recon):
+    return site_bytes(prec, recon, "k2a") + site_bytes(prec, recon, "k2b")
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        return 6800.0, "recipe fallback 6.8 TB/s (of fallback)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cuh", "common.cuh", "reduce.cuh", "dslash_inst.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2001_05706_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """Per-launch DRAM bytes recorded in profiles/<name>.md, if the kernel
+    source has not changed since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(float(vals["traffic_bytes_per_launch_full_size"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                 str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank].strip()
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle pieces (cpu_baseline leg and the reference arm only)
+# ---------------------------------------------------------------------------
+
+def oracle_setup(U):
+    import oracle
+    A = oracle.clover(DIMS, U, KAPPA, CSW)
+    Ai = oracle.clover_inverse(A)
+    return A, Ai
+
+
+def oracle_slab_rate(U, A, Ai, psi, target_s=15.0, max_slices=None):
+    """Time the oracle Mhat on whole time slices until ~target_s; returns
+    (sites per second, slices timed, seconds)."""
+    import oracle
+    out = np.zeros_like(psi)
+    t0 = time.perf_counter()
+    oracle.mhat_slab(DIMS, U, A, Ai, KAPPA, psi, 0, 1, out)
+    one = time.perf_counter() - t0
+    n = max(1, min(DIMS[3], int(target_s / max(one, 1e-3))))
+    if max_slices:
+        n = min(n, max_slices)
+    t0 = time.perf_counter()
+    oracle.mhat_slab(DIMS, U, A, Ai, KAPPA, psi, 0, n, out)
+    dt = time.perf_counter() - t0
+    sites = n * DIMS[0] * DIMS[1] * DIMS[2] // 2
+    return sites / dt, n, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def make_inputs():
+    import gen
+    U = gen.gauge_field(DIMS, EPS, GAUGE_SEED)
+    psi = gen.gaussian_spinor(DIMS, SRC_SEED)[0]
+    return U, psi
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    U, psi = make_inputs()
+    A, Ai = oracle_setup(U)
+    import oracle
+    out = np.zeros_like(psi)
+    # bounded per-step sample: whole time slices, sized so K+W steps take ~2 min
+    t0 = time.perf_counter()
+    oracle.mhat_slab(DIMS, U, A, Ai, KAPPA, psi, 0, 1, out)
+    one = time.perf_counter() - t0
+    per_step = max(1, min(DIMS[3], int(120.0 / max(1, args.steps + args.warmup) / max(one, 1e-3))))
+    for w in range(args.warmup):
+        t = (w * per_step) % DIMS[3]
+        oracle.mhat_slab(DIMS, U, A, Ai, KAPPA, psi, t, min(DIMS[3], t + per_step), out)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        t = (k * per_step) % DIMS[3]
+        oracle.mhat_slab(DIMS, U, A, Ai, KAPPA, psi, t, min(DIMS[3], t + per_step), out)
+    dt = time.perf_counter() - t0
+    sites = args.steps * per_step * DIMS[0] * DIMS[1] * DIMS[2] // 2
+    gbs = sites * mhat_bytes("f32", 12) / dt / 1e9
+    sample = (f"oracle Mhat (FP64, full 4x4 spin matrices, 12x12 clover) on {per_step} of {DIMS[3]} time slices "
+              f"per step of the 32^3x64 workload; GB/s counts the workload's FP32 12-real compulsory bytes "
+              f"({mhat_bytes('f32', 12)} B per output site)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "prec": "f32", "recon": 12, "nrhs": 1},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                         "sites_per_s": sites / dt},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_ms(torch, fn, steps, stream):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def kernel_only(args):
+    """A few launches of one kernel for an ncu capture."""
+    import torch
+    import gen
+    import paper_2001_05706_gb300 as L
+    dims = tuple(int(v) for v in args.lattice.split(","))
+    torch.cuda.set_device(0)
+    U = gen.gauge_field(dims, EPS, GAUGE_SEED)
+    psi = gen.gaussian_spinor(dims, SRC_SEED)[0]
+    P = L.PREC[args.prec]
+    with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(KAPPA, CSW)
+        ctx = lat.ctx
+        fx = L.lqcd_field_create(ctx, P, L.LQCD_ODD, args.nrhs)
+        fy = L.lqcd_field_create(ctx, P, L.LQCD_EVEN, args.nrhs)
+        fz = L.lqcd_field_create(ctx, P, L.LQCD_ODD, args.nrhs)
+        L.lqcd_field_import(ctx, fx, np.ascontiguousarray(np.broadcast_to(psi, (args.nrhs,) + psi.shape)))
+        L.lqcd_apply(ctx, L.LQCD_OP_K2A, args.recon, fy, fx)
+        L.lqcd_synchronize(ctx)
+        for _ in range(args.warmup + args.steps):
+            if args.kernel_only in ("k2a", "mhat"):
+                L.lqcd_apply(ctx, L.LQCD_OP_K2A, args.recon, fy, fx)
+            if args.kernel_only in ("k2b", "mhat"):
+                L.lqcd_apply_schur(ctx, args.recon, 0, fz, fx, fy)
+        L.lqcd_synchronize(ctx)
+        for f in (fx, fy, fz):
+            L.lqcd_field_destroy(f)
+    print(json.dumps({"kernel_only": args.kernel_only, "lattice": list(dims), "launches": args.steps + args.warmup}))
+    return 0
+
+
+def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
+    """FP64 CG vs mixed precision on the benchmark lattice, one Gaussian RHS."""
+    import gen
+    b = gen.gaussian_spinor(DIMS, 2003)[0]
+    bt = torch.from_numpy(b.view(np.float64).copy()).cuda()
+    res = {"lattice": list(DIMS), "kappa": KAPPA, "c_sw": CSW, "tol": 1e-10, "source": "Gaussian, seed 2003"}
+    xs = {}
+    for name, inner in (("fp64", L.LQCD_F64), ("mixed_f32", L.LQCD_F32), ("mixed_f16", L.LQCD_F16),
+                        ("mixed_bf16", L.LQCD_BF16)):
+        xt = torch.zeros_like(bt)
+        prm = L.solve_params(tol=1e-10, max_iter=40000, inner=inner, delta=0.1, recon=18, inner_recon=12,
+                             check_every=16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res[name] = {"seconds": wall, "iters": info.iters, "reliable_updates": info.reliable_updates,
+                     "mhat_applies": info.mhat_applies, "true_resid_gpu_fp64": info.true_resid[0],
+                     "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+        xs[name] = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
+    best = min((k for k in res if k.startswith("mixed") and res[k]["status"] == "ok"),
+               key=lambda k: res[k]["seconds"], default=None)
+    if best and res["fp64"]["status"] == "ok":
+        res["best_mixed"] = best
+        res["speedup_vs_fp64"] = res["fp64"]["seconds"] / res[best]["seconds"]
+    if want_oracle and oracle_AAi is not None:
+        import oracle
+        A, _ = oracle_AAi
+        for name, x in xs.items():
+            res[name]["true_resid_oracle"] = oracle.true_residual(DIMS, U, A, KAPPA, x, b)
+    return res
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    U, psi = make_inputs()
+    V = int(np.prod(DIMS))
+    Vh = V // 2
+    lat = L.Lattice(DIMS, stream=stream)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(KAPPA, CSW)
+    ctx = lat.ctx
+
+    def fields(prec):
+        P = L.PREC[prec]
+        fx = L.lqcd_field_create(ctx, P, L.LQCD_ODD, 1)
+        fy = L.lqcd_field_create(ctx, P, L.LQCD_EVEN, 1)
+        fz = L.lqcd_field_create(ctx, P, L.LQCD_ODD, 1)
+        L.lqcd_field_import(ctx, fx, psi)
+        return fx, fy, fz
+
+    fx, fy, fz = fields("f32")
+    mhat = lambda: L.lqcd_apply(ctx, L.LQCD_OP_MHAT, 12, fz, fx)
+    for _ in range(args.warmup):
+        mhat()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index(local_rank))
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = time_ms(torch, mhat, args.steps, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # per-kernel launch durations (same stream, events around K launches)
+    k2a_ms = time_ms(torch, lambda: L.lqcd_apply(ctx, L.LQCD_OP_K2A, 12, fy, fx), args.steps, stream)
+    k2b_ms = time_ms(torch, lambda: L.lqcd_apply_schur(ctx, 12, 0, fz, fx, fy), args.steps, stream)
+    clk = clocks.stop()
+    for f in (fx, fy, fz):
+        L.lqcd_field_destroy(f)
+
+    peak, peak_src = load_peaks()
+    gbs = world * Vh * mhat_bytes("f32", 12) / (ms * 1e-3) / 1e9
+    k2a_gbs = Vh * site_bytes("f32", 12, "k2a") / (k2a_ms * 1e-3) / 1e9
+    k2b_gbs = Vh * site_bytes("f32", 12, "k2b") / (k2b_ms * 1e-3) / 1e9
+    dom = "k2b" if k2b_ms >= k2a_ms else "k2a"
+    dom_ms, dom_gbs = (k2b_ms, k2b_gbs) if dom == "k2b" else (k2a_ms, k2a_gbs)
+    traffic = profiled_traffic(f"dslash_{dom}_f32_r12")
+
+    # precision / link-format variants of the full Mhat
+    variants = {}
+    vsteps = max(50, min(args.steps, 1000))
+    for prec, recon in (("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12)):
+        a, y, z = fields(prec)
+        f = lambda: L.lqcd_apply(ctx, L.LQCD_OP_MHAT, recon, z, a)
+        for _ in range(5):
+            f()
+        vms = time_ms(torch, f, vsteps if prec != "f64" else max(20, vsteps // 4), stream)
+        for g in (a, y, z):
+            L.lqcd_field_destroy(g)
+        b_site = mhat_bytes(prec, recon)
+        flops = (FLOPS["k2a"] + FLOPS["k2b"]) * Vh / (vms * 1e-3) / 1e12
+        variants[f"{prec}_r{recon}"] = {"ms": vms, "GBps": Vh * b_site / (vms * 1e-3) / 1e9,
+                                        "pct_hbm": 100 * Vh * b_site / (vms * 1e-3) / 1e9 / peak,
+                                        "TFLOPs": flops, "bytes_per_site": b_site}
+
+    # end to end through the C ABI with pinned host buffers
+    hin = torch.from_numpy(psi.view(np.float64).copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e2e_steps = 5
+    L.lqcd_dslash(ctx, hout, hin, 1, L.LQCD_OP_MHAT, L.LQCD_F32, 12)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.lqcd_dslash(ctx, hout, hin, 1, L.LQCD_OP_MHAT, L.LQCD_F32, 12)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = hin.numel() * 8
+    e2e = {"value": world * Vh * mhat_bytes("f32", 12) / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s * 1e3,
+           "path": "lqcd_dslash(op=MHAT, prec=F32, recon=12) on pinned host canonical FP64 arrays: H2D copy, "
+                   "pack, K2a, K2b, unpack, D2H copy"}
+
+    need_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    oracle_AAi = oracle_setup(U) if need_oracle else None
+    solve = None
+    if not args.no_solve:
+        solve = run_solves(L, torch, lat, U, rank, need_oracle, oracle_AAi)
+    cpu = None
+    if need_oracle:
+        rate, nsl, dt = oracle_slab_rate(U, oracle_AAi[0], oracle_AAi[1], psi)
+        cpu = {"value": rate * mhat_bytes("f32", 12) / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"oracle Mhat (FP64) on {nsl} of {DIMS[3]} time slices of the 32^3x64 workload "
+                         f"({dt:.1f} s); GB/s counts the workload's {mhat_bytes('f32', 12)} compulsory bytes "
+                         f"per output site", "sites_per_s": rate}
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "prec": "f32", "recon": 12, "nrhs": 1,
+                   "kappa": KAPPA, "c_sw": CSW, "eps": EPS, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each step streams ~1.2 GB (links 403 MB, clover 604 MB, spinors)"},
+        "pct_of_peak": 100.0 * gbs / world / peak,
+        "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s", "frac": dom_gbs / peak,
+                     "traffic": traffic, "kernel": f"dslash_kernel {dom} (FP32, 12-real)",
+                     "bytes_per_launch": Vh * site_bytes("f32", 12, dom), "ms_per_launch": dom_ms,
+                     "peak_source": peak_src},
+        "kernels": {"k2a_ms": k2a_ms, "k2a_GBps": k2a_gbs, "k2b_ms": k2b_ms, "k2b_GBps": k2b_gbs},
+        "variants": variants,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "solve": solve,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="lqcd", choices=["lqcd", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
+    ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--prec", default="f32")
+    ap.add_argument("--recon", type=int, default=12)
+    ap.add_argument("--nrhs", type=int, default=1)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    if args.kernel_only:
+        return kernel_only(args)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

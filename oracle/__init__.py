@@ -69,6 +69,8 @@ def _load():
                 "or_keep_parity": ([_ip, ctypes.c_int, _dp], None),
                 "or_apply_M": ([_ip, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int], None),
                 "or_apply_Mhat": ([_ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int], None),
+                "or_mhat_slab": ([_ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int,
+                                  _dp], None),
                 "or_prepare_source": ([_ip, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp], None),
                 "or_reconstruct": ([_ip, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp], None),
                 "or_norm2": ([ctypes.c_long, _dp], ctypes.c_double),
@@ -264,6 +266,20 @@ def apply_Mhat(dims, U, A, Ainv, kappa, psi, tbc=1, dagger=False):
     psi = keep_parity(dims, _field(psi, V), 1)
     out = np.empty(spinor_shape(dims), dtype=_c)
     _load().or_apply_Mhat(Ld, int(tbc), _p(U), _opt(A), _opt(Ainv), float(kappa), _p(psi), _p(out), int(dagger))
+    return out
+
+
+def mhat_slab(dims, U, A, Ainv, kappa, psi, t0, t1, out=None, tbc=1):
+    """Mhat psi_o on the odd sites of time slices t0 <= t < t1 only (a bounded
+    piece of the full application; the other sites of ``out`` are untouched)."""
+    Ld, V = _dims(dims)
+    U = _links(U, V)
+    psi = _field(psi, V)
+    if out is None:
+        out = np.zeros(spinor_shape(dims), dtype=_c)
+    if not (0 <= t0 < t1 <= dims[3]):
+        raise ValueError("need 0 <= t0 < t1 <= L3")
+    _load().or_mhat_slab(Ld, int(tbc), _p(U), _opt(A), _opt(Ainv), float(kappa), _p(psi), int(t0), int(t1), _p(out))
     return out
 
 

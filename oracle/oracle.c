@@ -434,6 +434,47 @@ void or_reconstruct(const int L[4], int tbc, const cplx *U, const cplx *Ainv, do
   free(u);
 }
 
+/* Mhat x at the odd sites with t0 <= t < t1 only (0 <= t0 < t1 <= L3),
+ * written into out at those sites; other sites of out are left untouched.
+ * The even-site intermediate y = A_ee^-1 D_eo x is formed only on the time
+ * slices t0-1 .. t1 that those sites reach.  A, Ainv: [V][12][12]. */
+void or_mhat_slab(const int L[4], int tbc, const cplx *U, const cplx *A, const cplx *Ainv, double kappa,
+                  const cplx *x, int t0, int t1, cplx *out) {
+  init_gammas();
+  long V = volume_of(L), slice = (long)L[0] * L[1] * L[2];
+  cplx *y = calloc(12 * V, sizeof(cplx));
+  int nt = t1 - t0 + 2 > L[3] ? L[3] : t1 - t0 + 2;
+  for (int k = 0; k < nt; k++) {
+    int t = ((t0 - 1 + k) % L[3] + L[3]) % L[3];
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < slice; i++) {
+      long s = t * slice + i;
+      if (parity_of(L, s) != 0) continue;
+      cplx d[4][3];
+      hop_site(L, tbc, U, x, s, 0, d);
+      if (Ainv)
+        site_matvec(Ainv + 144 * s, &d[0][0], y + 12 * s);
+      else
+        memcpy(y + 12 * s, &d[0][0], sizeof(cplx) * 12);
+    }
+  }
+  for (int t = t0; t < t1; t++) {
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < slice; i++) {
+      long s = t * slice + i;
+      if (parity_of(L, s) != 1) continue;
+      cplx d[4][3], ax[12];
+      hop_site(L, tbc, U, y, s, 0, d);
+      if (A)
+        site_matvec(A + 144 * s, x + 12 * s, ax);
+      else
+        memcpy(ax, x + 12 * s, sizeof(cplx) * 12);
+      for (int j = 0; j < 12; j++) out[12 * s + j] = ax[j] - kappa * kappa * (&d[0][0])[j];
+    }
+  }
+  free(y);
+}
+
 /* ------------------------------------------------------------------ */
 /* Vector algebra (sequential, fixed order)                             */
 /* ------------------------------------------------------------------ */

@@ -286,3 +286,16 @@ def test_cgls_interacting_clover():
     xo = oracle.keep_parity(dims, x, 1)
     bhat = oracle.prepare_source(dims, U, Ai, 0.125, b)
     assert rel(oracle.apply_Mhat(dims, U, A, Ai, 0.125, xo), bhat) < 1e-10
+
+
+def test_mhat_slab_matches_full(rough):
+    """The time-slab restriction of Mhat (used to bound CPU timings) equals the
+    full application on those slices, including the t wrap."""
+    dims, U, A, Ai = rough
+    psi = gen.gaussian_spinor(dims, 31)[0]
+    full = oracle.apply_Mhat(dims, U, A, Ai, KAPPA, psi)
+    for t0, t1 in ((0, 1), (2, 4), (5, 6), (0, dims[3])):
+        out = oracle.mhat_slab(dims, U, A, Ai, KAPPA, psi, t0, t1)
+        assert np.abs(out[t0:t1] - full[t0:t1]).max() < 1e-14 * np.abs(full).max()
+        rest = np.delete(out, range(t0, t1), axis=0)
+        assert rest.size == 0 or np.abs(rest).max() == 0
