@@ -14,7 +14,8 @@
 // FP32 arithmetic, x_lo in FP32, normalised so the inner residual starts at
 // norm 1; when it has fallen below delta (or reaches the target) the FP64
 // solution absorbs x_lo and the residual is recomputed with the FP64
-// operator; p is kept, rescaled into the new normalisation.
+// operator; the search direction p is kept, rescaled into the new
+// normalisation, and gamma = |Mhat^dag r|^2 recomputed from the new residual.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,7 +29,7 @@ namespace {
 
 struct SolveBufs {
   SolverScalars *sc = nullptr;  // device [nrhs]
-  double *fac = nullptr;        // device [nrhs] per-RHS factors
+  double *fac = nullptr;        // device [2 nrhs] per-RHS factors
   SolverScalars *h_sc = nullptr;  // pinned mirrors
   double *h_fac = nullptr;
   ~SolveBufs() {
@@ -247,20 +248,21 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
         continue;
       }
       done = false;
-      // keep p: gamma[cur] rescaled so that beta = (gamma'/gamma) (snew/sigma)
-      B.h_sc[k].gamma[cur] *= sigma[k] / snew;
-      B.h_fac[k] = 1.0 / snew;
+      // p (the next search direction) is kept, rescaled into the new
+      // normalisation r_lo = r64 / snew; gamma is recomputed from the new s
+      B.h_fac[k] = sigma[k] / snew;
       B.h_sc[k].rr = 1.0;
       sigma[k] = snew;
     }
     if (done) break;
+    // factors for p (sigma_old / sigma_new) in fac[0, n), for r (1 / sigma_new) in fac[n, 2n)
+    for (int k = 0; k < n; k++) B.h_fac[n + k] = B.h_sc[k].active != 0.0 ? 1.0 / sigma[k] : 0.0;
     LQ_TRY(write_scalars(c, B, n));
-    LQ_TRY(write_fac(c, B, n));
-    LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cur],
+    LQ_TRY(write_fac(c, B, 2 * n));
+    LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
+    LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
                    kScStride));
-    LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, cur, c->stream));
-    cur ^= 1;
     W.info->mhat_applies += 1;
   }
   W.info->iters = it;
@@ -299,9 +301,10 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
   const size_t nd = (size_t)n * c->V * 24;
 
   SolveBufs B;
-  if (cudaMalloc(&B.sc, sizeof(SolverScalars) * n) != cudaSuccess || cudaMalloc(&B.fac, sizeof(double) * n) != cudaSuccess ||
+  if (cudaMalloc(&B.sc, sizeof(SolverScalars) * n) != cudaSuccess ||
+      cudaMalloc(&B.fac, sizeof(double) * 2 * n) != cudaSuccess ||
       cudaMallocHost(&B.h_sc, sizeof(SolverScalars) * n) != cudaSuccess ||
-      cudaMallocHost(&B.h_fac, sizeof(double) * n) != cudaSuccess) {
+      cudaMallocHost(&B.h_fac, sizeof(double) * 2 * n) != cudaSuccess) {
     cudaGetLastError();
     return set_error(LQCD_ERR_OOM, "cannot allocate solver scalars");
   }
