@@ -209,6 +209,24 @@ typedef struct {
 lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device, const lqcd_solve_params *params,
                        lqcd_solve_info *info);
 
+/* ---- allocation-free reduction ---------------------------------------- */
+
+/* The paper has no counterpart of this call.  result[k] = sum_i x[k*n + i]^2
+ * for k < nrhs: the FP64 fixed-order sum of squares of nrhs device vectors
+ * of n doubles each (for example canonical spinors, n = 24 V), written to
+ * the device array `result` on `cuda_stream` (NULL: default stream); the
+ * call does not wait for it.  It allocates nothing, for callers that cannot
+ * call cudaMalloc (device memory owned by another allocator, or
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the
+ * device): its scratch -- at most 1024 x 64 partial sums (512 KiB) and a
+ * counter -- is a static array of the library that every GPU loading it
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address, so make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams, or from several threads) race and give wrong results.
+ * nrhs > 64, n < 1 or n > 2^40 give LQCD_ERR_ARG; no context is needed. */
+lqcd_status lqcd_norm2_noalloc(const double *x, long n, int nrhs, double *result, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 if not os.path.exists(_build.LIB):
     raise ImportError(
         f"{_build.LIB} is missing: build the CUDA library first "
-        "(python -c 'import __graft_entry__ as g; g.build()' or python -m paper_2001_05706_gb300.build)")
+        "(python -c 'import __graft_entry__ as g; g.build()' or python paper_2001_05706_gb300/build.py)")
 _lib = ctypes.CDLL(_build.LIB)
 
 # enums (include/lqcd.h)
@@ -74,6 +74,7 @@ _sig = {
     "lqcd_apply_schur": [_vp, _ip, _ip, _vp, _vp, _vp],
     "lqcd_field_norm2": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "lqcd_solve": [_vp, _vp, _vp, _ip, ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
+    "lqcd_norm2_noalloc": [_vp, ctypes.c_long, _ip, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -207,6 +208,16 @@ def lqcd_solve(ctx, x, b, params: lqcd_solve_params, raise_on_noconv=True):
     if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
         raise LqcdError(st, lqcd_last_error())
     return st, info
+
+
+def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):
+    """result[k] = sum of squares of x[k*n:(k+1)*n] (device tensors of float64);
+    allocates nothing (static library scratch), asynchronous on `stream`."""
+    px, dx = _buf(x)
+    pr, dr = _buf(result)
+    if not (dx and dr):
+        raise ValueError("x and result must be CUDA tensors")
+    _check(_lib.lqcd_norm2_noalloc(px, int(n), int(nrhs), pr, _stream_ptr(stream)))
 
 
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,

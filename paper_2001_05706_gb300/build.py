@@ -1,7 +1,7 @@
 """Build liblqcd.so from csrc/*.cu for GB300 (sm_103a) with nvcc.
 
 Translation units compile in parallel; the shared library is written beside
-this file (in-tree).  Usage:  python -m paper_2001_05706_gb300.build
+this file (in-tree).  Usage:  python paper_2001_05706_gb300/build.py
 """
 from __future__ import annotations
 
