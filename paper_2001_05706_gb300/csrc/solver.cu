@@ -15,9 +15,12 @@
 // norm 1; when it has fallen below delta (or reaches the target) the FP64
 // solution absorbs x_lo and the residual is recomputed with the FP64
 // operator; the search direction p is kept, rescaled into the new
-// normalisation, and gamma = |Mhat^dag r|^2 recomputed from the new residual.
+// normalisation, and gamma = |Mhat^dag r|^2 recomputed from the new residual;
+// an update that fails to reduce the residual restarts CG from p = s.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -29,7 +32,7 @@ namespace {
 
 struct SolveBufs {
   SolverScalars *sc = nullptr;  // device [nrhs]
-  double *fac = nullptr;        // device [2 nrhs] per-RHS factors
+  double *fac = nullptr;        // device [3 nrhs] per-RHS factors
   SolverScalars *h_sc = nullptr;  // pinned mirrors
   double *h_fac = nullptr;
   ~SolveBufs() {
@@ -41,6 +44,8 @@ struct SolveBufs {
 };
 
 const FieldRef kNone{nullptr, nullptr, 0};
+// LQCD_SOLVER_TRACE=1 prints one line per reliable update to stderr
+const bool kTrace = std::getenv("LQCD_SOLVER_TRACE") != nullptr;
 constexpr int kScStride = (int)(sizeof(SolverScalars) / sizeof(double));
 
 lqcd_status read_scalars(lqcd_ctx *c, SolveBufs &B, int nrhs) {
@@ -164,9 +169,13 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
   LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 35, &xlo));
   LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 23, &ye64));
   LQ_TRY(ensure_partials(c, n));
-  std::vector<double> target(n), sigma(n);
+  std::vector<double> target(n), sigma(n), best_rr(n, 1.0);
+  std::vector<int> stall(n, 0);
   for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
   const double delta2 = W.delta * W.delta;
+  // an inner residual that has not halved over kStallChecks checks is
+  // stagnating at the precision floor of the storage type: force an update
+  constexpr int kStallChecks = 3;
   const size_t xlo_bytes = (size_t)xlo->rhs_words() * 16 * n;
 
   // r64 = bhat - Mhat64 x64 -> sigma
@@ -213,16 +222,23 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
       W.info->mhat_applies += 2;
     }
     LQ_TRY(read_scalars(c, B, n));
-    // trigger: every active RHS dropped by delta, or one reached its target
-    bool all_dropped = true, any_target = false;
+    // trigger: every active RHS dropped by delta, or one reached its target,
+    // or one stagnates
+    bool all_dropped = true, any_target = false, any_stall = false;
     for (int k = 0; k < n; k++) {
       if (B.h_sc[k].active == 0.0) continue;
       const double rr = B.h_sc[k].rr;
       if (!(rr == rr)) return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
       if (rr > delta2) all_dropped = false;
       if (sigma[k] * std::sqrt(rr) <= target[k]) any_target = true;
+      if (rr < 0.25 * best_rr[k]) {
+        best_rr[k] = rr;
+        stall[k] = 0;
+      } else if (++stall[k] >= kStallChecks) {
+        any_stall = true;
+      }
     }
-    if (!(all_dropped || any_target || it >= W.max_iter)) continue;
+    if (!(all_dropped || any_target || any_stall || it >= W.max_iter)) continue;
 
     // ---- reliable update: x64 += sigma x_lo ; r64 = bhat - Mhat64 x64
     for (int k = 0; k < n; k++) B.h_fac[k] = B.h_sc[k].active != 0.0 ? sigma[k] : 0.0;
@@ -241,7 +257,11 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
         continue;
       }
       const double snew = std::sqrt(B.h_sc[k].aux);
-      if (!(snew == snew)) return set_error(LQCD_ERR_NOCONV, "FP64 residual of RHS %d is NaN", k);
+      if (kTrace)
+        std::fprintf(stderr, "lqcd: update %d it %d rhs %d inner |r| %.3e  FP64 |r| %.6e -> %.6e (target %.3e)\n",
+                     W.info->reliable_updates, it, k, std::sqrt(B.h_sc[k].rr), sigma[k], snew, target[k]);
+      if (!(snew == snew) || std::isinf(snew))
+        return set_error(LQCD_ERR_NOCONV, "FP64 residual of RHS %d is not finite", k);
       if (snew <= target[k]) {
         B.h_sc[k].active = 0.0;
         B.h_fac[k] = 0.0;
@@ -249,20 +269,27 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
       }
       done = false;
       // p (the next search direction) is kept, rescaled into the new
-      // normalisation r_lo = r64 / snew; gamma is recomputed from the new s
-      B.h_fac[k] = sigma[k] / snew;
+      // normalisation r_lo = r64 / snew, unless this update failed to reduce
+      // the residual: then CG restarts from p = s (low-precision noise has
+      // spoilt the conjugacy of p)
+      const bool restart = snew >= sigma[k] || stall[k] >= kStallChecks;
+      stall[k] = 0;
+      best_rr[k] = 1.0;
+      B.h_fac[k] = restart ? 0.0 : sigma[k] / snew;
+      B.h_fac[2 * n + k] = restart ? 1.0 : 0.0;
       B.h_sc[k].rr = 1.0;
       sigma[k] = snew;
     }
     if (done) break;
-    // factors for p (sigma_old / sigma_new) in fac[0, n), for r (1 / sigma_new) in fac[n, 2n)
+    // factors: p *= fac[0, n); r = r64 * fac[n, 2n); p += fac[2n, 3n) s
     for (int k = 0; k < n; k++) B.h_fac[n + k] = B.h_sc[k].active != 0.0 ? 1.0 / sigma[k] : 0.0;
     LQ_TRY(write_scalars(c, B, n));
-    LQ_TRY(write_fac(c, B, 2 * n));
+    LQ_TRY(write_fac(c, B, 3 * n));
     LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
     LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
     LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
                    kScStride));
+    LQ_CU(blas_axpy(L, L, c->Vh, n, p->mut(1), s->ref(1), B.fac + 2 * n, c->stream));
     W.info->mhat_applies += 1;
   }
   W.info->iters = it;
@@ -302,9 +329,9 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
 
   SolveBufs B;
   if (cudaMalloc(&B.sc, sizeof(SolverScalars) * n) != cudaSuccess ||
-      cudaMalloc(&B.fac, sizeof(double) * 2 * n) != cudaSuccess ||
+      cudaMalloc(&B.fac, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMallocHost(&B.h_sc, sizeof(SolverScalars) * n) != cudaSuccess ||
-      cudaMallocHost(&B.h_fac, sizeof(double) * 2 * n) != cudaSuccess) {
+      cudaMallocHost(&B.h_fac, sizeof(double) * 3 * n) != cudaSuccess) {
     cudaGetLastError();
     return set_error(LQCD_ERR_OOM, "cannot allocate solver scalars");
   }
