@@ -209,6 +209,65 @@ typedef struct {
 lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device, const lqcd_solve_params *params,
                        lqcd_solve_info *info);
 
+/* ---- overlap operator ---------------------------------------------------- */
+
+/* The overlap operator of GWU-code's inverter (abstract; Sec. 3; the overlap
+ * eigensystem run of Sec. 4), in its standard form
+ *   D_ov(m) = (1 - m/(2 rho)) rho (1 + g5 eps(H_W)) + m,   H_W = g5 D_W(-rho),
+ *   D_W(m') = 4 + m' - D/2 (plain Wilson kernel, no clover, full lattice),
+ * with the sign function eps(H_W) computed as
+ *   eps v = sum_i sign(lam_i) v_i <v_i, v> + H_W P(H_W^2) (v - sum_i v_i <v_i, v>)
+ * from the n_low eigenpairs (lam_i, v_i) of H_W of smallest |lam| and the
+ * Chebyshev interpolant P(y) of 1/sqrt(y) on [a, b], a = lam_{n_low+1}^2
+ * (the largest unprojected-range lower bound found), b = (4 - rho + 4)^2. */
+typedef struct {
+  double rho;        /* kernel mass parameter, 0 < rho < 2 (1.5 in the workloads)        */
+  double mass;       /* overlap quark mass m                                             */
+  int n_low;         /* low modes of H_W treated exactly, 0..64                          */
+  int max_degree;    /* cap on the Chebyshev degree                                      */
+  double sign_tol;   /* target sup |x P(x^2) - sign x| on [sqrt a, sqrt b]               */
+  double eig_tol;    /* target ||H_W v - lam v|| of every low mode (absolute, |v| = 1)   */
+  int max_filter;    /* cap on subspace-iteration sweeps of the low-mode solver          */
+  unsigned long long seed; /* seed of the random start block of the low-mode solver     */
+} lqcd_overlap_params;
+
+typedef struct {
+  int n_low;              /* low modes found                                           */
+  double lambda[64];      /* their eigenvalues of H_W, sorted by |lambda|              */
+  double resid[64];       /* ||H_W v - lambda v|| of each                              */
+  double a, b;            /* interval of the Chebyshev interpolant (in H_W^2)          */
+  int degree;             /* its degree                                                */
+  double sign_error;      /* its sup error on [sqrt a, sqrt b]                         */
+  int sweeps;             /* subspace-iteration sweeps used                            */
+  double seconds;         /* wall time of the set-up                                   */
+} lqcd_overlap_info;
+
+typedef enum {
+  LQCD_OV_APPLY = 0,      /* out = D_ov(m) in                                          */
+  LQCD_OV_APPLY_DAG = 1,  /* out = D_ov(m)^dag in                                      */
+  LQCD_OV_SIGN = 2,       /* out = eps(H_W) in                                         */
+  LQCD_OV_SOLVE = 3       /* out = D_ov(m)^-1 in by CG on the normal equations         */
+} lqcd_overlap_op;
+
+/* Compute the low modes of H_W (FP64 block subspace iteration on H_W^2 with
+ * Chebyshev filtering and Rayleigh-Ritz in H_W) and the Chebyshev
+ * coefficients for the sign function, and keep them in the context.  Needs
+ * the gauge field.  Blocks.  LQCD_ERR_NOCONV if the low modes do not reach
+ * eig_tol within max_filter sweeps (info is filled either way). */
+lqcd_status lqcd_overlap_setup(lqcd_ctx *ctx, const lqcd_overlap_params *params, lqcd_overlap_info *info);
+
+/* Copy the n_low low-mode vectors (canonical, n_low fields back to back,
+ * host or device) out of the context, in the order of info->lambda. */
+lqcd_status lqcd_overlap_lowmodes(lqcd_ctx *ctx, double *vecs, int on_device);
+
+/* Apply or invert the overlap operator set up by lqcd_overlap_setup on nrhs
+ * canonical full-lattice spinors (host or device), in FP64.  For
+ * LQCD_OV_SOLVE, cg->tol is the target ||b - D_ov x|| / ||b|| per right-hand
+ * side and cg->max_iter caps the iterations; info (may be NULL) receives the
+ * iteration count and the final residuals.  Blocks. */
+lqcd_status lqcd_overlap(lqcd_ctx *ctx, double *out, const double *in, int nrhs, int on_device, lqcd_overlap_op op,
+                         const lqcd_solve_params *cg, lqcd_solve_info *info);
+
 /* ---- allocation-free reduction ---------------------------------------- */
 
 /* The paper has no counterpart of this call.  result[k] = sum_i x[k*n + i]^2

@@ -49,6 +49,21 @@ class lqcd_solve_params(ctypes.Structure):
                 ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int)]
 
 
+class lqcd_overlap_params(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("mass", ctypes.c_double), ("n_low", ctypes.c_int),
+                ("max_degree", ctypes.c_int), ("sign_tol", ctypes.c_double), ("eig_tol", ctypes.c_double),
+                ("max_filter", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+class lqcd_overlap_info(ctypes.Structure):
+    _fields_ = [("n_low", ctypes.c_int), ("lambda_", ctypes.c_double * 64), ("resid", ctypes.c_double * 64),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("degree", ctypes.c_int),
+                ("sign_error", ctypes.c_double), ("sweeps", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
+LQCD_OV_APPLY, LQCD_OV_APPLY_DAG, LQCD_OV_SIGN, LQCD_OV_SOLVE = 0, 1, 2, 3
+
+
 class lqcd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("nrhs", ctypes.c_int),
                 ("true_resid", ctypes.c_double * 64), ("seconds", ctypes.c_double),
@@ -75,6 +90,10 @@ _sig = {
     "lqcd_field_norm2": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "lqcd_solve": [_vp, _vp, _vp, _ip, ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_norm2_noalloc": [_vp, ctypes.c_long, _ip, _vp, _vp],
+    "lqcd_overlap_setup": [_vp, ctypes.POINTER(lqcd_overlap_params), ctypes.POINTER(lqcd_overlap_info)],
+    "lqcd_overlap_lowmodes": [_vp, _vp, _ip],
+    "lqcd_overlap": [_vp, _vp, _vp, _ip, _ip, _ip, ctypes.POINTER(lqcd_solve_params),
+                     ctypes.POINTER(lqcd_solve_info)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -218,6 +237,37 @@ def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):
     if not (dx and dr):
         raise ValueError("x and result must be CUDA tensors")
     _check(_lib.lqcd_norm2_noalloc(px, int(n), int(nrhs), pr, _stream_ptr(stream)))
+
+
+def overlap_params(rho=1.5, mass=0.0, n_low=20, max_degree=4000, sign_tol=1e-10, eig_tol=1e-11, max_filter=200,
+                   seed=7):
+    return lqcd_overlap_params(rho, mass, n_low, max_degree, sign_tol, eig_tol, max_filter, seed)
+
+
+def lqcd_overlap_setup(ctx, params, raise_on_noconv=True):
+    info = lqcd_overlap_info()
+    st = _lib.lqcd_overlap_setup(ctx, ctypes.byref(params), ctypes.byref(info))
+    if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
+        raise LqcdError(st, lqcd_last_error())
+    return st, info
+
+
+def lqcd_overlap_lowmodes(ctx, vecs):
+    p, dev = _buf(vecs)
+    _check(_lib.lqcd_overlap_lowmodes(ctx, p, dev))
+
+
+def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):
+    po, do = _buf(out)
+    pi, di = _buf(inp)
+    if do != di:
+        raise ValueError("out and in must both be host or both be device buffers")
+    info = lqcd_solve_info()
+    cgp = ctypes.byref(cg) if cg is not None else None
+    st = _lib.lqcd_overlap(ctx, po, pi, int(nrhs), do, int(op), cgp, ctypes.byref(info))
+    if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
+        raise LqcdError(st, lqcd_last_error())
+    return st, info
 
 
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,

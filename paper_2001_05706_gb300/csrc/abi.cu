@@ -108,12 +108,12 @@ lqcd_status lqcd_create(lqcd_ctx **ctx, const int dims[4], int t_antiperiodic, v
   g.tbc = c->tbc;
   lqcd_status s = LQCD_OK;
   if ((s = alloc_dev((void **)&c->counter, 64 * sizeof(unsigned), "reduction counter")) != LQCD_OK ||
-      (s = alloc_dev((void **)&c->results, 256 * sizeof(double), "reduction results")) != LQCD_OK) {
+      (s = alloc_dev((void **)&c->results, 1024 * sizeof(double), "reduction results")) != LQCD_OK) {
     lqcd_destroy(c);
     return s;
   }
   if (cudaMemsetAsync(c->counter, 0, 64 * sizeof(unsigned), c->stream) != cudaSuccess ||
-      cudaMallocHost(&c->h_results, 256 * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&c->h_results, 1024 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     lqcd_destroy(c);
     return set_error(LQCD_ERR_CUDA, "context set-up failed");
@@ -136,6 +136,7 @@ lqcd_status lqcd_destroy(lqcd_ctx *c) {
     if (kv.second->scale_alloc) cudaFree(kv.second->scale_alloc);
     delete kv.second;
   }
+  overlap_free(c);
   if (c->U64) cudaFree(c->U64);
   if (c->partials) cudaFree(c->partials);
   if (c->counter) cudaFree(c->counter);
@@ -168,6 +169,7 @@ lqcd_status lqcd_load_gauge(lqcd_ctx *c, const double *U, int on_device) {
   if (!c->U64) LQ_TRY(alloc_dev((void **)&c->U64, n * sizeof(double), "gauge field"));
   free_links(c);
   free_clover(c);
+  overlap_free(c);
   c->have_gauge = false;
   LQ_CU(cudaMemcpyAsync(c->U64, U, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         c->stream));

@@ -76,6 +76,11 @@ struct lqcd_field {
   bool has(int p) const { return subset == LQCD_FULL || (int)subset == p; }
 };
 
+namespace lqcd {
+struct OverlapState;
+void overlap_free(lqcd_ctx *c);
+}  // namespace lqcd
+
 struct CloverStore {
   void *A[2] = {nullptr, nullptr};
   void *Ainv[2] = {nullptr, nullptr};
@@ -103,13 +108,15 @@ struct lqcd_ctx {
   double *partials = nullptr;
   size_t partials_n = 0;
   unsigned *counter = nullptr;
-  double *results = nullptr;  // 256 doubles
+  double *results = nullptr;  // 1024 doubles: [0,256) norms, [256,1024) small per-RHS coefficient arrays
   double *h_results = nullptr;  // pinned mirror
   // canonical staging for host <-> device transfers
   double *canon[2] = {nullptr, nullptr};
   size_t canon_n[2] = {0, 0};
   // cached intermediate fields (key: 10*prec + nrhs*1000 + slot)
   std::map<long, lqcd_field *> temps;
+  // overlap operator state (low modes, Chebyshev coefficients), overlap.cu
+  lqcd::OverlapState *ov = nullptr;
 };
 
 // ---- errors (abi.cu)

@@ -1,0 +1,854 @@
+// Overlap operator: low modes of H_W, the polynomial sign function and the
+// overlap operator and its CG inverse (GWU-code's overlap inverter, abstract
+// and Secs. 3-4 of the paper; standard definitions, see include/lqcd.h).
+//
+//  * Low modes: block subspace iteration on H_W^2 in FP64.  Each sweep
+//    applies a Chebyshev filter of H_W^2 that damps the interval
+//    [mu_max, b] (mu_max the largest Ritz value of H_W^2 in the block),
+//    orthonormalises the block by Cholesky QR (twice), and does a
+//    Rayleigh-Ritz step with H_W^2; once the wanted vectors have converged,
+//    a Rayleigh-Ritz step with H_W in their span fixes the signs of the
+//    eigenvalues.  The block inner products and rotations are plain GEMMs
+//    (cuBLAS ZGEMM); the m x m Hermitian eigenproblem (m <= 96) is solved on
+//    the host by cyclic Jacobi rotations.
+//  * Sign function: exact low modes plus H_W P(H_W^2) on their complement,
+//    P the Chebyshev interpolant of 1/sqrt(y) on [a, b], evaluated by the
+//    Clenshaw recurrence b_k = c_k w + 2 T b_{k+1} - b_{k+2},
+//    T = (2 H_W^2 - a - b)/(b - a); each step is two H_W applications (the
+//    dslash kernel, all right-hand sides per launch) and one fused
+//    three-term kernel.
+//  * D_ov(m) = f (1 + g5 eps) + m with f = (1 - m/(2 rho)) rho, and CG on its
+//    normal equations for the inverse.
+#include <cublas_v2.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace lqcd {
+
+using zc = std::complex<double>;
+
+struct OverlapState {
+  bool ready = false;
+  lqcd_overlap_params prm{};
+  int nlow = 0;
+  std::vector<double> lam;
+  lqcd_field *vecs = nullptr;  // FULL FP64, nrhs = nlow
+  std::vector<double> coef;
+  double a = 0, b = 0;
+  int degree = 0;
+  cublasHandle_t blas = nullptr;
+  double2 *dsmall = nullptr;  // device scratch for small matrices
+  size_t dsmall_n = 0;
+};
+
+void overlap_free(lqcd_ctx *c) {
+  OverlapState *s = c->ov;
+  if (!s) return;
+  if (s->vecs) lqcd_field_destroy(s->vecs);
+  if (s->blas) cublasDestroy(s->blas);
+  if (s->dsmall) cudaFree(s->dsmall);
+  delete s;
+  c->ov = nullptr;
+}
+
+namespace {
+
+constexpr int kT = 256;
+
+// ---- kernels on FULL FP64 fields: grid (blocks over words*Vh, nrhs, parity) --
+
+// out = cw w + t (s2 hh + s0 b1) - b2   (w, b2 may be null: zero)
+__global__ void clenshaw_kernel(long n, double2 *o0, double2 *o1, const double2 *w0, const double2 *w1,
+                                const double2 *h0, const double2 *h1, const double2 *a0, const double2 *a1,
+                                const double2 *c0, const double2 *c1, double cw, double t, double s2, double s0) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long off = (long)blockIdx.y * n + i;
+  if (i >= n) return;
+  const int p = blockIdx.z;
+  double2 *o = p ? o1 : o0;
+  const double2 *w = p ? w1 : w0, *h = p ? h1 : h0, *b1 = p ? a1 : a0, *b2 = p ? c1 : c0;
+  const double2 hv = h[off], bv = b1[off];
+  double2 r = make_double2(t * (s2 * hv.x + s0 * bv.x), t * (s2 * hv.y + s0 * bv.y));
+  if (w) {
+    const double2 wv = w[off];
+    r.x += cw * wv.x;
+    r.y += cw * wv.y;
+  }
+  if (b2) {
+    const double2 cv = b2[off];
+    r.x -= cv.x;
+    r.y -= cv.y;
+  }
+  o[off] = r;
+}
+
+// out = a in + b (g5 e or e); FP64 word w of a site holds spin w / 3
+__global__ void ov_combine_kernel(long Vh, long n, double2 *o0, double2 *o1, const double2 *i0, const double2 *i1,
+                                  const double2 *e0, const double2 *e1, double a, double b, int g5) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long off = (long)blockIdx.y * n + i;
+  const int p = blockIdx.z;
+  const double2 x = (p ? i1 : i0)[off], e = (p ? e1 : e0)[off];
+  const int spin = (int)(i / Vh) / 3;
+  const double g = (g5 && spin >= 2) ? -b : b;
+  (p ? o1 : o0)[off] = make_double2(a * x.x + g * e.x, a * x.y + g * e.y);
+}
+
+// Gaussian fill of raw doubles: SplitMix64 (Steele et al. 2014) counters + Box-Muller
+__device__ __forceinline__ unsigned long long sm64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__global__ void gauss_fill_kernel(double *x, long n, unsigned long long seed) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * k >= n) return;
+  const unsigned long long s = sm64(seed);
+  const double u1 = ((double)((sm64(s ^ (2 * k + 1) * 0xD1B54A32D192ED03ULL) >> 11) + 1)) * 0x1.0p-53;
+  const double u2 = ((double)((sm64(s ^ (2 * k + 2) * 0xD1B54A32D192ED03ULL) >> 11) + 1)) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  x[2 * k] = r * cs;
+  if (2 * k + 1 < n) x[2 * k + 1] = r * sn;
+}
+
+// per-RHS ||x_k + c_k y_k||^2 over both parities (c on the device)
+__global__ void axpy_norm_kernel(long n, const double2 *x0, const double2 *x1, const double2 *y0, const double2 *y1,
+                                 const double *c, double *partials, unsigned *counter, double *result, int nrhs) {
+  const int k = blockIdx.y;
+  const double ck = c[k];
+  double v[1] = {0.0};
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += (long)gridDim.x * blockDim.x) {
+    const int p = i >= n;
+    const long off = (long)k * n + (p ? i - n : i);
+    const double2 a = (p ? x1 : x0)[off], b = (p ? y1 : y0)[off];
+    const double re = a.x + ck * b.x, im = a.y + ck * b.y;
+    v[0] += re * re + im * im;
+  }
+  grid_reduce<1>(v, partials, counter, result, k, nrhs, 1);
+}
+
+__global__ void scale_rows_kernel(double2 *m, int rows, int cols, const double *s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const double f = s[i % rows];
+  m[i] = make_double2(f * m[i].x, f * m[i].y);
+}
+
+// ---- host helpers ------------------------------------------------------------
+
+lqcd_status blas_ok(cublasStatus_t s, const char *what) {
+  return s == CUBLAS_STATUS_SUCCESS ? LQCD_OK : set_error(LQCD_ERR_CUDA, "%s failed (cuBLAS status %d)", what, (int)s);
+}
+
+lqcd_status ensure_state(lqcd_ctx *c) {
+  if (!c->ov) c->ov = new OverlapState();
+  OverlapState &s = *c->ov;
+  if (!s.blas) {
+    if (cublasCreate(&s.blas) != CUBLAS_STATUS_SUCCESS) return set_error(LQCD_ERR_CUDA, "cublasCreate failed");
+  }
+  if (cublasSetStream(s.blas, c->stream) != CUBLAS_STATUS_SUCCESS)
+    return set_error(LQCD_ERR_CUDA, "cublasSetStream failed");
+  return LQCD_OK;
+}
+
+lqcd_status small_scratch(lqcd_ctx *c, size_t n, double2 **p) {
+  OverlapState &s = *c->ov;
+  if (s.dsmall_n < n) {
+    if (s.dsmall) {
+      LQ_CU(cudaStreamSynchronize(c->stream));
+      cudaFree(s.dsmall);
+      s.dsmall = nullptr;
+    }
+    LQ_CU(cudaMalloc(&s.dsmall, n * sizeof(double2)));
+    s.dsmall_n = n;
+  }
+  *p = s.dsmall;
+  return LQCD_OK;
+}
+
+long cwords(const lqcd_field *f) { return 12L * f->Vh; }  // complex numbers per RHS per parity (FP64)
+
+double2 *col(const lqcd_field *f, int p, int k) {
+  return reinterpret_cast<double2 *>(f->data[p]) + (long)k * cwords(f);
+}
+
+// C(p x q) = X^H Y over both parities (X: first p RHS of fx, Y: first q RHS of fy), C on the device
+lqcd_status gram(lqcd_ctx *c, const lqcd_field *fx, int p, const lqcd_field *fy, int q, double2 *C) {
+  OverlapState &s = *c->ov;
+  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+  const int N = (int)cwords(fx);
+  for (int par = 0; par < 2; par++)
+    LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one,
+                               reinterpret_cast<const cuDoubleComplex *>(col(fx, par, 0)), N,
+                               reinterpret_cast<const cuDoubleComplex *>(col(fy, par, 0)), N, par ? &one : &zero,
+                               reinterpret_cast<cuDoubleComplex *>(C), p),
+                   "ZGEMM (Gram)"));
+  return LQCD_OK;
+}
+
+// Z = alpha X M + beta Z (X: N x p block of fx, M: p x q on the device, Z: N x q block of fz)
+lqcd_status rotate(lqcd_ctx *c, const lqcd_field *fx, int p, const double2 *M, int q, lqcd_field *fz, zc alpha,
+                   zc beta) {
+  OverlapState &s = *c->ov;
+  const cuDoubleComplex al = make_cuDoubleComplex(alpha.real(), alpha.imag());
+  const cuDoubleComplex be = make_cuDoubleComplex(beta.real(), beta.imag());
+  const int N = (int)cwords(fx);
+  for (int par = 0; par < 2; par++)
+    LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al,
+                               reinterpret_cast<const cuDoubleComplex *>(col(fx, par, 0)), N,
+                               reinterpret_cast<const cuDoubleComplex *>(M), p, &be,
+                               reinterpret_cast<cuDoubleComplex *>(col(fz, par, 0)), N),
+                   "ZGEMM (rotation)"));
+  return LQCD_OK;
+}
+
+// Cyclic Jacobi eigensolver for a Hermitian m x m matrix (column-major).
+// On return A is diagonal (eigenvalues on the diagonal) and V holds the
+// eigenvectors as columns: A_in = V diag V^H.
+void jacobi_eigh(int m, std::vector<zc> &A, std::vector<zc> &V, std::vector<double> &w) {
+  auto at = [&](int i, int j) -> zc & { return A[i + (size_t)m * j]; };
+  V.assign((size_t)m * m, zc(0, 0));
+  for (int i = 0; i < m; i++) V[i + (size_t)m * i] = 1.0;
+  for (int sweep = 0; sweep < 100; sweep++) {
+    double off = 0, dia = 0;
+    for (int j = 0; j < m; j++)
+      for (int i = 0; i < m; i++) (i == j ? dia : off) += std::norm(at(i, j));
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < m - 1; p++)
+      for (int q = p + 1; q < m; q++) {
+        const zc apq = at(p, q);
+        const double g = std::abs(apq);
+        if (g < 1e-300) continue;
+        const zc e = apq / g;  // phase: D = diag(1 at p, conj(e) at q) makes a_pq real
+        const double app = at(p, p).real(), aqq = at(q, q).real();
+        const double tau = (aqq - app) / (2 * g);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1 + tau * tau));
+        const double cs = 1 / std::sqrt(1 + t * t), sn = t * cs;
+        // unitary U on columns (p, q): U = D R, R = [[cs, sn], [-sn, cs]]
+        const zc u_pp = cs, u_pq = sn, u_qp = -sn * std::conj(e), u_qq = cs * std::conj(e);
+        for (int k = 0; k < m; k++) {  // A <- A U
+          const zc akp = at(k, p), akq = at(k, q);
+          at(k, p) = akp * u_pp + akq * u_qp;
+          at(k, q) = akp * u_pq + akq * u_qq;
+        }
+        for (int k = 0; k < m; k++) {  // A <- U^H A
+          const zc apk = at(p, k), aqk = at(q, k);
+          at(p, k) = std::conj(u_pp) * apk + std::conj(u_qp) * aqk;
+          at(q, k) = std::conj(u_pq) * apk + std::conj(u_qq) * aqk;
+        }
+        for (int k = 0; k < m; k++) {  // V <- V U
+          const zc vkp = V[k + (size_t)m * p], vkq = V[k + (size_t)m * q];
+          V[k + (size_t)m * p] = vkp * u_pp + vkq * u_qp;
+          V[k + (size_t)m * q] = vkp * u_pq + vkq * u_qq;
+        }
+        at(p, q) = at(q, p) = 0.0;
+      }
+  }
+  w.resize(m);
+  for (int i = 0; i < m; i++) w[i] = at(i, i).real();
+}
+
+// Cholesky G = R^H R of a Hermitian positive definite m x m matrix and the
+// inverse of the upper-triangular R (column-major); false if not positive.
+bool chol_inv(int m, const std::vector<zc> &G, std::vector<zc> &Rinv) {
+  std::vector<zc> R((size_t)m * m, 0.0);
+  auto g = [&](int i, int j) { return G[i + (size_t)m * j]; };
+  auto r = [&](int i, int j) -> zc & { return R[i + (size_t)m * j]; };
+  for (int j = 0; j < m; j++) {
+    double d = g(j, j).real();
+    for (int k = 0; k < j; k++) d -= std::norm(r(k, j));
+    if (!(d > 0)) return false;
+    r(j, j) = std::sqrt(d);
+    for (int i = j + 1; i < m; i++) {
+      zc t = g(j, i);
+      for (int k = 0; k < j; k++) t -= std::conj(r(k, j)) * r(k, i);
+      r(j, i) = t / r(j, j).real();
+    }
+  }
+  Rinv.assign((size_t)m * m, 0.0);
+  for (int j = 0; j < m; j++) {  // solve R x = e_j by back substitution
+    for (int i = j; i >= 0; i--) {
+      zc t = (i == j) ? zc(1.0) : zc(0.0);
+      for (int k = i + 1; k <= j; k++) t -= R[i + (size_t)m * k] * Rinv[k + (size_t)m * j];
+      Rinv[i + (size_t)m * j] = t / R[i + (size_t)m * i].real();
+    }
+  }
+  return true;
+}
+
+lqcd_status to_host(lqcd_ctx *c, const double2 *d, size_t n, std::vector<zc> &h) {
+  h.resize(n);
+  LQ_CU(cudaMemcpyAsync(h.data(), d, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+lqcd_status to_dev(lqcd_ctx *c, const std::vector<zc> &h, double2 *d) {
+  LQ_CU(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+lqcd_status new_full(lqcd_ctx *c, int nrhs, lqcd_field **f) { return lqcd_field_create(c, LQCD_F64, LQCD_FULL, nrhs, f); }
+
+struct FieldGuard {
+  std::vector<lqcd_field *> f;
+  ~FieldGuard() {
+    for (auto *x : f)
+      if (x) lqcd_field_destroy(x);
+  }
+};
+
+lqcd_status hw(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in) {
+  MutField o[2] = {out->mut(0), out->mut(1)};
+  FieldRef x[2] = {in->ref(0), in->ref(1)};
+  return op_hw(c, LQCD_F64, 18, nrhs, o, x, nullptr, 0);
+}
+
+dim3 fgrid(long n, int nrhs) { return dim3((unsigned)((n + kT - 1) / kT), (unsigned)nrhs, 2); }
+
+lqcd_status clenshaw(lqcd_ctx *c, int nrhs, lqcd_field *o, const lqcd_field *w, const lqcd_field *hh,
+                     const lqcd_field *b1, const lqcd_field *b2, double cw, double t, double s2, double s0) {
+  const long n = cwords(o);
+  auto P = [](const lqcd_field *f, int p) { return f ? (const double2 *)f->data[p] : (const double2 *)nullptr; };
+  clenshaw_kernel<<<fgrid(n, nrhs), kT, 0, c->stream>>>(n, (double2 *)o->data[0], (double2 *)o->data[1], P(w, 0),
+                                                         P(w, 1), P(hh, 0), P(hh, 1), P(b1, 0), P(b1, 1), P(b2, 0),
+                                                         P(b2, 1), cw, t, s2, s0);
+  LQ_CU(cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status copy_field(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs) {
+  const size_t bytes = (size_t)cwords(src) * 16 * nrhs;
+  for (int p = 0; p < 2; p++)
+    LQ_CU(cudaMemcpyAsync(dst->data[p], src->data[p], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return LQCD_OK;
+}
+
+// per-RHS ||x + c y||^2 (c on the host) into out
+lqcd_status axpy_norms(lqcd_ctx *c, const lqcd_field *x, const lqcd_field *y, const std::vector<double> &cf, int nrhs,
+                       std::vector<double> &out) {
+  if (nrhs > 256) return set_error(LQCD_ERR_ARG, "at most 256 vectors per norm batch");
+  LQ_TRY(ensure_partials(c, nrhs));
+  double *dc = c->results + 256;
+  LQ_CU(cudaMemcpyAsync(dc, cf.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+  const long n = cwords(x);
+  // grid-stride: at most as many blocks per RHS as the partials hold
+  const long gx = std::min<long>(std::min<long>(1024, (2 * n + kT - 1) / kT), (c->Vh + 127) / 128 + 1);
+  dim3 g((unsigned)gx, (unsigned)nrhs);
+  axpy_norm_kernel<<<g, kT, 0, c->stream>>>(n, (const double2 *)x->data[0], (const double2 *)x->data[1],
+                                            (const double2 *)y->data[0], (const double2 *)y->data[1], dc, c->partials,
+                                            c->counter, c->results, nrhs);
+  LQ_CU(cudaGetLastError());
+  out.resize(nrhs);
+  LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  std::memcpy(out.data(), c->h_results, sizeof(double) * nrhs);
+  return LQCD_OK;
+}
+
+// orthonormalise the first m RHS of X (Cholesky QR), result in X (T scratch)
+lqcd_status orthonormalise(lqcd_ctx *c, lqcd_field *&X, lqcd_field *&T, int m) {
+  double2 *d;
+  LQ_TRY(small_scratch(c, (size_t)m * m, &d));
+  std::vector<zc> G, Rinv;
+  for (int pass = 0; pass < 2; pass++) {
+    LQ_TRY(gram(c, X, m, X, m, d));
+    LQ_TRY(to_host(c, d, (size_t)m * m, G));
+    if (!chol_inv(m, G, Rinv)) return set_error(LQCD_ERR_NOCONV, "low-mode block lost rank");
+    LQ_TRY(to_dev(c, Rinv, d));
+    LQ_TRY(rotate(c, X, m, d, m, T, 1.0, 0.0));
+    std::swap(X, T);
+  }
+  return LQCD_OK;
+}
+
+// Chebyshev coefficients of 1/sqrt(y) on [a, b], degree n (c[0] halved)
+void cheb_coeffs(double a, double b, int n, std::vector<double> &c) {
+  const int N = n + 1;
+  c.assign(N, 0.0);
+  std::vector<double> f(N), th(N);
+  for (int j = 0; j < N; j++) {
+    th[j] = M_PI * (j + 0.5) / N;
+    f[j] = 1.0 / std::sqrt(0.5 * ((b - a) * std::cos(th[j]) + a + b));
+  }
+  for (int k = 0; k < N; k++) {
+    double s = 0;
+    for (int j = 0; j < N; j++) s += f[j] * std::cos(k * th[j]);
+    c[k] = 2.0 * s / N;
+  }
+  c[0] *= 0.5;
+}
+
+double cheb_eval(double a, double b, const std::vector<double> &c, double y) {
+  const double t = (2 * y - a - b) / (b - a);
+  double b1 = 0, b2 = 0;
+  for (int k = (int)c.size() - 1; k >= 1; k--) {
+    const double b0 = c[k] + 2 * t * b1 - b2;
+    b2 = b1;
+    b1 = b0;
+  }
+  return c[0] + t * b1 - b2;
+}
+
+// sup over x in [sqrt a, sqrt b] of |x P(x^2) - 1|: a fine grid in x plus the nodes
+double sign_error(double a, double b, const std::vector<double> &c) {
+  const int npts = 50000;
+  double worst = 0;
+  const double lo = std::sqrt(a), hi = std::sqrt(b);
+  for (int i = 0; i < npts; i++) {
+    const double x = lo + (hi - lo) * i / (npts - 1);
+    worst = std::max(worst, std::fabs(x * cheb_eval(a, b, c, x * x) - 1));
+  }
+  const int N = (int)c.size();
+  for (int j = 0; j < N; j++) {
+    const double y = 0.5 * ((b - a) * std::cos(M_PI * (j + 0.5) / N) + a + b);
+    worst = std::max(worst, std::fabs(std::sqrt(y) * cheb_eval(a, b, c, y) - 1));
+  }
+  return worst;
+}
+
+// smallest degree <= nmax meeting tol (bisection around the Bernstein estimate)
+int cheb_degree(double a, double b, double tol, int nmax, std::vector<double> &c) {
+  auto ok = [&](int n) {
+    std::vector<double> cc;
+    cheb_coeffs(a, b, n, cc);
+    return sign_error(a, b, cc) <= tol;
+  };
+  int hi = std::max(4, (int)(std::log(2.0 / tol) * std::sqrt(b / a) / 2.0 * 1.2));
+  while (hi <= nmax && !ok(hi)) hi = (int)(hi * 1.5) + 1;
+  if (hi > nmax) {
+    if (!ok(nmax)) return -1;
+    hi = nmax;
+  }
+  int lo = 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (ok(mid))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  cheb_coeffs(a, b, hi, c);
+  return hi;
+}
+
+// eps(H_W) in -> out (nrhs RHS), FULL FP64 fields
+lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *out) {
+  OverlapState &S = *c->ov;
+  FieldGuard g;
+  lqcd_field *w, *b1, *b2, *h, *hh;
+  LQ_TRY(new_full(c, nrhs, &w));
+  g.f.push_back(w);
+  LQ_TRY(new_full(c, nrhs, &b1));
+  g.f.push_back(b1);
+  LQ_TRY(new_full(c, nrhs, &b2));
+  g.f.push_back(b2);
+  LQ_TRY(new_full(c, nrhs, &h));
+  g.f.push_back(h);
+  LQ_TRY(new_full(c, nrhs, &hh));
+  g.f.push_back(hh);
+  LQ_TRY(copy_field(c, w, in, nrhs));
+  double2 *proj = nullptr;
+  const int nl = S.nlow;
+  if (nl > 0) {
+    LQ_TRY(small_scratch(c, (size_t)nl * nrhs, &proj));
+    LQ_TRY(gram(c, S.vecs, nl, in, nrhs, proj));                // P = V^H in
+    LQ_TRY(rotate(c, S.vecs, nl, proj, nrhs, w, -1.0, 1.0));   // w = in - V P
+  }
+  const double a = S.a, b = S.b;
+  const double s2 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
+  const int n = S.degree;
+  // b_n = c_n w
+  LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[n], 0.0, 0.0, 0.0));
+  bool b2_zero = true;
+  for (int k = n - 1; k >= 1; k--) {
+    LQ_TRY(hw(c, nrhs, h, b1));
+    LQ_TRY(hw(c, nrhs, hh, h));
+    LQ_TRY(clenshaw(c, nrhs, b2, w, hh, b1, b2_zero ? nullptr : b2, S.coef[k], 2.0, s2, s0));
+    b2_zero = false;
+    std::swap(b1, b2);
+  }
+  // P w = c0 w + T b1 - b2
+  if (n >= 1) {
+    LQ_TRY(hw(c, nrhs, h, b1));
+    LQ_TRY(hw(c, nrhs, hh, h));
+    LQ_TRY(clenshaw(c, nrhs, b2, w, hh, b1, b2_zero ? nullptr : b2, S.coef[0], 1.0, s2, s0));
+    std::swap(b1, b2);
+  } else {
+    LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[0], 0.0, 0.0, 0.0));
+  }
+  LQ_TRY(hw(c, nrhs, out, b1));  // H P(H^2) w
+  if (nl > 0) {
+    double *dsg = c->results + 512;
+    std::vector<double> sg(nl);
+    for (int i = 0; i < nl; i++) sg[i] = S.lam[i] > 0 ? 1.0 : -1.0;
+    LQ_CU(cudaMemcpyAsync(dsg, sg.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, c->stream));
+    scale_rows_kernel<<<(nl * nrhs + 255) / 256, 256, 0, c->stream>>>(proj, nl, nrhs, dsg);
+    LQ_CU(cudaGetLastError());
+    LQ_TRY(rotate(c, S.vecs, nl, proj, nrhs, out, 1.0, 1.0));  // += V sign(lam) P
+    LQ_CU(cudaStreamSynchronize(c->stream));  // dsg and proj are reused by the next call
+  }
+  return LQCD_OK;
+}
+
+// out = a in + b (g5 e or e) on FULL FP64 fields
+lqcd_status combine(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in, const lqcd_field *e, double a,
+                    double b, int g5) {
+  const long n = cwords(in);
+  ov_combine_kernel<<<fgrid(n, nrhs), kT, 0, c->stream>>>(
+      in->Vh, n, (double2 *)out->data[0], (double2 *)out->data[1], (const double2 *)in->data[0],
+      (const double2 *)in->data[1], (const double2 *)e->data[0], (const double2 *)e->data[1], a, b, g5);
+  LQ_CU(cudaGetLastError());
+  return LQCD_OK;
+}
+
+// out = D_ov in = f (in + g5 eps in) + m in, or
+// out = D_ov^dag in = f (in + eps g5 in) + m in   (eps Hermitian)
+lqcd_status dov_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *out, int dagger) {
+  OverlapState &S = *c->ov;
+  const double rho = S.prm.rho, m = S.prm.mass;
+  const double f = (1.0 - m / (2.0 * rho)) * rho;
+  FieldGuard g;
+  lqcd_field *e;
+  LQ_TRY(new_full(c, nrhs, &e));
+  g.f.push_back(e);
+  if (!dagger) {
+    LQ_TRY(sign_apply(c, nrhs, in, e));
+    LQ_TRY(combine(c, nrhs, out, in, e, f + m, f, 1));
+  } else {
+    lqcd_field *g5in;
+    LQ_TRY(new_full(c, nrhs, &g5in));
+    g.f.push_back(g5in);
+    LQ_TRY(combine(c, nrhs, g5in, in, in, 0.0, 1.0, 1));  // g5 in
+    LQ_TRY(sign_apply(c, nrhs, g5in, e));
+    LQ_TRY(combine(c, nrhs, out, in, e, f + m, f, 0));
+  }
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+}  // namespace
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params *prm, lqcd_overlap_info *info) {
+  if (!c || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
+  if (!(prm->rho > 0 && prm->rho < 2)) return set_error(LQCD_ERR_ARG, "rho must be in (0, 2)");
+  if (prm->n_low < 0 || prm->n_low > 64) return set_error(LQCD_ERR_ARG, "n_low must be in 0..64");
+  if (!(prm->sign_tol > 0) || !(prm->eig_tol > 0)) return set_error(LQCD_ERR_ARG, "tolerances must be > 0");
+  if (prm->max_degree < 1 || prm->max_filter < 1) return set_error(LQCD_ERR_ARG, "max_degree, max_filter >= 1");
+  const auto t0 = std::chrono::steady_clock::now();
+  lqcd_overlap_info local{};
+  lqcd_overlap_info *inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  overlap_free(c);
+  LQ_TRY(ensure_state(c));
+  OverlapState &S = *c->ov;
+  S.prm = *prm;
+  LQ_TRY(lqcd_set_rho(c, prm->rho));
+  const long N = 12L * c->V;
+  const int want = std::max(1, prm->n_low);
+  // the block holds the wanted modes plus a margin wide enough to contain a
+  // near-degenerate cluster at the edge (smooth fields keep the free field's
+  // 12-fold momentum multiplets almost degenerate)
+  int m = std::min<long>(want + std::max(16, want), 96);
+  if (m > N) m = (int)N;
+  if (want >= m) return set_error(LQCD_ERR_ARG, "lattice too small for %d low modes", want);
+  FieldGuard g;
+  lqcd_field *X, *T, *HX, *Y, *Z;
+  LQ_TRY(new_full(c, m, &X));
+  g.f.push_back(X);
+  LQ_TRY(new_full(c, m, &T));
+  g.f.push_back(T);
+  LQ_TRY(new_full(c, m, &HX));
+  g.f.push_back(HX);
+  LQ_TRY(new_full(c, m, &Y));
+  g.f.push_back(Y);
+  LQ_TRY(new_full(c, m, &Z));
+  g.f.push_back(Z);
+  {
+    const long nd = 2L * cwords(X) * m;  // doubles per parity block
+    for (int p = 0; p < 2; p++) {
+      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)X->data[p], nd,
+                                                                                   prm->seed * 2 + p + 1);
+      LQ_CU(cudaGetLastError());
+    }
+  }
+  LQ_TRY(orthonormalise(c, X, T, m));
+  const double bmax = std::pow(4.0 - prm->rho + 4.0, 2);
+  std::vector<double> theta, resid;
+  std::vector<int> order;
+  double2 *d;
+  int sweep = 0;
+  bool converged = false;
+  for (;; sweep++) {
+    // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
+    // extremal problem; Rayleigh-Ritz with H_W itself would be an interior one
+    // and produce spurious Ritz values near zero)
+    LQ_TRY(hw(c, m, HX, X));
+    LQ_TRY(small_scratch(c, (size_t)m * m, &d));
+    LQ_TRY(gram(c, HX, m, HX, m, d));
+    std::vector<zc> W, Q;
+    LQ_TRY(to_host(c, d, (size_t)m * m, W));
+    for (int j = 0; j < m; j++)  // symmetrise
+      for (int i = 0; i < j; i++) {
+        const zc avg = 0.5 * (W[i + (size_t)m * j] + std::conj(W[j + (size_t)m * i]));
+        W[i + (size_t)m * j] = avg;
+        W[j + (size_t)m * i] = std::conj(avg);
+      }
+    std::vector<double> mu;
+    jacobi_eigh(m, W, Q, mu);
+    // ascending order of mu
+    order.resize(m);
+    for (int i = 0; i < m; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] < mu[y]; });
+    std::vector<zc> Qs((size_t)m * m);
+    std::vector<double> mus(m);
+    for (int jj = 0; jj < m; jj++) {
+      mus[jj] = mu[order[jj]];
+      for (int i = 0; i < m; i++) Qs[i + (size_t)m * jj] = Q[i + (size_t)m * order[jj]];
+    }
+    LQ_TRY(to_dev(c, Qs, d));
+    LQ_TRY(rotate(c, X, m, d, m, T, 1.0, 0.0));
+    LQ_TRY(rotate(c, HX, m, d, m, Y, 1.0, 0.0));
+    std::swap(X, T);
+    std::swap(HX, Y);
+    // residuals of H_W^2: || H_W (H_W x) - mu x ||
+    LQ_TRY(hw(c, m, Z, HX));
+    std::vector<double> neg(m), r2;
+    for (int i = 0; i < m; i++) neg[i] = -mus[i];
+    LQ_TRY(axpy_norms(c, Z, X, neg, m, r2));
+    converged = true;
+    for (int i = 0; i < want; i++) converged &= std::sqrt(r2[i]) <= prm->eig_tol;
+    theta = mus;
+    if (converged || sweep + 1 >= prm->max_filter) break;
+    // Chebyshev filter of H_W^2 damping [mu_max, bmax]
+    const double lo = std::min(std::max(mus[m - 1], 1.05 * mus[want - 1]), 0.9 * bmax), hi = bmax;
+    const double s2 = 2.0 / (hi - lo), s0 = -(hi + lo) / (hi - lo);
+    const int deg = 16;
+    // Y0 = X, Y1 = T(X) into Y, Y_{k+1} = 2 T(Y_k) - Y_{k-1}
+    LQ_TRY(hw(c, m, T, X));
+    LQ_TRY(hw(c, m, Z, T));
+    LQ_TRY(clenshaw(c, m, Y, nullptr, Z, X, nullptr, 0.0, 1.0, s2, s0));
+    lqcd_field *prev = X, *cur = Y, *nxt = HX;  // HX is free until the next Rayleigh-Ritz
+    for (int k = 1; k < deg; k++) {
+      LQ_TRY(hw(c, m, T, cur));
+      LQ_TRY(hw(c, m, Z, T));
+      LQ_TRY(clenshaw(c, m, nxt, nullptr, Z, cur, prev, 0.0, 2.0, s2, s0));
+      lqcd_field *t = prev;
+      prev = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    if (cur != X) {  // the filtered block becomes X; the other two are scratch
+      lqcd_field *others[3] = {X, Y, HX};
+      lqcd_field *rest[2];
+      int r = 0;
+      for (auto *o : others)
+        if (o != cur) rest[r++] = o;
+      X = cur;
+      Y = rest[0];
+      HX = rest[1];
+    }
+    LQ_TRY(orthonormalise(c, X, T, m));
+  }
+  // Rayleigh-Ritz with H_W in the span of the `want` converged vectors of
+  // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors
+  {
+    LQ_TRY(hw(c, want, HX, X));
+    LQ_TRY(small_scratch(c, (size_t)want * want, &d));
+    LQ_TRY(gram(c, X, want, HX, want, d));
+    std::vector<zc> W, Q;
+    LQ_TRY(to_host(c, d, (size_t)want * want, W));
+    for (int j = 0; j < want; j++)
+      for (int i = 0; i < j; i++) {
+        const zc avg = 0.5 * (W[i + (size_t)want * j] + std::conj(W[j + (size_t)want * i]));
+        W[i + (size_t)want * j] = avg;
+        W[j + (size_t)want * i] = std::conj(avg);
+      }
+    jacobi_eigh(want, W, Q, theta);
+    LQ_TRY(to_dev(c, Q, d));
+    LQ_TRY(rotate(c, X, want, d, want, T, 1.0, 0.0));
+    LQ_TRY(rotate(c, HX, want, d, want, Y, 1.0, 0.0));
+    std::swap(X, T);
+    std::swap(HX, Y);
+    std::vector<double> neg(want), r2;
+    for (int i = 0; i < want; i++) neg[i] = -theta[i];
+    LQ_TRY(axpy_norms(c, HX, X, neg, want, r2));
+    resid.resize(want);
+    for (int i = 0; i < want; i++) resid[i] = std::sqrt(r2[i]);
+    order.resize(want);
+    for (int i = 0; i < want; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return std::fabs(theta[x]) < std::fabs(theta[y]); });
+  }
+  inf->sweeps = sweep + 1;
+  // keep the `want` lowest (by |theta|), sorted
+  S.nlow = prm->n_low;
+  S.lam.assign(S.nlow, 0.0);
+  if (S.nlow > 0) {
+    LQ_TRY(lqcd_field_create(c, LQCD_F64, LQCD_FULL, S.nlow, &S.vecs));
+    const size_t bytes = (size_t)cwords(X) * 16;
+    for (int i = 0; i < S.nlow; i++) {
+      S.lam[i] = theta[order[i]];
+      for (int p = 0; p < 2; p++)
+        LQ_CU(cudaMemcpyAsync(col(S.vecs, p, i), col(X, p, order[i]), bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  inf->n_low = S.nlow;
+  for (int i = 0; i < std::min(64, want); i++) {
+    if (i < S.nlow) inf->lambda[i] = theta[order[i]];
+    inf->resid[i] = resid[order[i]];
+  }
+  // interval of the polynomial: every unprojected |lambda| >= |lambda_{n_low}|
+  const double lam_edge = std::fabs(theta[order[want - 1]]);
+  const double lam_a = prm->n_low > 0 ? lam_edge : lam_edge - resid[order[0]];
+  S.a = std::max(lam_a * lam_a, 1e-8);
+  S.b = bmax;
+  S.degree = cheb_degree(S.a, S.b, prm->sign_tol, prm->max_degree, S.coef);
+  if (S.degree < 0) return set_error(LQCD_ERR_NOCONV, "no Chebyshev degree <= %d reaches %.3g", prm->max_degree, prm->sign_tol);
+  inf->a = S.a;
+  inf->b = S.b;
+  inf->degree = S.degree;
+  inf->sign_error = sign_error(S.a, S.b, S.coef);
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  S.ready = true;
+  if (!converged) return set_error(LQCD_ERR_NOCONV, "low modes not converged in %d sweeps", prm->max_filter);
+  return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_overlap_lowmodes(lqcd_ctx *c, double *vecs, int on_device) {
+  if (!c || !vecs) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!c->ov || !c->ov->ready) return set_error(LQCD_ERR_STATE, "overlap not set up");
+  if (c->ov->nlow == 0) return LQCD_OK;
+  return lqcd_field_export(c, c->ov->vecs, vecs, on_device);
+}
+
+extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, int nrhs, int on_device,
+                                    lqcd_overlap_op op, const lqcd_solve_params *cg, lqcd_solve_info *info) {
+  if (!c || !out || !in) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!c->ov || !c->ov->ready) return set_error(LQCD_ERR_STATE, "overlap not set up (lqcd_overlap_setup)");
+  if (nrhs < 1 || nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
+  if ((int)op < 0 || (int)op > 3) return set_error(LQCD_ERR_ARG, "bad overlap op");
+  if (op == LQCD_OV_SOLVE && (!cg || !(cg->tol > 0) || cg->max_iter < 1))
+    return set_error(LQCD_ERR_ARG, "solve needs cg with tol > 0 and max_iter >= 1");
+  LQ_TRY(ensure_state(c));
+  const auto t0 = std::chrono::steady_clock::now();
+  FieldGuard g;
+  lqcd_field *fin, *fout;
+  LQ_TRY(new_full(c, nrhs, &fin));
+  g.f.push_back(fin);
+  LQ_TRY(new_full(c, nrhs, &fout));
+  g.f.push_back(fout);
+  LQ_TRY(lqcd_field_import(c, fin, in, on_device));
+  lqcd_solve_info local{};
+  lqcd_solve_info *inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  inf->nrhs = nrhs;
+  lqcd_status result = LQCD_OK;
+  if (op == LQCD_OV_SIGN) {
+    LQ_TRY(sign_apply(c, nrhs, fin, fout));
+  } else if (op == LQCD_OV_APPLY || op == LQCD_OV_APPLY_DAG) {
+    LQ_TRY(dov_apply(c, nrhs, fin, fout, op == LQCD_OV_APPLY_DAG));
+  } else {
+    // CGLS on D_ov: r = b (x0 = 0), s = D^dag r, p = s
+    lqcd_field *r, *s, *p, *q;
+    LQ_TRY(new_full(c, nrhs, &r));
+    g.f.push_back(r);
+    LQ_TRY(new_full(c, nrhs, &s));
+    g.f.push_back(s);
+    LQ_TRY(new_full(c, nrhs, &p));
+    g.f.push_back(p);
+    LQ_TRY(new_full(c, nrhs, &q));
+    g.f.push_back(q);
+    const size_t bytes = (size_t)cwords(fin) * 16 * nrhs;
+    for (int par = 0; par < 2; par++) LQ_CU(cudaMemsetAsync(fout->data[par], 0, bytes, c->stream));
+    LQ_TRY(copy_field(c, r, fin, nrhs));
+    std::vector<double> zero(nrhs, 0.0), bn2, gam, qq, rr;
+    LQ_TRY(axpy_norms(c, fin, fin, zero, nrhs, bn2));
+    LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+    LQ_TRY(copy_field(c, p, s, nrhs));
+    LQ_TRY(axpy_norms(c, s, s, zero, nrhs, gam));
+    std::vector<char> active(nrhs, 1);
+    double *dfac = c->results + 768;
+    auto axpy = [&](lqcd_field *y, const lqcd_field *x, const std::vector<double> &f) -> lqcd_status {
+      LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+      for (int par = 0; par < 2; par++)
+        LQ_CU(blas_axpy(LQCD_F64, LQCD_F64, c->Vh, nrhs, y->mut(par), x->ref(par), dfac, c->stream));
+      LQ_CU(cudaStreamSynchronize(c->stream));
+      return LQCD_OK;
+    };
+    auto scale = [&](lqcd_field *y, const std::vector<double> &f) -> lqcd_status {
+      LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+      for (int par = 0; par < 2; par++)
+        LQ_CU(blas_scale(LQCD_F64, LQCD_F64, c->Vh, nrhs, y->mut(par), y->ref(par), dfac, c->stream));
+      LQ_CU(cudaStreamSynchronize(c->stream));
+      return LQCD_OK;
+    };
+    int it = 0;
+    bool all = false;
+    for (; it < cg->max_iter; it++) {
+      LQ_TRY(dov_apply(c, nrhs, p, q, 0));
+      LQ_TRY(axpy_norms(c, q, q, zero, nrhs, qq));
+      std::vector<double> al(nrhs), nal(nrhs);
+      for (int k = 0; k < nrhs; k++) {
+        al[k] = active[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
+        nal[k] = -al[k];
+      }
+      LQ_TRY(axpy(fout, p, al));
+      LQ_TRY(axpy(r, q, nal));
+      LQ_TRY(axpy_norms(c, r, r, zero, nrhs, rr));
+      all = true;
+      for (int k = 0; k < nrhs; k++) {
+        if (!(rr[k] == rr[k])) return set_error(LQCD_ERR_NOCONV, "overlap CG residual is NaN");
+        if (active[k] && rr[k] <= std::pow(0.5 * cg->tol, 2) * bn2[k]) active[k] = 0;
+        all &= !active[k];
+      }
+      if (all) {
+        it++;
+        break;
+      }
+      LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+      std::vector<double> gn;
+      LQ_TRY(axpy_norms(c, s, s, zero, nrhs, gn));
+      std::vector<double> be(nrhs), one(nrhs);
+      for (int k = 0; k < nrhs; k++) {
+        be[k] = active[k] && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
+        one[k] = active[k] ? 1.0 : 0.0;
+        if (active[k]) gam[k] = gn[k];
+      }
+      LQ_TRY(scale(p, be));
+      LQ_TRY(axpy(p, s, one));
+    }
+    inf->iters = it;
+    // true residual b - D_ov x
+    LQ_TRY(dov_apply(c, nrhs, fout, q, 0));
+    std::vector<double> mone(nrhs, -1.0), res;
+    LQ_TRY(axpy_norms(c, fin, q, mone, nrhs, res));
+    bool ok = true;
+    for (int k = 0; k < nrhs; k++) {
+      inf->true_resid[k] = std::sqrt(res[k] / bn2[k]);
+      ok &= inf->true_resid[k] <= cg->tol;
+    }
+    if (!ok) result = set_error(LQCD_ERR_NOCONV, "overlap CG: true residual above tol after %d iterations", it);
+  }
+  LQ_TRY(lqcd_field_export(c, fout, out, on_device));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return result;
+}
