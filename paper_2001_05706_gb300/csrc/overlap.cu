@@ -39,7 +39,8 @@ struct OverlapState {
   lqcd_overlap_params prm{};
   int nlow = 0;
   std::vector<double> lam;
-  lqcd_field *vecs = nullptr;  // FULL FP64, nrhs = nlow
+  lqcd_field *vecs = nullptr;    // FULL FP64, nrhs = nlow
+  lqcd_field *vecs32 = nullptr;  // the same in FP32 (inner solves)
   std::vector<double> coef;
   double a = 0, b = 0;
   int degree = 0;
@@ -52,6 +53,7 @@ void overlap_free(lqcd_ctx *c) {
   OverlapState *s = c->ov;
   if (!s) return;
   if (s->vecs) lqcd_field_destroy(s->vecs);
+  if (s->vecs32) lqcd_field_destroy(s->vecs32);
   if (s->blas) cublasDestroy(s->blas);
   if (s->dsmall) cudaFree(s->dsmall);
   delete s;
@@ -64,42 +66,61 @@ constexpr int kT = 256;
 
 // ---- kernels on FULL FP64 fields: grid (blocks over words*Vh, nrhs, parity) --
 
-// out = cw w + t (s2 hh + s0 b1) - b2   (w, b2 may be null: zero)
-__global__ void clenshaw_kernel(long n, double2 *o0, double2 *o1, const double2 *w0, const double2 *w1,
-                                const double2 *h0, const double2 *h1, const double2 *a0, const double2 *a1,
-                                const double2 *c0, const double2 *c1, double cw, double t, double s2, double s0) {
+// out = cw w + t (s2 hh + s0 b1) - b2   (w, b2 may be null: zero), element-wise
+// on the complex numbers of FULL fields (FP64: double2, FP32: float2 view);
+// coefficients in FP64, arithmetic in the storage precision's math type
+template <typename C2>
+__global__ void clenshaw_kernel(long n, C2 *o0, C2 *o1, const C2 *w0, const C2 *w1, const C2 *h0, const C2 *h1,
+                                const C2 *a0, const C2 *a1, const C2 *c0, const C2 *c1, double cw_, double t_,
+                                double s2_, double s0_) {
+  using R = decltype(C2{}.x);
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long off = (long)blockIdx.y * n + i;
   if (i >= n) return;
   const int p = blockIdx.z;
-  double2 *o = p ? o1 : o0;
-  const double2 *w = p ? w1 : w0, *h = p ? h1 : h0, *b1 = p ? a1 : a0, *b2 = p ? c1 : c0;
-  const double2 hv = h[off], bv = b1[off];
-  double2 r = make_double2(t * (s2 * hv.x + s0 * bv.x), t * (s2 * hv.y + s0 * bv.y));
+  const R cw = (R)cw_, t = (R)t_, s2 = (R)s2_, s0 = (R)s0_;
+  C2 *o = p ? o1 : o0;
+  const C2 *w = p ? w1 : w0, *h = p ? h1 : h0, *b1 = p ? a1 : a0, *b2 = p ? c1 : c0;
+  const C2 hv = h[off], bv = b1[off];
+  C2 r;
+  r.x = t * (s2 * hv.x + s0 * bv.x);
+  r.y = t * (s2 * hv.y + s0 * bv.y);
   if (w) {
-    const double2 wv = w[off];
+    const C2 wv = w[off];
     r.x += cw * wv.x;
     r.y += cw * wv.y;
   }
   if (b2) {
-    const double2 cv = b2[off];
+    const C2 cv = b2[off];
     r.x -= cv.x;
     r.y -= cv.y;
   }
   o[off] = r;
 }
 
-// out = a in + b (g5 e or e); FP64 word w of a site holds spin w / 3
-__global__ void ov_combine_kernel(long Vh, long n, double2 *o0, double2 *o1, const double2 *i0, const double2 *i1,
-                                  const double2 *e0, const double2 *e1, double a, double b, int g5) {
+// out = a in + b (g5 e or e), element-wise on complex numbers.  Element e of
+// one RHS of one parity holds spin: FP64 (one complex per 16-byte word w,
+// e = w Vh + i) spin = w / 3; FP32 (two complex per word, e = 2 (w Vh + i) + j)
+// spin = (2 w + j) / 3.
+template <typename C2>
+__global__ void ov_combine_kernel(long Vh, long n, C2 *o0, C2 *o1, const C2 *i0, const C2 *i1, const C2 *e0,
+                                  const C2 *e1, double a_, double b_, int g5) {
+  using R = decltype(C2{}.x);
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long off = (long)blockIdx.y * n + i;
   const int p = blockIdx.z;
-  const double2 x = (p ? i1 : i0)[off], e = (p ? e1 : e0)[off];
-  const int spin = (int)(i / Vh) / 3;
-  const double g = (g5 && spin >= 2) ? -b : b;
-  (p ? o1 : o0)[off] = make_double2(a * x.x + g * e.x, a * x.y + g * e.y);
+  const C2 x = (p ? i1 : i0)[off], e = (p ? e1 : e0)[off];
+  int spin;
+  if (sizeof(R) == 8)
+    spin = (int)(i / Vh) / 3;
+  else
+    spin = (int)(2 * ((i >> 1) / Vh) + (i & 1)) / 3;
+  const R a = (R)a_, b = (g5 && spin >= 2) ? (R)-b_ : (R)b_;
+  C2 r;
+  r.x = a * x.x + b * e.x;
+  r.y = a * x.y + b * e.y;
+  (p ? o1 : o0)[off] = r;
 }
 
 // Gaussian fill of raw doubles: SplitMix64 (Steele et al. 2014) counters + Box-Muller
@@ -138,11 +159,13 @@ __global__ void axpy_norm_kernel(long n, const double2 *x0, const double2 *x1, c
   grid_reduce<1>(v, partials, counter, result, k, nrhs, 1);
 }
 
-__global__ void scale_rows_kernel(double2 *m, int rows, int cols, const double *s) {
+template <typename C2>
+__global__ void scale_rows_kernel(C2 *m, int rows, int cols, const double *s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * cols) return;
   const double f = s[i % rows];
-  m[i] = make_double2(f * m[i].x, f * m[i].y);
+  m[i].x *= f;
+  m[i].y *= f;
 }
 
 // ---- host helpers ------------------------------------------------------------
@@ -177,39 +200,56 @@ lqcd_status small_scratch(lqcd_ctx *c, size_t n, double2 **p) {
   return LQCD_OK;
 }
 
-long cwords(const lqcd_field *f) { return 12L * f->Vh; }  // complex numbers per RHS per parity (FP64)
+long cwords(const lqcd_field *f) { return 12L * f->Vh; }  // complex numbers per RHS per parity
+size_t celem(const lqcd_field *f) { return f->prec == LQCD_F64 ? 16 : 8; }  // bytes per complex number
 
-double2 *col(const lqcd_field *f, int p, int k) {
-  return reinterpret_cast<double2 *>(f->data[p]) + (long)k * cwords(f);
+void *col(const lqcd_field *f, int p, int k) {
+  return reinterpret_cast<char *>(f->data[p]) + (size_t)k * cwords(f) * celem(f);
 }
 
-// C(p x q) = X^H Y over both parities (X: first p RHS of fx, Y: first q RHS of fy), C on the device
-lqcd_status gram(lqcd_ctx *c, const lqcd_field *fx, int p, const lqcd_field *fy, int q, double2 *C) {
+// C(p x q) = X^H Y over both parities (X: first p RHS of fx, Y: first q RHS of
+// fy, same precision), C on the device as double2 (FP64) or float2 (FP32)
+lqcd_status gram(lqcd_ctx *c, const lqcd_field *fx, int p, const lqcd_field *fy, int q, void *C) {
   OverlapState &s = *c->ov;
-  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
   const int N = (int)cwords(fx);
-  for (int par = 0; par < 2; par++)
-    LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one,
-                               reinterpret_cast<const cuDoubleComplex *>(col(fx, par, 0)), N,
-                               reinterpret_cast<const cuDoubleComplex *>(col(fy, par, 0)), N, par ? &one : &zero,
-                               reinterpret_cast<cuDoubleComplex *>(C), p),
-                   "ZGEMM (Gram)"));
+  for (int par = 0; par < 2; par++) {
+    if (fx->prec == LQCD_F64) {
+      const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+      LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one,
+                                 (const cuDoubleComplex *)col(fx, par, 0), N, (const cuDoubleComplex *)col(fy, par, 0),
+                                 N, par ? &one : &zero, (cuDoubleComplex *)C, p),
+                     "ZGEMM (Gram)"));
+    } else {
+      const cuComplex one = make_cuComplex(1, 0), zero = make_cuComplex(0, 0);
+      LQ_TRY(blas_ok(cublasCgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one, (const cuComplex *)col(fx, par, 0), N,
+                                 (const cuComplex *)col(fy, par, 0), N, par ? &one : &zero, (cuComplex *)C, p),
+                     "CGEMM (Gram)"));
+    }
+  }
   return LQCD_OK;
 }
 
 // Z = alpha X M + beta Z (X: N x p block of fx, M: p x q on the device, Z: N x q block of fz)
-lqcd_status rotate(lqcd_ctx *c, const lqcd_field *fx, int p, const double2 *M, int q, lqcd_field *fz, zc alpha,
+lqcd_status rotate(lqcd_ctx *c, const lqcd_field *fx, int p, const void *M, int q, lqcd_field *fz, zc alpha,
                    zc beta) {
   OverlapState &s = *c->ov;
-  const cuDoubleComplex al = make_cuDoubleComplex(alpha.real(), alpha.imag());
-  const cuDoubleComplex be = make_cuDoubleComplex(beta.real(), beta.imag());
   const int N = (int)cwords(fx);
-  for (int par = 0; par < 2; par++)
-    LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al,
-                               reinterpret_cast<const cuDoubleComplex *>(col(fx, par, 0)), N,
-                               reinterpret_cast<const cuDoubleComplex *>(M), p, &be,
-                               reinterpret_cast<cuDoubleComplex *>(col(fz, par, 0)), N),
-                   "ZGEMM (rotation)"));
+  for (int par = 0; par < 2; par++) {
+    if (fx->prec == LQCD_F64) {
+      const cuDoubleComplex al = make_cuDoubleComplex(alpha.real(), alpha.imag());
+      const cuDoubleComplex be = make_cuDoubleComplex(beta.real(), beta.imag());
+      LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al,
+                                 (const cuDoubleComplex *)col(fx, par, 0), N, (const cuDoubleComplex *)M, p, &be,
+                                 (cuDoubleComplex *)col(fz, par, 0), N),
+                     "ZGEMM (rotation)"));
+    } else {
+      const cuComplex al = make_cuComplex((float)alpha.real(), (float)alpha.imag());
+      const cuComplex be = make_cuComplex((float)beta.real(), (float)beta.imag());
+      LQ_TRY(blas_ok(cublasCgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al, (const cuComplex *)col(fx, par, 0), N,
+                                 (const cuComplex *)M, p, &be, (cuComplex *)col(fz, par, 0), N),
+                     "CGEMM (rotation)"));
+    }
+  }
   return LQCD_OK;
 }
 
@@ -301,6 +341,9 @@ lqcd_status to_dev(lqcd_ctx *c, const std::vector<zc> &h, double2 *d) {
 }
 
 lqcd_status new_full(lqcd_ctx *c, int nrhs, lqcd_field **f) { return lqcd_field_create(c, LQCD_F64, LQCD_FULL, nrhs, f); }
+lqcd_status new_like(lqcd_ctx *c, const lqcd_field *ref, int nrhs, lqcd_field **f) {
+  return lqcd_field_create(c, ref->prec, LQCD_FULL, nrhs, f);
+}
 
 struct FieldGuard {
   std::vector<lqcd_field *> f;
@@ -313,7 +356,15 @@ struct FieldGuard {
 lqcd_status hw(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in) {
   MutField o[2] = {out->mut(0), out->mut(1)};
   FieldRef x[2] = {in->ref(0), in->ref(1)};
-  return op_hw(c, LQCD_F64, 18, nrhs, o, x, nullptr, 0);
+  return op_hw(c, out->prec, out->prec == LQCD_F64 ? 18 : 12, nrhs, o, x, nullptr, 0);
+}
+
+// dst = src converted between precisions (FULL fields, first nrhs RHS)
+lqcd_status convert_full(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs) {
+  for (int p = 0; p < 2; p++)
+    LQ_CU(convert_spinor(src->prec, dst->prec, c->Vh, nrhs, src->data[p], src->scale[p], src->rhs_words(),
+                         dst->data[p], dst->scale[p], dst->rhs_words(), 1.0, c->stream));
+  return LQCD_OK;
 }
 
 dim3 fgrid(long n, int nrhs) { return dim3((unsigned)((n + kT - 1) / kT), (unsigned)nrhs, 2); }
@@ -321,16 +372,25 @@ dim3 fgrid(long n, int nrhs) { return dim3((unsigned)((n + kT - 1) / kT), (unsig
 lqcd_status clenshaw(lqcd_ctx *c, int nrhs, lqcd_field *o, const lqcd_field *w, const lqcd_field *hh,
                      const lqcd_field *b1, const lqcd_field *b2, double cw, double t, double s2, double s0) {
   const long n = cwords(o);
-  auto P = [](const lqcd_field *f, int p) { return f ? (const double2 *)f->data[p] : (const double2 *)nullptr; };
-  clenshaw_kernel<<<fgrid(n, nrhs), kT, 0, c->stream>>>(n, (double2 *)o->data[0], (double2 *)o->data[1], P(w, 0),
-                                                         P(w, 1), P(hh, 0), P(hh, 1), P(b1, 0), P(b1, 1), P(b2, 0),
-                                                         P(b2, 1), cw, t, s2, s0);
+  if (o->prec == LQCD_F64) {
+    auto P = [](const lqcd_field *f, int p) { return f ? (const double2 *)f->data[p] : (const double2 *)nullptr; };
+    clenshaw_kernel<double2><<<fgrid(n, nrhs), kT, 0, c->stream>>>(
+        n, (double2 *)o->data[0], (double2 *)o->data[1], P(w, 0), P(w, 1), P(hh, 0), P(hh, 1), P(b1, 0), P(b1, 1),
+        P(b2, 0), P(b2, 1), cw, t, s2, s0);
+  } else if (o->prec == LQCD_F32) {
+    auto P = [](const lqcd_field *f, int p) { return f ? (const float2 *)f->data[p] : (const float2 *)nullptr; };
+    clenshaw_kernel<float2><<<fgrid(n, nrhs), kT, 0, c->stream>>>(
+        n, (float2 *)o->data[0], (float2 *)o->data[1], P(w, 0), P(w, 1), P(hh, 0), P(hh, 1), P(b1, 0), P(b1, 1),
+        P(b2, 0), P(b2, 1), cw, t, s2, s0);
+  } else {
+    return set_error(LQCD_ERR_ARG, "three-term kernel needs FP64 or FP32 fields");
+  }
   LQ_CU(cudaGetLastError());
   return LQCD_OK;
 }
 
 lqcd_status copy_field(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs) {
-  const size_t bytes = (size_t)cwords(src) * 16 * nrhs;
+  const size_t bytes = (size_t)cwords(src) * celem(src) * nrhs;
   for (int p = 0; p < 2; p++)
     LQ_CU(cudaMemcpyAsync(dst->data[p], src->data[p], bytes, cudaMemcpyDeviceToDevice, c->stream));
   return LQCD_OK;
@@ -444,28 +504,26 @@ int cheb_degree(double a, double b, double tol, int nmax, std::vector<double> &c
   return hi;
 }
 
-// eps(H_W) in -> out (nrhs RHS), FULL FP64 fields
+// eps(H_W) in -> out (nrhs RHS), FULL fields of one precision (FP64 or FP32)
 lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *out) {
   OverlapState &S = *c->ov;
+  const bool f64 = in->prec == LQCD_F64;
   FieldGuard g;
   lqcd_field *w, *b1, *b2, *h, *hh;
-  LQ_TRY(new_full(c, nrhs, &w));
-  g.f.push_back(w);
-  LQ_TRY(new_full(c, nrhs, &b1));
-  g.f.push_back(b1);
-  LQ_TRY(new_full(c, nrhs, &b2));
-  g.f.push_back(b2);
-  LQ_TRY(new_full(c, nrhs, &h));
-  g.f.push_back(h);
-  LQ_TRY(new_full(c, nrhs, &hh));
-  g.f.push_back(hh);
+  for (lqcd_field **q : {&w, &b1, &b2, &h, &hh}) {
+    LQ_TRY(new_like(c, in, nrhs, q));
+    g.f.push_back(*q);
+  }
   LQ_TRY(copy_field(c, w, in, nrhs));
-  double2 *proj = nullptr;
+  void *proj = nullptr;
   const int nl = S.nlow;
+  const lqcd_field *V = f64 ? S.vecs : S.vecs32;
   if (nl > 0) {
-    LQ_TRY(small_scratch(c, (size_t)nl * nrhs, &proj));
-    LQ_TRY(gram(c, S.vecs, nl, in, nrhs, proj));                // P = V^H in
-    LQ_TRY(rotate(c, S.vecs, nl, proj, nrhs, w, -1.0, 1.0));   // w = in - V P
+    double2 *d;
+    LQ_TRY(small_scratch(c, (size_t)nl * nrhs, &d));
+    proj = d;
+    LQ_TRY(gram(c, V, nl, in, nrhs, proj));             // P = V^H in
+    LQ_TRY(rotate(c, V, nl, proj, nrhs, w, -1.0, 1.0));  // w = in - V P
   }
   const double a = S.a, b = S.b;
   const double s2 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
@@ -495,21 +553,29 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
     std::vector<double> sg(nl);
     for (int i = 0; i < nl; i++) sg[i] = S.lam[i] > 0 ? 1.0 : -1.0;
     LQ_CU(cudaMemcpyAsync(dsg, sg.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, c->stream));
-    scale_rows_kernel<<<(nl * nrhs + 255) / 256, 256, 0, c->stream>>>(proj, nl, nrhs, dsg);
+    if (f64)
+      scale_rows_kernel<double2><<<(nl * nrhs + 255) / 256, 256, 0, c->stream>>>((double2 *)proj, nl, nrhs, dsg);
+    else
+      scale_rows_kernel<float2><<<(nl * nrhs + 255) / 256, 256, 0, c->stream>>>((float2 *)proj, nl, nrhs, dsg);
     LQ_CU(cudaGetLastError());
-    LQ_TRY(rotate(c, S.vecs, nl, proj, nrhs, out, 1.0, 1.0));  // += V sign(lam) P
+    LQ_TRY(rotate(c, V, nl, proj, nrhs, out, 1.0, 1.0));  // += V sign(lam) P
     LQ_CU(cudaStreamSynchronize(c->stream));  // dsg and proj are reused by the next call
   }
   return LQCD_OK;
 }
 
-// out = a in + b (g5 e or e) on FULL FP64 fields
+// out = a in + b (g5 e or e) on FULL fields of one precision
 lqcd_status combine(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in, const lqcd_field *e, double a,
                     double b, int g5) {
   const long n = cwords(in);
-  ov_combine_kernel<<<fgrid(n, nrhs), kT, 0, c->stream>>>(
-      in->Vh, n, (double2 *)out->data[0], (double2 *)out->data[1], (const double2 *)in->data[0],
-      (const double2 *)in->data[1], (const double2 *)e->data[0], (const double2 *)e->data[1], a, b, g5);
+  if (in->prec == LQCD_F64)
+    ov_combine_kernel<double2><<<fgrid(n, nrhs), kT, 0, c->stream>>>(
+        in->Vh, n, (double2 *)out->data[0], (double2 *)out->data[1], (const double2 *)in->data[0],
+        (const double2 *)in->data[1], (const double2 *)e->data[0], (const double2 *)e->data[1], a, b, g5);
+  else
+    ov_combine_kernel<float2><<<fgrid(n, nrhs), kT, 0, c->stream>>>(
+        in->Vh, n, (float2 *)out->data[0], (float2 *)out->data[1], (const float2 *)in->data[0],
+        (const float2 *)in->data[1], (const float2 *)e->data[0], (const float2 *)e->data[1], a, b, g5);
   LQ_CU(cudaGetLastError());
   return LQCD_OK;
 }
@@ -522,20 +588,234 @@ lqcd_status dov_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *o
   const double f = (1.0 - m / (2.0 * rho)) * rho;
   FieldGuard g;
   lqcd_field *e;
-  LQ_TRY(new_full(c, nrhs, &e));
+  LQ_TRY(new_like(c, in, nrhs, &e));
   g.f.push_back(e);
   if (!dagger) {
     LQ_TRY(sign_apply(c, nrhs, in, e));
     LQ_TRY(combine(c, nrhs, out, in, e, f + m, f, 1));
   } else {
     lqcd_field *g5in;
-    LQ_TRY(new_full(c, nrhs, &g5in));
+    LQ_TRY(new_like(c, in, nrhs, &g5in));
     g.f.push_back(g5in);
     LQ_TRY(combine(c, nrhs, g5in, in, in, 0.0, 1.0, 1));  // g5 in
     LQ_TRY(sign_apply(c, nrhs, g5in, e));
     LQ_TRY(combine(c, nrhs, out, in, e, f + m, f, 0));
   }
   LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+// per-RHS ||v||^2 of a FULL field (any precision), both parities
+lqcd_status field_norms(lqcd_ctx *c, const lqcd_field *v, int nrhs, std::vector<double> &out) {
+  if (nrhs > 128) return set_error(LQCD_ERR_ARG, "at most 128 vectors per norm batch");
+  LQ_TRY(ensure_partials(c, nrhs));
+  for (int p = 0; p < 2; p++)
+    LQ_CU(blas_norm2(v->prec, c->Vh, nrhs, v->ref(p), c->partials, c->counter, c->results + 128 * p, 1, c->stream));
+  LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * 256, cudaMemcpyDeviceToHost, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  out.resize(nrhs);
+  for (int k = 0; k < nrhs; k++) out[k] = c->h_results[k] + c->h_results[128 + k];
+  return LQCD_OK;
+}
+
+// y += f_k x (per-RHS factors on the host), FULL fields, y precision >= x precision
+lqcd_status axpy_full(lqcd_ctx *c, lqcd_field *y, const lqcd_field *x, const std::vector<double> &f, int nrhs) {
+  double *dfac = c->results + 768;
+  LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+  for (int par = 0; par < 2; par++)
+    LQ_CU(blas_axpy(y->prec, x->prec, c->Vh, nrhs, y->mut(par), x->ref(par), dfac, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+// y = f_k x (precision conversion included), FULL fields
+lqcd_status scale_full(lqcd_ctx *c, lqcd_field *y, const lqcd_field *x, const std::vector<double> &f, int nrhs) {
+  double *dfac = c->results + 768;
+  LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
+  for (int par = 0; par < 2; par++)
+    LQ_CU(blas_scale(y->prec, x->prec, c->Vh, nrhs, y->mut(par), x->ref(par), dfac, c->stream));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+// CG on the normal equations of D_ov x = b, FP64 throughout (x0 = 0)
+lqcd_status ov_cgls_fp64(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field *x, const lqcd_solve_params *cg,
+                         lqcd_solve_info *inf, const std::vector<double> &bn2) {
+  FieldGuard g;
+  lqcd_field *r, *s, *p, *q;
+  for (lqcd_field **f : {&r, &s, &p, &q}) {
+    LQ_TRY(new_full(c, nrhs, f));
+    g.f.push_back(*f);
+  }
+  const size_t bytes = (size_t)cwords(b) * 16 * nrhs;
+  for (int par = 0; par < 2; par++) LQ_CU(cudaMemsetAsync(x->data[par], 0, bytes, c->stream));
+  LQ_TRY(copy_field(c, r, b, nrhs));
+  std::vector<double> gam, qq, rr;
+  LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+  LQ_TRY(copy_field(c, p, s, nrhs));
+  LQ_TRY(field_norms(c, s, nrhs, gam));
+  std::vector<char> active(nrhs, 1);
+  int it = 0;
+  for (; it < cg->max_iter; it++) {
+    LQ_TRY(dov_apply(c, nrhs, p, q, 0));
+    LQ_TRY(field_norms(c, q, nrhs, qq));
+    std::vector<double> al(nrhs), nal(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+      al[k] = active[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
+      nal[k] = -al[k];
+    }
+    LQ_TRY(axpy_full(c, x, p, al, nrhs));
+    LQ_TRY(axpy_full(c, r, q, nal, nrhs));
+    LQ_TRY(field_norms(c, r, nrhs, rr));
+    bool all = true;
+    for (int k = 0; k < nrhs; k++) {
+      if (!(rr[k] == rr[k])) return set_error(LQCD_ERR_NOCONV, "overlap CG residual is NaN");
+      if (active[k] && rr[k] <= std::pow(0.5 * cg->tol, 2) * bn2[k]) active[k] = 0;
+      all &= !active[k];
+    }
+    if (all) {
+      it++;
+      break;
+    }
+    LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+    std::vector<double> gn, be(nrhs), one(nrhs);
+    LQ_TRY(field_norms(c, s, nrhs, gn));
+    for (int k = 0; k < nrhs; k++) {
+      be[k] = active[k] && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
+      one[k] = active[k] ? 1.0 : 0.0;
+      if (active[k]) gam[k] = gn[k];
+    }
+    LQ_TRY(scale_full(c, p, p, be, nrhs));
+    LQ_TRY(axpy_full(c, p, s, one, nrhs));
+  }
+  inf->iters = it;
+  inf->mhat_applies += 2.0 * it + 1;
+  return LQCD_OK;
+}
+
+// Mixed precision: CG on the normal equations of D_ov with FP32 storage and
+// arithmetic (FP32 sign function) on the residual normalised to 1; the FP64
+// solution absorbs the inner one and the residual is recomputed with the FP64
+// operator whenever the inner residual fell below delta (or stagnated); the
+// search direction is kept across updates, rescaled, unless the update failed
+// to reduce the residual.
+lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field *x, const lqcd_solve_params *cg,
+                          lqcd_solve_info *inf, const std::vector<double> &bn2) {
+  FieldGuard g;
+  lqcd_field *r64, *t64, *xlo, *r, *s, *p, *q;
+  for (lqcd_field **f : {&r64, &t64}) {
+    LQ_TRY(new_full(c, nrhs, f));
+    g.f.push_back(*f);
+  }
+  for (lqcd_field **f : {&xlo, &r, &s, &p, &q}) {
+    LQ_TRY(lqcd_field_create(c, LQCD_F32, LQCD_FULL, nrhs, f));
+    g.f.push_back(*f);
+  }
+  const double delta = (cg->delta > 0 && cg->delta < 1) ? cg->delta : 0.1;
+  const size_t bytes64 = (size_t)cwords(b) * 16 * nrhs, bytes32 = (size_t)cwords(b) * 8 * nrhs;
+  for (int par = 0; par < 2; par++) {
+    LQ_CU(cudaMemsetAsync(x->data[par], 0, bytes64, c->stream));
+    LQ_CU(cudaMemsetAsync(xlo->data[par], 0, bytes32, c->stream));
+  }
+  std::vector<double> target(nrhs), sigma(nrhs), inv(nrhs), gam, qq, rr, best(nrhs, 1.0);
+  std::vector<int> stall(nrhs, 0);
+  std::vector<char> active(nrhs, 1);
+  for (int k = 0; k < nrhs; k++) {
+    target[k] = 0.5 * cg->tol * std::sqrt(bn2[k]);
+    sigma[k] = std::sqrt(bn2[k]);
+    inv[k] = 1.0 / sigma[k];
+  }
+  LQ_TRY(copy_field(c, r64, b, nrhs));
+  LQ_TRY(scale_full(c, r, r64, inv, nrhs));
+  LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+  LQ_TRY(copy_field(c, p, s, nrhs));
+  LQ_TRY(field_norms(c, s, nrhs, gam));
+  int it = 0;
+  bool done = false;
+  while (!done && it < cg->max_iter) {
+    LQ_TRY(dov_apply(c, nrhs, p, q, 0));
+    LQ_TRY(field_norms(c, q, nrhs, qq));
+    std::vector<double> al(nrhs), nal(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+      al[k] = active[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
+      nal[k] = -al[k];
+    }
+    LQ_TRY(axpy_full(c, xlo, p, al, nrhs));
+    LQ_TRY(axpy_full(c, r, q, nal, nrhs));
+    LQ_TRY(field_norms(c, r, nrhs, rr));
+    it++;
+    bool all_dropped = true, any_target = false, any_stall = false;
+    for (int k = 0; k < nrhs; k++) {
+      if (!active[k]) continue;
+      if (!(rr[k] == rr[k])) return set_error(LQCD_ERR_NOCONV, "overlap inner residual is NaN");
+      if (rr[k] > delta * delta) all_dropped = false;
+      if (sigma[k] * std::sqrt(rr[k]) <= target[k]) any_target = true;
+      if (rr[k] < 0.25 * best[k]) {
+        best[k] = rr[k];
+        stall[k] = 0;
+      } else if (++stall[k] >= 16) {
+        any_stall = true;
+      }
+    }
+    if (all_dropped || any_target || any_stall || it >= cg->max_iter) {
+      // reliable update in FP64
+      std::vector<double> fx(nrhs), mone(nrhs, -1.0), r2;
+      for (int k = 0; k < nrhs; k++) fx[k] = active[k] ? sigma[k] : 0.0;
+      LQ_TRY(axpy_full(c, x, xlo, fx, nrhs));
+      for (int par = 0; par < 2; par++) LQ_CU(cudaMemsetAsync(xlo->data[par], 0, bytes32, c->stream));
+      LQ_TRY(dov_apply(c, nrhs, x, t64, 0));
+      LQ_TRY(copy_field(c, r64, b, nrhs));
+      LQ_TRY(axpy_full(c, r64, t64, mone, nrhs));
+      LQ_TRY(field_norms(c, r64, nrhs, r2));
+      inf->reliable_updates++;
+      inf->mhat_applies += 1;
+      done = true;
+      std::vector<double> fp(nrhs), fr(nrhs), fs(nrhs, 0.0);
+      for (int k = 0; k < nrhs; k++) {
+        if (!active[k]) {
+          fp[k] = 0.0;
+          fr[k] = 0.0;
+          continue;
+        }
+        const double snew = std::sqrt(r2[k]);
+        if (!(snew == snew)) return set_error(LQCD_ERR_NOCONV, "overlap FP64 residual is NaN");
+        if (snew <= target[k]) {
+          active[k] = 0;
+          fp[k] = fr[k] = 0.0;
+          continue;
+        }
+        done = false;
+        const bool restart = snew >= sigma[k] || stall[k] >= 16;
+        fp[k] = restart ? 0.0 : sigma[k] / snew;
+        fs[k] = restart ? 1.0 : 0.0;
+        fr[k] = 1.0 / snew;
+        sigma[k] = snew;
+        best[k] = 1.0;
+        stall[k] = 0;
+      }
+      if (done) break;
+      LQ_TRY(scale_full(c, p, p, fp, nrhs));
+      LQ_TRY(scale_full(c, r, r64, fr, nrhs));
+      LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+      std::vector<double> gn;
+      LQ_TRY(field_norms(c, s, nrhs, gn));
+      for (int k = 0; k < nrhs; k++)
+        if (active[k]) gam[k] = gn[k];
+      LQ_TRY(axpy_full(c, p, s, fs, nrhs));
+      continue;
+    }
+    LQ_TRY(dov_apply(c, nrhs, r, s, 1));
+    std::vector<double> gn, be(nrhs), one(nrhs);
+    LQ_TRY(field_norms(c, s, nrhs, gn));
+    for (int k = 0; k < nrhs; k++) {
+      be[k] = active[k] && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
+      one[k] = active[k] ? 1.0 : 0.0;
+      if (active[k]) gam[k] = gn[k];
+    }
+    LQ_TRY(scale_full(c, p, p, be, nrhs));
+    LQ_TRY(axpy_full(c, p, s, one, nrhs));
+  }
+  inf->iters = it;
   return LQCD_OK;
 }
 
@@ -594,7 +874,10 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   std::vector<double> theta, resid;
   std::vector<int> order;
   double2 *d;
-  int sweep = 0;
+  int sweep = 0, kneed = want;
+  bool fp32_phase = true;
+  double prev_worst = 1e300;
+  lqcd_field *Xs = nullptr, *Ys = nullptr, *Hs = nullptr, *Ts = nullptr, *Zs = nullptr;  // FP32 filter block
   bool converged = false;
   for (;; sweep++) {
     // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
@@ -633,29 +916,55 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     std::vector<double> neg(m), r2;
     for (int i = 0; i < m; i++) neg[i] = -mus[i];
     LQ_TRY(axpy_norms(c, Z, X, neg, m, r2));
+    // converge the wanted vectors and every vector nearly degenerate with the
+    // edge of the wanted set (a near-degenerate +-lambda partner left outside
+    // would stay mixed into a wanted vector)
+    kneed = want;
+    while (kneed < m - 4 && mus[kneed] <= 1.01 * mus[want - 1]) kneed++;
     converged = true;
-    for (int i = 0; i < want; i++) converged &= std::sqrt(r2[i]) <= prm->eig_tol;
+    for (int i = 0; i < kneed; i++) converged &= std::sqrt(r2[i]) <= prm->eig_tol;
     theta = mus;
     if (converged || sweep + 1 >= prm->max_filter) break;
-    // Chebyshev filter of H_W^2 damping [mu_max, bmax]
-    const double lo = std::min(std::max(mus[m - 1], 1.05 * mus[want - 1]), 0.9 * bmax), hi = bmax;
+    // Chebyshev filter of H_W^2 damping [mu_max, bmax], in FP32 while the
+    // residuals are far above the FP32 noise floor, in FP64 afterwards
+    double worst = 0;
+    for (int i = 0; i < kneed; i++) worst = std::max(worst, std::sqrt(r2[i]));
+    // FP32 filtering injects ~1e-7 relative noise: use it only while the
+    // residuals are large and still falling, FP64 from then on
+    if (fp32_phase && (worst < 1e-4 || worst > 0.5 * prev_worst)) fp32_phase = false;
+    prev_worst = worst;
+    const bool low = fp32_phase;
+    const double lo = std::min(std::max(mus[m - 1], 1.02 * mus[kneed - 1]), 0.9 * bmax), hi = bmax;
     const double s2 = 2.0 / (hi - lo), s0 = -(hi + lo) / (hi - lo);
     const int deg = 16;
+    lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T, *fZ = Z;
+    if (low) {
+      if (!Xs) {
+        for (lqcd_field **q : {&Xs, &Ys, &Hs, &Ts, &Zs}) {
+          LQ_TRY(lqcd_field_create(c, LQCD_F32, LQCD_FULL, m, q));
+          g.f.push_back(*q);
+        }
+      }
+      LQ_TRY(convert_full(c, Xs, X, m));
+      fX = Xs, fY = Ys, fH = Hs, fT = Ts, fZ = Zs;
+    }
     // Y0 = X, Y1 = T(X) into Y, Y_{k+1} = 2 T(Y_k) - Y_{k-1}
-    LQ_TRY(hw(c, m, T, X));
-    LQ_TRY(hw(c, m, Z, T));
-    LQ_TRY(clenshaw(c, m, Y, nullptr, Z, X, nullptr, 0.0, 1.0, s2, s0));
-    lqcd_field *prev = X, *cur = Y, *nxt = HX;  // HX is free until the next Rayleigh-Ritz
+    LQ_TRY(hw(c, m, fT, fX));
+    LQ_TRY(hw(c, m, fZ, fT));
+    LQ_TRY(clenshaw(c, m, fY, nullptr, fZ, fX, nullptr, 0.0, 1.0, s2, s0));
+    lqcd_field *prev = fX, *cur = fY, *nxt = fH;
     for (int k = 1; k < deg; k++) {
-      LQ_TRY(hw(c, m, T, cur));
-      LQ_TRY(hw(c, m, Z, T));
-      LQ_TRY(clenshaw(c, m, nxt, nullptr, Z, cur, prev, 0.0, 2.0, s2, s0));
+      LQ_TRY(hw(c, m, fT, cur));
+      LQ_TRY(hw(c, m, fZ, fT));
+      LQ_TRY(clenshaw(c, m, nxt, nullptr, fZ, cur, prev, 0.0, 2.0, s2, s0));
       lqcd_field *t = prev;
       prev = cur;
       cur = nxt;
       nxt = t;
     }
-    if (cur != X) {  // the filtered block becomes X; the other two are scratch
+    if (low) {
+      LQ_TRY(convert_full(c, X, cur, m));
+    } else if (cur != X) {  // the filtered block becomes X; the other two are scratch
       lqcd_field *others[3] = {X, Y, HX};
       lqcd_field *rest[2];
       int r = 0;
@@ -667,33 +976,35 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     }
     LQ_TRY(orthonormalise(c, X, T, m));
   }
-  // Rayleigh-Ritz with H_W in the span of the `want` converged vectors of
-  // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors
+  // Rayleigh-Ritz with H_W in the span of the kneed converged vectors of
+  // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors; the
+  // `want` of smallest |lambda| are kept
   {
-    LQ_TRY(hw(c, want, HX, X));
-    LQ_TRY(small_scratch(c, (size_t)want * want, &d));
-    LQ_TRY(gram(c, X, want, HX, want, d));
+    const int k = kneed;
+    LQ_TRY(hw(c, k, HX, X));
+    LQ_TRY(small_scratch(c, (size_t)k * k, &d));
+    LQ_TRY(gram(c, X, k, HX, k, d));
     std::vector<zc> W, Q;
-    LQ_TRY(to_host(c, d, (size_t)want * want, W));
-    for (int j = 0; j < want; j++)
+    LQ_TRY(to_host(c, d, (size_t)k * k, W));
+    for (int j = 0; j < k; j++)
       for (int i = 0; i < j; i++) {
-        const zc avg = 0.5 * (W[i + (size_t)want * j] + std::conj(W[j + (size_t)want * i]));
-        W[i + (size_t)want * j] = avg;
-        W[j + (size_t)want * i] = std::conj(avg);
+        const zc avg = 0.5 * (W[i + (size_t)k * j] + std::conj(W[j + (size_t)k * i]));
+        W[i + (size_t)k * j] = avg;
+        W[j + (size_t)k * i] = std::conj(avg);
       }
-    jacobi_eigh(want, W, Q, theta);
+    jacobi_eigh(k, W, Q, theta);
     LQ_TRY(to_dev(c, Q, d));
-    LQ_TRY(rotate(c, X, want, d, want, T, 1.0, 0.0));
-    LQ_TRY(rotate(c, HX, want, d, want, Y, 1.0, 0.0));
+    LQ_TRY(rotate(c, X, k, d, k, T, 1.0, 0.0));
+    LQ_TRY(rotate(c, HX, k, d, k, Y, 1.0, 0.0));
     std::swap(X, T);
     std::swap(HX, Y);
-    std::vector<double> neg(want), r2;
-    for (int i = 0; i < want; i++) neg[i] = -theta[i];
-    LQ_TRY(axpy_norms(c, HX, X, neg, want, r2));
-    resid.resize(want);
-    for (int i = 0; i < want; i++) resid[i] = std::sqrt(r2[i]);
-    order.resize(want);
-    for (int i = 0; i < want; i++) order[i] = i;
+    std::vector<double> neg(k), r2;
+    for (int i = 0; i < k; i++) neg[i] = -theta[i];
+    LQ_TRY(axpy_norms(c, HX, X, neg, k, r2));
+    resid.resize(k);
+    for (int i = 0; i < k; i++) resid[i] = std::sqrt(r2[i]);
+    order.resize(k);
+    for (int i = 0; i < k; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int x, int y) { return std::fabs(theta[x]) < std::fabs(theta[y]); });
   }
   inf->sweeps = sweep + 1;
@@ -766,77 +1077,25 @@ extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, 
   } else if (op == LQCD_OV_APPLY || op == LQCD_OV_APPLY_DAG) {
     LQ_TRY(dov_apply(c, nrhs, fin, fout, op == LQCD_OV_APPLY_DAG));
   } else {
-    // CGLS on D_ov: r = b (x0 = 0), s = D^dag r, p = s
-    lqcd_field *r, *s, *p, *q;
-    LQ_TRY(new_full(c, nrhs, &r));
-    g.f.push_back(r);
-    LQ_TRY(new_full(c, nrhs, &s));
-    g.f.push_back(s);
-    LQ_TRY(new_full(c, nrhs, &p));
-    g.f.push_back(p);
+    std::vector<double> bn2;
+    LQ_TRY(field_norms(c, fin, nrhs, bn2));
+    for (int k = 0; k < nrhs; k++)
+      if (!(bn2[k] > 0)) return set_error(LQCD_ERR_ARG, "right-hand side %d is zero", k);
+    if (cg->inner == LQCD_F64) {
+      LQ_TRY(ov_cgls_fp64(c, nrhs, fin, fout, cg, inf, bn2));
+    } else {
+      if (cg->inner != LQCD_F32) return set_error(LQCD_ERR_ARG, "overlap inner precision must be F64 or F32");
+      if (c->ov->nlow > 0 && !c->ov->vecs32) {
+        LQ_TRY(lqcd_field_create(c, LQCD_F32, LQCD_FULL, c->ov->nlow, &c->ov->vecs32));
+        LQ_TRY(convert_full(c, c->ov->vecs32, c->ov->vecs, c->ov->nlow));
+      }
+      LQ_TRY(ov_cgls_mixed(c, nrhs, fin, fout, cg, inf, bn2));
+    }
+    int it = inf->iters;
+    lqcd_field *q;
     LQ_TRY(new_full(c, nrhs, &q));
     g.f.push_back(q);
-    const size_t bytes = (size_t)cwords(fin) * 16 * nrhs;
-    for (int par = 0; par < 2; par++) LQ_CU(cudaMemsetAsync(fout->data[par], 0, bytes, c->stream));
-    LQ_TRY(copy_field(c, r, fin, nrhs));
-    std::vector<double> zero(nrhs, 0.0), bn2, gam, qq, rr;
-    LQ_TRY(axpy_norms(c, fin, fin, zero, nrhs, bn2));
-    LQ_TRY(dov_apply(c, nrhs, r, s, 1));
-    LQ_TRY(copy_field(c, p, s, nrhs));
-    LQ_TRY(axpy_norms(c, s, s, zero, nrhs, gam));
-    std::vector<char> active(nrhs, 1);
-    double *dfac = c->results + 768;
-    auto axpy = [&](lqcd_field *y, const lqcd_field *x, const std::vector<double> &f) -> lqcd_status {
-      LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
-      for (int par = 0; par < 2; par++)
-        LQ_CU(blas_axpy(LQCD_F64, LQCD_F64, c->Vh, nrhs, y->mut(par), x->ref(par), dfac, c->stream));
-      LQ_CU(cudaStreamSynchronize(c->stream));
-      return LQCD_OK;
-    };
-    auto scale = [&](lqcd_field *y, const std::vector<double> &f) -> lqcd_status {
-      LQ_CU(cudaMemcpyAsync(dfac, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream));
-      for (int par = 0; par < 2; par++)
-        LQ_CU(blas_scale(LQCD_F64, LQCD_F64, c->Vh, nrhs, y->mut(par), y->ref(par), dfac, c->stream));
-      LQ_CU(cudaStreamSynchronize(c->stream));
-      return LQCD_OK;
-    };
-    int it = 0;
-    bool all = false;
-    for (; it < cg->max_iter; it++) {
-      LQ_TRY(dov_apply(c, nrhs, p, q, 0));
-      LQ_TRY(axpy_norms(c, q, q, zero, nrhs, qq));
-      std::vector<double> al(nrhs), nal(nrhs);
-      for (int k = 0; k < nrhs; k++) {
-        al[k] = active[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
-        nal[k] = -al[k];
-      }
-      LQ_TRY(axpy(fout, p, al));
-      LQ_TRY(axpy(r, q, nal));
-      LQ_TRY(axpy_norms(c, r, r, zero, nrhs, rr));
-      all = true;
-      for (int k = 0; k < nrhs; k++) {
-        if (!(rr[k] == rr[k])) return set_error(LQCD_ERR_NOCONV, "overlap CG residual is NaN");
-        if (active[k] && rr[k] <= std::pow(0.5 * cg->tol, 2) * bn2[k]) active[k] = 0;
-        all &= !active[k];
-      }
-      if (all) {
-        it++;
-        break;
-      }
-      LQ_TRY(dov_apply(c, nrhs, r, s, 1));
-      std::vector<double> gn;
-      LQ_TRY(axpy_norms(c, s, s, zero, nrhs, gn));
-      std::vector<double> be(nrhs), one(nrhs);
-      for (int k = 0; k < nrhs; k++) {
-        be[k] = active[k] && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
-        one[k] = active[k] ? 1.0 : 0.0;
-        if (active[k]) gam[k] = gn[k];
-      }
-      LQ_TRY(scale(p, be));
-      LQ_TRY(axpy(p, s, one));
-    }
-    inf->iters = it;
-    // true residual b - D_ov x
+    // true residual b - D_ov x, FP64
     LQ_TRY(dov_apply(c, nrhs, fout, q, 0));
     std::vector<double> mone(nrhs, -1.0), res;
     LQ_TRY(axpy_norms(c, fin, q, mone, nrhs, res));

@@ -120,17 +120,20 @@ def test_free_field_closed_form(lib):
     lat.close()
 
 
-def test_overlap_solve(lib):
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_overlap_solve(lib, inner):
     L = lib
     dims = (4, 4, 4, 8)
     U = gen.gauge_field(dims, 0.1, 5)
     m = 0.05
     lat, info, lam, vecs = _setup(L, dims, U, 6, mass=m)
     b = gen.gaussian_spinor(dims, 2005, nrhs=2)
-    cg = L.solve_params(tol=1e-10, max_iter=2000, nrhs=2)
+    cg = L.solve_params(tol=1e-10, max_iter=2000, nrhs=2, inner=L.PREC[inner], delta=0.1)
     x = np.zeros_like(b)
     st, sinfo = L.lqcd_overlap(lat.ctx, x, b, 2, L.LQCD_OV_SOLVE, cg)
     assert st == L.LQCD_OK
+    if inner == "f32":
+        assert sinfo.reliable_updates >= 1
     n, c = oracle.cheb_degree(info.a, info.b, 1e-12)
     for k in range(2):
         r = b[k] - oracle.apply_overlap(dims, U, RHO, m, x[k], info.a, info.b, c, lam=lam, vecs=vecs)
