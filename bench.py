@@ -11,7 +11,8 @@ input spinor, the output spinor, the clover block pair (and the local
 spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
-                  [--no-solve] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
+                  [--no-solve] [--no-batch] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
+  python bench.py --overlap      (overlap set-up and 12-RHS solve on 16^3x32)
 
 --impl reference times the FP64 CPU oracle on the same workload (bounded
 time-slab samples per step).  --kernel-only runs just that kernel (for ncu).
@@ -300,7 +301,7 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
                         ("mixed_bf16", L.LQCD_BF16)):
         xt = torch.zeros_like(bt)
         prm = L.solve_params(tol=1e-10, max_iter=40000, inner=inner, delta=0.1, recon=18, inner_recon=12,
-                             check_every=16)
+                             check_every=0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
@@ -321,6 +322,116 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
         for name, x in xs.items():
             res[name]["true_resid_oracle"] = oracle.true_residual(DIMS, U, A, KAPPA, x, b)
     return res
+
+
+def run_multi_rhs(L, torch, lat, U, want_oracle, oracle_AAi):
+    """Config 4 (i): the 12 spin-colour point sources on the benchmark lattice,
+    mixed precision (FP16 inner), one multi-RHS solve."""
+    import gen
+    b = gen.point_sources(DIMS)
+    bt = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda()
+    xt = torch.zeros_like(bt)
+    prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=12, recon=18, inner_recon=12,
+                         check_every=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    res = {"rhs": "12 point sources at the origin", "inner": "f16", "seconds": wall, "iters": info.iters,
+           "reliable_updates": info.reliable_updates, "mhat_applies": info.mhat_applies,
+           "max_true_resid_gpu_fp64": max(info.true_resid[:12]),
+           "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+    if want_oracle and oracle_AAi is not None:
+        import oracle
+        x = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
+        res["true_resid_oracle_rhs0_rhs11"] = [oracle.true_residual(DIMS, U, oracle_AAi[0], KAPPA, x[k], b[k])
+                                               for k in (0, 11)]
+    return res
+
+
+def run_batch(L, torch, stream):
+    """Config 4 (ii): 24 lattices of uneven volume (8 each of 16^3x32, 20^3x40,
+    24^3x48; eps 0.2, kappa 0.125, c_sw 1.0), 4 Gaussian RHS each, mixed
+    precision, one graph-captured batched solve."""
+    import gen
+    shapes = [(16, 16, 16, 32)] * 8 + [(20, 20, 20, 40)] * 8 + [(24, 24, 24, 48)] * 8
+    lats, bs, xs = [], [], []
+    for j, d in enumerate(shapes):
+        U = gen.gauge_field(d, EPS, 3000 + j)
+        lat = L.Lattice(d, stream=stream)
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(KAPPA, CSW)
+        lats.append(lat)
+        b = torch.from_numpy(gen.gaussian_spinor(d, 4000 + j, nrhs=4).view(np.float64).reshape(-1).copy()).cuda()
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=4, recon=18, inner_recon=12,
+                         check_every=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    sites = sum(int(np.prod(d)) for d in shapes)
+    res = {"lattices": "8 x 16^3x32 + 8 x 20^3x40 + 8 x 24^3x48", "sites": sites, "rhs_per_lattice": 4,
+           "inner": "f16", "seconds": wall, "max_iters": max(i.iters for i in infos),
+           "max_true_resid_gpu_fp64": max(max(i.true_resid[:4]) for i in infos),
+           "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+    for lat in lats:
+        lat.close()
+    return res
+
+
+def run_overlap(args):
+    """Config 5: overlap operator on 16^3x32 (eps 0.1, rho 1.5, m 0.05), 20
+    exact low modes, Chebyshev sign to 1e-10, 12 RHS, mixed-precision CG."""
+    import torch
+    import gen
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(0)
+    dims = (16, 16, 16, 32)
+    U = gen.gauge_field(dims, 0.1, 1005)
+    b = gen.gaussian_spinor(dims, 2005, nrhs=12)
+    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "config": {
+        "workload": "overlap D_ov(m) = rho[1 + g5 sign(H_W)] + ..., 16^3x32, eps 0.1, rho 1.5, m 0.05, 20 low modes, "
+                    "sign to 1e-10, 12 Gaussian RHS, CG on the normal equations with FP32 sign inside and FP64 "
+                    "reliable updates"}}
+    with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
+        lat.load_gauge(U.view(np.float64))
+        prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400)
+        t0 = time.perf_counter()
+        st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
+        out["setup"] = {"seconds": time.perf_counter() - t0, "status": "ok" if st == 0 else L.lqcd_last_error(),
+                        "sweeps": info.sweeps, "degree": info.degree, "a": info.a, "b": info.b,
+                        "sign_error": info.sign_error, "max_eig_resid": max(info.resid[:20]),
+                        "lambda_min_max": [min(abs(v) for v in info.lambda_[:20]),
+                                           max(abs(v) for v in info.lambda_[:20])]}
+        x = np.zeros_like(b)
+        t0 = time.perf_counter()
+        L.lqcd_overlap(lat.ctx, x, b, 12, L.LQCD_OV_APPLY)
+        t_apply = time.perf_counter() - t0
+        out["apply_fp64_12rhs"] = {"seconds": t_apply, "hw_applications": 2 * info.degree + 1,
+                                   "wilson_rhs_applications_per_s": 12 * (2 * info.degree + 1) / t_apply}
+        cg = L.solve_params(tol=1e-10, max_iter=4000, nrhs=12, inner=L.LQCD_F32, delta=0.1)
+        t0 = time.perf_counter()
+        st, si = L.lqcd_overlap(lat.ctx, x, b, 12, L.LQCD_OV_SOLVE, cg, raise_on_noconv=False)
+        out["solve_mixed_12rhs"] = {"seconds": time.perf_counter() - t0, "iters": si.iters,
+                                    "reliable_updates": si.reliable_updates, "status": "ok" if st == 0 else
+                                    L.lqcd_last_error(), "max_true_resid_gpu_fp64": max(si.true_resid[:12])}
+        if not args.no_cpu_baseline:
+            import oracle
+            vecs = np.zeros((20,) + oracle.spinor_shape(dims), dtype=np.complex128)
+            L.lqcd_overlap_lowmodes(lat.ctx, vecs)
+            lam = np.array(info.lambda_[:20])
+            res, ortho = oracle.eigen_residuals(dims, U, 1.5, lam, vecs)
+            out["oracle_eig_resid_max"] = float(res.max())
+            out["oracle_eig_ortho"] = float(ortho)
+            n, c = oracle.cheb_degree(info.a, info.b, 1e-10)
+            r = b[0] - oracle.apply_overlap(dims, U, 1.5, 0.05, x[0], info.a, info.b, c, lam=lam, vecs=vecs)
+            out["oracle_true_resid_rhs0"] = float(np.linalg.norm(r) / np.linalg.norm(b[0]))
+    print(json.dumps(out))
+    return 0
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -419,6 +530,10 @@ def run_gpu(args, rank, world, local_rank):
     solve = None
     if not args.no_solve:
         solve = run_solves(L, torch, lat, U, rank, need_oracle, oracle_AAi)
+    multi = None
+    if not args.no_batch:
+        multi = {"point_sources_32x32x32x64": run_multi_rhs(L, torch, lat, U, need_oracle, oracle_AAi),
+                 "batch_24_lattices": run_batch(L, torch, stream)}
     cpu = None
     if need_oracle:
         rate, nsl, dt = oracle_slab_rate(U, oracle_AAi[0], oracle_AAi[1], psi)
@@ -450,6 +565,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
         "cpu_baseline": cpu,
         "solve": solve,
+        "multi_rhs_and_batch": multi,
     }
     print(json.dumps(line))
     return 0
@@ -463,6 +579,8 @@ def main():
     ap.add_argument("--impl", default="lqcd", choices=["lqcd", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="f32")
@@ -478,6 +596,8 @@ def main():
         return run_reference(args, rank)
     if args.kernel_only:
         return kernel_only(args)
+    if args.overlap:
+        return run_overlap(args) if rank == 0 else 0
     return run_gpu(args, rank, world, local_rank)
 
 

@@ -209,6 +209,21 @@ typedef struct {
 lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device, const lqcd_solve_params *params,
                        lqcd_solve_info *info);
 
+/* Solve several lattices at once (each its own context: geometry, gauge
+ * field, clover term), nrhs right-hand sides each, with the mixed-precision
+ * recursion of lqcd_solve (params->inner must not be LQCD_F64).  Every
+ * lattice runs on a private stream for the duration of the call, and one
+ * segment of params->check_every iterations (rounded up to even) of all
+ * unfinished lattices is captured once into a single CUDA graph (fork/join
+ * across the streams) and replayed; the host checks the residuals between
+ * replays and re-captures when a lattice finishes.  x[i], b[i]: canonical
+ * arrays of lattice i (host or device, all alike); infos: nctx records or
+ * NULL.  The result of each lattice equals lqcd_solve's for the same inputs.
+ * Returns the first failure (LQCD_ERR_NOCONV if a lattice did not converge;
+ * every lattice's x and info are written regardless).  Blocks. */
+lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double *const *x, const double *const *b,
+                             int on_device, const lqcd_solve_params *params, lqcd_solve_info *infos);
+
 /* ---- overlap operator ---------------------------------------------------- */
 
 /* The overlap operator of GWU-code's inverter (abstract; Sec. 3; the overlap

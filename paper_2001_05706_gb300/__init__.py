@@ -90,6 +90,8 @@ _sig = {
     "lqcd_field_norm2": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "lqcd_solve": [_vp, _vp, _vp, _ip, ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_norm2_noalloc": [_vp, ctypes.c_long, _ip, _vp, _vp],
+    "lqcd_solve_batch": [ctypes.POINTER(_vp), _ip, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip,
+                         ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_overlap_setup": [_vp, ctypes.POINTER(lqcd_overlap_params), ctypes.POINTER(lqcd_overlap_info)],
     "lqcd_overlap_lowmodes": [_vp, _vp, _ip],
     "lqcd_overlap": [_vp, _vp, _vp, _ip, _ip, _ip, ctypes.POINTER(lqcd_solve_params),
@@ -227,6 +229,26 @@ def lqcd_solve(ctx, x, b, params: lqcd_solve_params, raise_on_noconv=True):
     if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
         raise LqcdError(st, lqcd_last_error())
     return st, info
+
+
+def lqcd_solve_batch(ctxs, xs, bs, params, raise_on_noconv=True):
+    """Solve lattice i (context ctxs[i]) for xs[i] given bs[i]; returns (status, [info])."""
+    n = len(ctxs)
+    if not (len(xs) == len(bs) == n):
+        raise ValueError("one x and one b per context")
+    bufs_x = [_buf(a) for a in xs]
+    bufs_b = [_buf(a) for a in bs]
+    dev = {d for _, d in bufs_x + bufs_b}
+    if len(dev) != 1:
+        raise ValueError("all buffers must be host or all device")
+    carr = (_vp * n)(*[c.value if isinstance(c, _vp) else c for c in ctxs])
+    xarr = (_vp * n)(*[p.value for p, _ in bufs_x])
+    barr = (_vp * n)(*[p.value for p, _ in bufs_b])
+    infos = (lqcd_solve_info * n)()
+    st = _lib.lqcd_solve_batch(carr, n, xarr, barr, dev.pop(), ctypes.byref(params), infos)
+    if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
+        raise LqcdError(st, lqcd_last_error())
+    return st, list(infos)
 
 
 def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):

@@ -1,6 +1,13 @@
 // Operator layer: the even-odd Wilson-clover operators built from launches
 // of the generic dslash kernel, and the lazily packed link and clover forms
 // they read.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "internal.h"
 
 namespace lqcd {
@@ -73,12 +80,95 @@ lqcd_status ensure_partials(lqcd_ctx *c, int nrhs) {
   return LQCD_OK;
 }
 
-static int pick_nr(lqcd_prec prec, int mode, int nrhs) {
+// ---------------------------------------------------------------------------
+// Autotuner for the number of right-hand sides each thread carries (links
+// and clover loaded once for all of them): on the first launch of a given
+// (precision, link form, mode, nrhs, volume) every admissible choice is timed
+// with CUDA events on the context's stream and the fastest is kept, in memory
+// and, if LQCD_TUNE_CACHE names a file, in that file (one line per entry).
+// Re-running a launch is harmless: the kernel never writes its inputs.
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int, long>;
+static std::map<TuneKey, int> g_tune;
+static std::mutex g_tune_mu;
+static bool g_tune_loaded = false;
+
+static void tune_load() {
+  g_tune_loaded = true;
+  const char *path = std::getenv("LQCD_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return;
+  int a, b, m, n, nr;
+  long v;
+  while (std::fscanf(f, "%d %d %d %d %ld %d", &a, &b, &m, &n, &v, &nr) == 6) g_tune[TuneKey(a, b, m, n, v)] = nr;
+  std::fclose(f);
+}
+
+static void tune_store(const TuneKey &k, int nr) {
+  const char *path = std::getenv("LQCD_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %ld %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+               std::get<4>(k), nr);
+  std::fclose(f);
+}
+
+static int default_nr(lqcd_prec prec, int mode, int nrhs) {
   if (mode == MODE_FOLDED_AINV) return 1;
   if (prec == LQCD_F64) return nrhs % 2 == 0 ? 2 : 1;
   if (nrhs % 4 == 0) return 4;
   if (nrhs % 2 == 0) return 2;
   return 1;
+}
+
+static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon, int mode, int nrhs) {
+  if (mode == MODE_FOLDED_AINV || nrhs == 1) return 1;
+  std::vector<int> cand;
+  for (int nr : {1, 2, 4})
+    if (nrhs % nr == 0) cand.push_back(nr);
+  if (cand.size() == 1) return cand[0];
+  const TuneKey key((int)prec, recon, mode, nrhs, c->Vh);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return default_nr(prec, mode, nrhs);
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return default_nr(prec, mode, nrhs);
+  }
+  int best = default_nr(prec, mode, nrhs);
+  float best_ms = 1e30f;
+  for (int nr : cand) {
+    if (launch_dslash_prec(prec, P, recon, mode, nr, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 3; r++) launch_dslash_prec(prec, P, recon, mode, nr, c->stream);
+    cudaEventRecord(e1, c->stream);
+    float ms = 0;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = nr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  tune_store(key, best);
+  return best;
 }
 
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
@@ -121,7 +211,7 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
     P.norm_result = norm_result;
     P.norm_stride = norm_stride;
   }
-  const int nr = pick_nr(prec, mode, nrhs);
+  const int nr = pick_nr(c, P, prec, recon, mode, nrhs);
   LQ_CU(launch_dslash_prec(prec, P, recon, mode, nr, c->stream));
   return LQCD_OK;
 }

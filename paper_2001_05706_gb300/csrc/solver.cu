@@ -17,7 +17,10 @@
 // operator; the search direction p is kept, rescaled into the new
 // normalisation, and gamma = |Mhat^dag r|^2 recomputed from the new residual;
 // an update that fails to reduce the residual restarts CG from p = s.
+#include <algorithm>
 #include <chrono>
+#include <functional>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -156,133 +159,203 @@ lqcd_status cgls_fp64(Work &W, SolveBufs &B) {
   return all_done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "CG did not converge in %d iterations", W.max_iter);
 }
 
-lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
-  lqcd_ctx *c = W.c;
-  const int n = W.nrhs;
-  const lqcd_prec L = W.lo;
-  lqcd_field *s, *p, *q, *ye, *r, *xlo, *ye64;
-  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 30, &s));
-  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 31, &p));
-  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 32, &q));
-  LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 33, &ye));
-  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 34, &r));
-  LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 35, &xlo));
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 23, &ye64));
-  LQ_TRY(ensure_partials(c, n));
-  std::vector<double> target(n), sigma(n), best_rr(n, 1.0);
-  std::vector<int> stall(n, 0);
-  for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
-  const double delta2 = W.delta * W.delta;
-  // an inner residual that has not halved over kStallChecks checks is
+// Mixed-precision CGLS as a resumable state machine: init() once, then
+// enqueue(k) launches k iterations without any host synchronisation (so a
+// batch of lattices can be captured into one CUDA graph), advance(k) books
+// them, and check() reads the residuals and performs a reliable update when
+// one is due.
+struct MixedCG {
+  Work &W;
+  SolveBufs &B;
+  lqcd_ctx *c;
+  int n;
+  lqcd_prec L;
+  lqcd_field *s = nullptr, *p = nullptr, *q = nullptr, *ye = nullptr, *r = nullptr, *xlo = nullptr, *ye64 = nullptr;
+  lqcd_field *xbest = nullptr, *xtry = nullptr, *rtry = nullptr;
+  std::vector<double> target, sigma, best_rr, ref_rr;
+  std::vector<int> stall;
+  std::vector<char> grown;
+  double delta2 = 0;
+  size_t xlo_bytes = 0, rhs_bytes64 = 0, rhs_bytes32 = 0;
+  int cur = 0, it = 0;
+  bool done = false;
+  // an inner residual that has not halved over kStallIters iterations is
   // stagnating at the precision floor of the storage type: force an update
-  constexpr int kStallChecks = 3;
-  const size_t xlo_bytes = (size_t)xlo->rhs_words() * 16 * n;
+  static constexpr int kStallIters = 48;
+  int last_it = 0;
 
-  // r64 = bhat - Mhat64 x64 -> sigma
-  LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
-                 &B.sc[0].aux, kScStride));
-  W.info->mhat_applies += 1;
-  LQ_TRY(read_scalars(c, B, n));
-  int nactive = 0;
-  for (int k = 0; k < n; k++) {
-    sigma[k] = std::sqrt(B.h_sc[k].aux);
-    B.h_sc[k].active = sigma[k] > target[k] ? 1.0 : 0.0;
-    nactive += B.h_sc[k].active != 0.0;
-    B.h_fac[k] = sigma[k] > 0 ? 1.0 / sigma[k] : 0.0;
-    B.h_sc[k].rr = 1.0;
-  }
-  if (nactive == 0) {
-    W.info->iters = 0;
+  MixedCG(Work &w, SolveBufs &b) : W(w), B(b), c(w.c), n(w.nrhs), L(w.lo) {}
+
+  lqcd_status init() {
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 30, &s));
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 31, &p));
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 32, &q));
+    LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 33, &ye));
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 34, &r));
+    LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 35, &xlo));
+    LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 36, &xbest));
+    LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 37, &xtry));
+    LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 38, &rtry));
+    LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 23, &ye64));
+    LQ_TRY(ensure_partials(c, n));
+    target.assign(n, 0.0);
+    sigma.assign(n, 0.0);
+    best_rr.assign(n, 1.0);
+    ref_rr.assign(n, 1.0);
+    stall.assign(n, 0);
+    grown.assign(n, 0);
+    for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
+    delta2 = W.delta * W.delta;
+    rhs_bytes32 = (size_t)xlo->rhs_words() * 16;
+    rhs_bytes64 = (size_t)xtry->rhs_words() * 16;
+    xlo_bytes = rhs_bytes32 * n;
+    // r64 = bhat - Mhat64 x64 -> sigma
+    LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
+                   &B.sc[0].aux, kScStride));
+    W.info->mhat_applies += 1;
+    LQ_TRY(read_scalars(c, B, n));
+    int nactive = 0;
+    for (int k = 0; k < n; k++) {
+      sigma[k] = std::sqrt(B.h_sc[k].aux);
+      B.h_sc[k].active = sigma[k] > target[k] ? 1.0 : 0.0;
+      nactive += B.h_sc[k].active != 0.0;
+      B.h_fac[k] = sigma[k] > 0 ? 1.0 / sigma[k] : 0.0;
+      B.h_sc[k].rr = 1.0;
+    }
+    if (nactive == 0) {
+      done = true;
+      return LQCD_OK;
+    }
+    LQ_TRY(write_scalars(c, B, n));
+    LQ_TRY(write_fac(c, B, n));
+    // r_lo = r64 / sigma ; x_lo = x_best = 0 ; s = Mhat^dag r ; p = s
+    LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
+    LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
+    LQ_CU(cudaMemsetAsync(xbest->data[1], 0, xlo_bytes, c->stream));
+    cur = 0;
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
+                   kScStride));
+    LQ_CU(cudaMemcpyAsync(p->data[1], s->data[1], (size_t)p->rhs_words() * 16 * n, cudaMemcpyDeviceToDevice,
+                          c->stream));
+    if (p->scale[1])
+      LQ_CU(cudaMemcpyAsync(p->scale[1], s->scale[1], sizeof(float) * c->Vh * n, cudaMemcpyDeviceToDevice, c->stream));
+    W.info->mhat_applies += 1;
+    // pack the inner links/clover and fill the tuning cache before any capture
+    LQ_CU(cudaStreamSynchronize(c->stream));
     return LQCD_OK;
   }
-  LQ_TRY(write_scalars(c, B, n));
-  LQ_TRY(write_fac(c, B, n));
-  // r_lo = r64 / sigma ; x_lo = 0 ; s = Mhat^dag r ; p = s
-  LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
-  LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
-  int cur = 0;
-  LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur], kScStride));
-  LQ_CU(cudaMemcpyAsync(p->data[1], s->data[1], (size_t)p->rhs_words() * 16 * n, cudaMemcpyDeviceToDevice, c->stream));
-  if (p->scale[1])
-    LQ_CU(cudaMemcpyAsync(p->scale[1], s->scale[1], sizeof(float) * c->Vh * n, cudaMemcpyDeviceToDevice, c->stream));
-  W.info->mhat_applies += 1;
 
-  int it = 0;
-  bool done = false;
-  while (!done) {
-    if (it >= W.max_iter) break;
-    for (int j = 0; j < W.check_every && it < W.max_iter; j++, it++) {
+  // k CG iterations starting at the current ping-pong index; no host sync
+  lqcd_status enqueue(int k) const {
+    int cc = cur;
+    for (int j = 0; j < k; j++) {
       LQ_TRY(op_mhat(c, L, W.recon_lo, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
-      LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, cur, c->partials,
+      LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, cc, c->partials,
                        c->counter, c->stream));
-      LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cur],
+      LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cc],
                      kScStride));
-      LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, cur, c->stream));
-      cur ^= 1;
-      W.info->mhat_applies += 2;
+      LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, cc, c->stream));
+      cc ^= 1;
     }
+    return LQCD_OK;
+  }
+
+  void advance(int k) {
+    it += k;
+    if (k & 1) cur ^= 1;
+    W.info->mhat_applies += 2.0 * k;
+  }
+
+  char *rhs_ptr(lqcd_field *f, int k, size_t bytes) const { return static_cast<char *>(f->data[1]) + bytes * k; }
+
+  lqcd_status check() {
     LQ_TRY(read_scalars(c, B, n));
-    // trigger: every active RHS dropped by delta, or one reached its target,
-    // or one stagnates
-    bool all_dropped = true, any_target = false, any_stall = false;
+    // keep the best inner iterate (smallest iterated residual); trigger an
+    // update when every active RHS dropped by delta, one reached its target,
+    // one stagnates, or one grew past twice its best (low-precision noise
+    // makes CG diverge on ill-conditioned systems)
+    bool all_dropped = true, any_target = false, any_stall = false, any_grow = false;
     for (int k = 0; k < n; k++) {
       if (B.h_sc[k].active == 0.0) continue;
       const double rr = B.h_sc[k].rr;
       if (!(rr == rr)) return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
-      if (rr > delta2) all_dropped = false;
-      if (sigma[k] * std::sqrt(rr) <= target[k]) any_target = true;
-      if (rr < 0.25 * best_rr[k]) {
+      if (rr < best_rr[k]) {
         best_rr[k] = rr;
+        LQ_CU(cudaMemcpyAsync(rhs_ptr(xbest, k, rhs_bytes32), rhs_ptr(xlo, k, rhs_bytes32), rhs_bytes32,
+                              cudaMemcpyDeviceToDevice, c->stream));
+      }
+      if (rr < 0.25 * ref_rr[k]) {
+        ref_rr[k] = rr;
         stall[k] = 0;
-      } else if (++stall[k] >= kStallChecks) {
+      } else if ((stall[k] += it - last_it) >= kStallIters) {
         any_stall = true;
       }
+      if (rr > 4.0 * best_rr[k]) {
+        grown[k] = 1;
+        any_grow = true;
+      }
+      if (best_rr[k] > delta2) all_dropped = false;
+      if (sigma[k] * std::sqrt(best_rr[k]) <= target[k]) any_target = true;
     }
-    if (!(all_dropped || any_target || any_stall || it >= W.max_iter)) continue;
+    last_it = it;
+    if (!(all_dropped || any_target || any_stall || any_grow || it >= W.max_iter)) return LQCD_OK;
 
-    // ---- reliable update: x64 += sigma x_lo ; r64 = bhat - Mhat64 x64
+    // ---- reliable update with the best inner iterate, accepted only if it
+    // lowers the FP64 residual: x_try = x64 + sigma x_best, r_try = bhat - Mhat64 x_try
     for (int k = 0; k < n; k++) B.h_fac[k] = B.h_sc[k].active != 0.0 ? sigma[k] : 0.0;
     LQ_TRY(write_fac(c, B, n));
-    LQ_CU(blas_axpy(LQCD_F64, LQCD_F32, c->Vh, n, W.x64->mut(1), xlo->ref(1), B.fac, c->stream));
-    LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
-    LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
+    LQ_CU(cudaMemcpyAsync(xtry->data[1], W.x64->data[1], rhs_bytes64 * n, cudaMemcpyDeviceToDevice, c->stream));
+    LQ_CU(blas_axpy(LQCD_F64, LQCD_F32, c->Vh, n, xtry->mut(1), xbest->ref(1), B.fac, c->stream));
+    LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, rtry->mut(1), xtry->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
                    &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
     W.info->reliable_updates += 1;
     LQ_TRY(read_scalars(c, B, n));
     done = true;
     for (int k = 0; k < n; k++) {
-      if (B.h_sc[k].active == 0.0) {
-        B.h_fac[k] = 0.0;
-        continue;
-      }
+      B.h_fac[k] = 0.0;
+      B.h_fac[n + k] = 0.0;
+      B.h_fac[2 * n + k] = 0.0;
+      if (B.h_sc[k].active == 0.0) continue;
       const double snew = std::sqrt(B.h_sc[k].aux);
       if (kTrace)
-        std::fprintf(stderr, "lqcd: update %d it %d rhs %d inner |r| %.3e  FP64 |r| %.6e -> %.6e (target %.3e)\n",
-                     W.info->reliable_updates, it, k, std::sqrt(B.h_sc[k].rr), sigma[k], snew, target[k]);
+        std::fprintf(stderr,
+                     "lqcd: update %d it %d rhs %d inner |r| %.3e best %.3e  FP64 |r| %.6e -> %.6e (target %.3e)\n",
+                     W.info->reliable_updates, it, k, std::sqrt(B.h_sc[k].rr), std::sqrt(best_rr[k]), sigma[k], snew,
+                     target[k]);
       if (!(snew == snew) || std::isinf(snew))
         return set_error(LQCD_ERR_NOCONV, "FP64 residual of RHS %d is not finite", k);
-      if (snew <= target[k]) {
-        B.h_sc[k].active = 0.0;
-        B.h_fac[k] = 0.0;
-        continue;
+      const bool accept = snew < sigma[k];
+      if (accept) {
+        LQ_CU(cudaMemcpyAsync(rhs_ptr(W.x64, k, rhs_bytes64), rhs_ptr(xtry, k, rhs_bytes64), rhs_bytes64,
+                              cudaMemcpyDeviceToDevice, c->stream));
+        LQ_CU(cudaMemcpyAsync(rhs_ptr(W.r64, k, rhs_bytes64), rhs_ptr(rtry, k, rhs_bytes64), rhs_bytes64,
+                              cudaMemcpyDeviceToDevice, c->stream));
+        if (snew <= target[k]) {
+          B.h_sc[k].active = 0.0;
+          continue;
+        }
       }
       done = false;
       // p (the next search direction) is kept, rescaled into the new
-      // normalisation r_lo = r64 / snew, unless this update failed to reduce
-      // the residual: then CG restarts from p = s (low-precision noise has
-      // spoilt the conjugacy of p)
-      const bool restart = snew >= sigma[k] || stall[k] >= kStallChecks;
-      stall[k] = 0;
-      best_rr[k] = 1.0;
-      B.h_fac[k] = restart ? 0.0 : sigma[k] / snew;
+      // normalisation r_lo = r64 / snew, only if the update used the current
+      // iterate and improved; otherwise CG restarts from p = s
+      const bool restart = !accept || grown[k] || stall[k] >= kStallIters || best_rr[k] < B.h_sc[k].rr;
+      const double snext = accept ? snew : sigma[k];
+      B.h_fac[k] = restart ? 0.0 : sigma[k] / snext;
+      B.h_fac[n + k] = 1.0 / snext;
       B.h_fac[2 * n + k] = restart ? 1.0 : 0.0;
       B.h_sc[k].rr = 1.0;
-      sigma[k] = snew;
+      sigma[k] = snext;
+      best_rr[k] = 1.0;
+      ref_rr[k] = 1.0;
+      stall[k] = 0;
+      grown[k] = 0;
     }
-    if (done) break;
+    LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
+    LQ_CU(cudaMemsetAsync(xbest->data[1], 0, xlo_bytes, c->stream));
+    if (done) return LQCD_OK;
     // factors: p *= fac[0, n); r = r64 * fac[n, 2n); p += fac[2n, 3n) s
-    for (int k = 0; k < n; k++) B.h_fac[n + k] = B.h_sc[k].active != 0.0 ? 1.0 / sigma[k] : 0.0;
     LQ_TRY(write_scalars(c, B, n));
     LQ_TRY(write_fac(c, B, 3 * n));
     LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
@@ -291,21 +364,45 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
                    kScStride));
     LQ_CU(blas_axpy(L, L, c->Vh, n, p->mut(1), s->ref(1), B.fac + 2 * n, c->stream));
     W.info->mhat_applies += 1;
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
   }
-  W.info->iters = it;
-  return done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "mixed CG did not converge in %d iterations", W.max_iter);
+};
+
+lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
+  MixedCG m(W, B);
+  LQ_TRY(m.init());
+  while (!m.done && m.it < W.max_iter) {
+    const int k = std::min(W.check_every, W.max_iter - m.it);
+    LQ_TRY(m.enqueue(k));
+    m.advance(k);
+    LQ_TRY(m.check());
+  }
+  W.info->iters = m.it;
+  return m.done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "mixed CG did not converge in %d iterations", W.max_iter);
 }
 
-}  // namespace
+// One solve: staging, even-odd source, the recursion, reconstruction and the
+// FP64 true residual.  Split so that a batch of lattices can share the loop.
+struct SolveJob {
+  lqcd_ctx *c = nullptr;
+  double *x = nullptr;
+  const double *b = nullptr;
+  int on_device = 0;
+  lqcd_solve_params prm{};
+  lqcd_solve_info *inf = nullptr;
+  lqcd_solve_info local{};
+  SolveBufs B;
+  Work W;
+  lqcd_field *bf = nullptr, *xf = nullptr, *bhat = nullptr, *r64 = nullptr, *tmpe = nullptr;
+  double *dx = nullptr;
+  size_t nd = 0;
+  std::chrono::steady_clock::time_point t0;
+};
 
-}  // namespace lqcd
-
-using namespace lqcd;
-
-extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int on_device,
-                                  const lqcd_solve_params *prm, lqcd_solve_info *info) {
+lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
   if (!c) return set_error(LQCD_ERR_ARG, "context is NULL");
-  if (!x || !b || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!prm) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (!(prm->tol > 0.0)) return set_error(LQCD_ERR_ARG, "tol must be > 0");
   if (prm->max_iter < 1) return set_error(LQCD_ERR_ARG, "max_iter must be >= 1");
   if (prm->nrhs < 1 || prm->nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
@@ -314,20 +411,22 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
     return set_error(LQCD_ERR_ARG, "delta must be in (0, 1)");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
-  const int recon64 = prm->recon == 12 ? 12 : 18;
   const int recon_lo = prm->inner_recon == 18 ? 18 : 12;
-  if (prec_half(prm->inner) && recon_lo != 12) {
-    return set_error(LQCD_ERR_ARG, "FP16/BF16 inner solves need 12-real links");
-  }
-  const auto t0 = std::chrono::steady_clock::now();
-  lqcd_solve_info local{};
-  lqcd_solve_info *inf = info ? info : &local;
+  if (prec_half(prm->inner) && recon_lo != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 inner solves need 12-real links");
+  return LQCD_OK;
+}
+
+lqcd_status job_prepare(SolveJob &J) {
+  lqcd_ctx *c = J.c;
+  const lqcd_solve_params *prm = &J.prm;
+  J.t0 = std::chrono::steady_clock::now();
+  J.inf = J.inf ? J.inf : &J.local;
+  lqcd_solve_info *inf = J.inf;
   std::memset(inf, 0, sizeof(*inf));
   const int n = prm->nrhs;
   inf->nrhs = n;
-  const size_t nd = (size_t)n * c->V * 24;
-
-  SolveBufs B;
+  J.nd = (size_t)n * c->V * 24;
+  SolveBufs &B = J.B;
   if (cudaMalloc(&B.sc, sizeof(SolverScalars) * n) != cudaSuccess ||
       cudaMalloc(&B.fac, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMallocHost(&B.h_sc, sizeof(SolverScalars) * n) != cudaSuccess ||
@@ -340,91 +439,230 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
     B.h_sc[k].active = 1.0;
   }
   LQ_CU(cudaMemcpyAsync(B.sc, B.h_sc, sizeof(SolverScalars) * n, cudaMemcpyHostToDevice, c->stream));
-
   // stage b (and x0) on the device
-  const double *db = b;
-  const double *dx0 = x;
-  double *dx = x;
-  if (!on_device) {
+  const double *db = J.b;
+  const double *dx0 = J.x;
+  J.dx = J.x;
+  if (!J.on_device) {
     double *d0, *d1;
-    LQ_TRY(staging(c, 0, nd, &d0));
-    LQ_TRY(staging(c, 1, nd, &d1));
-    LQ_CU(cudaMemcpyAsync(d0, b, nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (prm->use_x0) LQ_CU(cudaMemcpyAsync(d1, x, nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LQ_TRY(staging(c, 0, J.nd, &d0));
+    LQ_TRY(staging(c, 1, J.nd, &d1));
+    LQ_CU(cudaMemcpyAsync(d0, J.b, J.nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (prm->use_x0) LQ_CU(cudaMemcpyAsync(d1, J.x, J.nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     db = d0;
     dx0 = d1;
-    dx = d1;
+    J.dx = d1;
   }
-  lqcd_field *bf, *xf, *bhat, *r64, *tmpe;
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_FULL, n, 10, &bf));
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_FULL, n, 11, &xf));
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 12, &bhat));
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 13, &r64));
-  LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 14, &tmpe));
+  LQ_TRY(temp_field(c, LQCD_F64, LQCD_FULL, n, 10, &J.bf));
+  LQ_TRY(temp_field(c, LQCD_F64, LQCD_FULL, n, 11, &J.xf));
+  LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 12, &J.bhat));
+  LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 13, &J.r64));
+  LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 14, &J.tmpe));
   for (int p = 0; p < 2; p++)
-    LQ_CU(pack_spinor(LQCD_F64, c->geom, p, db, n, bf->data[p], nullptr, bf->rhs_words(), c->stream));
+    LQ_CU(pack_spinor(LQCD_F64, c->geom, p, db, n, J.bf->data[p], nullptr, J.bf->rhs_words(), c->stream));
   if (prm->use_x0)
-    LQ_CU(pack_spinor(LQCD_F64, c->geom, 1, dx0, n, xf->data[1], nullptr, xf->rhs_words(), c->stream));
+    LQ_CU(pack_spinor(LQCD_F64, c->geom, 1, dx0, n, J.xf->data[1], nullptr, J.xf->rhs_words(), c->stream));
   else
-    LQ_CU(cudaMemsetAsync(xf->data[1], 0, (size_t)xf->rhs_words() * 16 * n, c->stream));
-
-  Work W;
+    LQ_CU(cudaMemsetAsync(J.xf->data[1], 0, (size_t)J.xf->rhs_words() * 16 * n, c->stream));
+  Work &W = J.W;
   W.c = c;
   W.nrhs = n;
-  W.recon64 = recon64;
-  W.recon_lo = recon_lo;
+  W.recon64 = prm->recon == 12 ? 12 : 18;
+  W.recon_lo = prm->inner_recon == 18 ? 18 : 12;
   W.lo = prm->inner;
   W.tol = prm->tol;
   W.delta = prm->delta;
   W.max_iter = prm->max_iter;
-  W.check_every = prm->check_every > 0 ? prm->check_every : 8;
+  // check often with 16-bit storage: its inner solves can turn round quickly
+  W.check_every = prm->check_every > 0 ? prm->check_every : (prec_half(prm->inner) ? 4 : 8);
   W.info = inf;
   W.bnorm.assign(n, 0.0);
   {
     std::vector<double> e(n), o(n);
-    LQ_TRY(norms(c, LQCD_F64, n, bf->ref(0), e.data()));
-    LQ_TRY(norms(c, LQCD_F64, n, bf->ref(1), o.data()));
+    LQ_TRY(norms(c, LQCD_F64, n, J.bf->ref(0), e.data()));
+    LQ_TRY(norms(c, LQCD_F64, n, J.bf->ref(1), o.data()));
     for (int k = 0; k < n; k++) W.bnorm[k] = std::sqrt(e[k] + o[k]);
   }
   for (int k = 0; k < n; k++)
     if (!(W.bnorm[k] > 0.0)) return set_error(LQCD_ERR_ARG, "right-hand side %d is zero or not finite", k);
-  LQ_TRY(op_prepare(c, LQCD_F64, recon64, n, bhat->mut(1), bf->ref(0), bf->ref(1), tmpe->mut(0)));
-  W.bhat = bhat;
-  W.x64 = xf;
-  W.r64 = r64;
+  LQ_TRY(op_prepare(c, LQCD_F64, W.recon64, n, J.bhat->mut(1), J.bf->ref(0), J.bf->ref(1), J.tmpe->mut(0)));
+  W.bhat = J.bhat;
+  W.x64 = J.xf;
+  W.r64 = J.r64;
+  return LQCD_OK;
+}
 
-  lqcd_status st;
-  if (prm->inner == LQCD_F64) {
-    st = cgls_fp64(W, B);
-  } else {
-    st = cgls_mixed(W, B);
-  }
-  lqcd_status solve_status = st;
+lqcd_status job_finish(SolveJob &J, lqcd_status solve_status) {
+  lqcd_ctx *c = J.c;
+  const int n = J.prm.nrhs;
+  lqcd_solve_info *inf = J.inf;
+  const int recon64 = J.W.recon64;
   // reconstruct x_e, then the FP64 full-lattice residual b - M x
-  LQ_TRY(op_reconstruct(c, LQCD_F64, recon64, n, xf->mut(0), bf->ref(0), xf->ref(1)));
+  LQ_TRY(op_reconstruct(c, LQCD_F64, recon64, n, J.xf->mut(0), J.bf->ref(0), J.xf->ref(1)));
   {
     lqcd_field *rf;
     LQ_TRY(temp_field(c, LQCD_F64, LQCD_FULL, n, 15, &rf));
     MutField o[2] = {rf->mut(0), rf->mut(1)};
-    FieldRef xr[2] = {xf->ref(0), xf->ref(1)};
-    FieldRef zr[2] = {bf->ref(0), bf->ref(1)};
+    FieldRef xr[2] = {J.xf->ref(0), J.xf->ref(1)};
+    FieldRef zr[2] = {J.bf->ref(0), J.bf->ref(1)};
     LQ_TRY(op_M(c, LQCD_F64, recon64, 0, n, o, xr, zr, -1.0, nullptr, 0));
     std::vector<double> e(n), od(n);
     LQ_TRY(norms(c, LQCD_F64, n, rf->ref(0), e.data()));
     LQ_TRY(norms(c, LQCD_F64, n, rf->ref(1), od.data()));
     bool ok = true;
     for (int k = 0; k < n; k++) {
-      const double rel = std::sqrt(e[k] + od[k]) / W.bnorm[k];
+      const double rel = std::sqrt(e[k] + od[k]) / J.W.bnorm[k];
       if (k < 64) inf->true_resid[k] = rel;
-      if (!(rel <= prm->tol)) ok = false;
+      if (!(rel <= J.prm.tol)) ok = false;
     }
     if (solve_status == LQCD_OK && !ok)
       solve_status = set_error(LQCD_ERR_NOCONV, "true residual above tol after convergence of the iterated one");
   }
   for (int p = 0; p < 2; p++)
-    LQ_CU(unpack_spinor(LQCD_F64, c->geom, p, xf->data[p], nullptr, xf->rhs_words(), n, dx, c->stream));
-  if (!on_device) LQ_CU(cudaMemcpyAsync(x, dx, nd * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(unpack_spinor(LQCD_F64, c->geom, p, J.xf->data[p], nullptr, J.xf->rhs_words(), n, J.dx, c->stream));
+  if (!J.on_device) LQ_CU(cudaMemcpyAsync(J.x, J.dx, J.nd * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LQ_CU(cudaStreamSynchronize(c->stream));
-  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - J.t0).count();
   return solve_status;
+}
+
+}  // namespace
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int on_device,
+                                  const lqcd_solve_params *prm, lqcd_solve_info *info) {
+  LQ_TRY(check_params(c, prm));
+  if (!x || !b) return set_error(LQCD_ERR_ARG, "NULL argument");
+  SolveJob J;
+  J.c = c;
+  J.x = x;
+  J.b = b;
+  J.on_device = on_device;
+  J.prm = *prm;
+  J.inf = info;
+  LQ_TRY(job_prepare(J));
+  const lqcd_status st = prm->inner == LQCD_F64 ? cgls_fp64(J.W, J.B) : cgls_mixed(J.W, J.B);
+  return job_finish(J, st);
+}
+
+// Several lattices at once: every lattice runs on its own stream, and one
+// segment of `check_every` iterations of all of them is captured once into a
+// CUDA graph (fork/join across the streams) and replayed; the host checks the
+// residuals between replays and re-captures when a lattice has finished.
+extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double *const *x, const double *const *b,
+                                        int on_device, const lqcd_solve_params *prm, lqcd_solve_info *infos) {
+  if (!ctxs || !x || !b || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (nctx < 1 || nctx > 256) return set_error(LQCD_ERR_ARG, "nctx must be in 1..256");
+  if (prm->inner == LQCD_F64) return set_error(LQCD_ERR_ARG, "batched solves run the mixed-precision recursion");
+  for (int i = 0; i < nctx; i++) {
+    LQ_TRY(check_params(ctxs[i], prm));
+    if (!x[i] || !b[i]) return set_error(LQCD_ERR_ARG, "NULL buffer for lattice %d", i);
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) return set_error(LQCD_ERR_ARG, "lattice %d repeats a context", i);
+  }
+  // private non-blocking streams for the duration of the call
+  std::vector<cudaStream_t> saved(nctx), own(nctx, nullptr);
+  cudaStream_t root = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join(nctx, nullptr);
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (int i = 0; i < nctx; i++) {
+      if (own[i]) {
+        cudaStreamSynchronize(own[i]);
+        ctxs[i]->stream = saved[i];
+        cudaStreamDestroy(own[i]);
+      }
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (root) cudaStreamDestroy(root);
+  };
+  struct Guard {
+    std::function<void()> f;
+    ~Guard() { f(); }
+  } guard{cleanup};
+  LQ_CU(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+  LQ_CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (int i = 0; i < nctx; i++) {
+    LQ_CU(cudaStreamSynchronize(ctxs[i]->stream));
+    saved[i] = ctxs[i]->stream;
+    LQ_CU(cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking));
+    ctxs[i]->stream = own[i];
+    LQ_CU(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+  }
+  std::vector<std::unique_ptr<SolveJob>> jobs(nctx);
+  std::vector<std::unique_ptr<MixedCG>> cgs(nctx);
+  for (int i = 0; i < nctx; i++) {
+    jobs[i].reset(new SolveJob());
+    SolveJob &J = *jobs[i];
+    J.c = ctxs[i];
+    J.x = x[i];
+    J.b = b[i];
+    J.on_device = on_device;
+    J.prm = *prm;
+    J.inf = infos ? &infos[i] : nullptr;
+    LQ_TRY(job_prepare(J));
+    cgs[i].reset(new MixedCG(J.W, J.B));
+    LQ_TRY(cgs[i]->init());
+  }
+  const int seg = std::max(2, (jobs[0]->W.check_every + 1) & ~1);  // even: the ping-pong index returns
+  std::vector<int> active_prev;
+  while (true) {
+    std::vector<int> active;
+    for (int i = 0; i < nctx; i++)
+      if (!cgs[i]->done && cgs[i]->it < prm->max_iter) active.push_back(i);
+    if (active.empty()) break;
+    if (active != active_prev || !exec) {
+      if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      LQ_CU(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
+      lqcd_status st = LQCD_OK;
+      if (cudaEventRecord(fork, root) != cudaSuccess) st = set_error(LQCD_ERR_CUDA, "event record in capture");
+      for (int i : active) {
+        if (st != LQCD_OK) break;
+        if (cudaStreamWaitEvent(ctxs[i]->stream, fork, 0) != cudaSuccess) {
+          st = set_error(LQCD_ERR_CUDA, "stream wait in capture");
+          break;
+        }
+        st = cgs[i]->enqueue(seg);
+        if (st == LQCD_OK && (cudaEventRecord(join[i], ctxs[i]->stream) != cudaSuccess ||
+                              cudaStreamWaitEvent(root, join[i], 0) != cudaSuccess))
+          st = set_error(LQCD_ERR_CUDA, "join in capture");
+      }
+      const cudaError_t ec = cudaStreamEndCapture(root, &graph);
+      if (st != LQCD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ec != cudaSuccess) return set_error(LQCD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) return set_error(LQCD_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+      active_prev = active;
+    }
+    LQ_CU(cudaGraphLaunch(exec, root));
+    LQ_CU(cudaStreamSynchronize(root));
+    for (int i : active) {
+      cgs[i]->advance(seg);
+      LQ_TRY(cgs[i]->check());
+    }
+  }
+  lqcd_status result = LQCD_OK;
+  for (int i = 0; i < nctx; i++) {
+    jobs[i]->inf->iters = cgs[i]->it;
+    const lqcd_status st =
+        cgs[i]->done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "lattice %d did not converge in %d iterations", i,
+                                           prm->max_iter);
+    const lqcd_status fs = job_finish(*jobs[i], st);
+    if (fs != LQCD_OK && result == LQCD_OK) result = fs;
+  }
+  return result;
 }

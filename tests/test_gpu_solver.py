@@ -102,3 +102,33 @@ def test_noconv_reports(lib):
     assert st == lib.LQCD_ERR_NOCONV
     assert info.iters == 3 and info.true_resid[0] > 1e-10
     lat.close()
+
+
+def test_batch_of_uneven_lattices(lib):
+    """Three lattices of different volumes in one graph-captured batch: each
+    reaches 1e-10 (oracle) and equals the single-lattice solve bitwise."""
+    L = lib
+    dims_list = [(4, 4, 4, 8), (6, 4, 4, 8), (8, 4, 6, 4)]
+    kappa, csw = 0.125, 1.0
+    lats, Us, bs = [], [], []
+    for j, dims in enumerate(dims_list):
+        U = gen.gauge_field(dims, 0.2, 3000 + j)
+        lat = L.Lattice(dims)
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(kappa, csw)
+        lats.append(lat)
+        Us.append(U)
+        bs.append(np.ascontiguousarray(gen.gaussian_spinor(dims, 4000 + j, nrhs=2)))
+    xs = [np.zeros_like(b) for b in bs]
+    prm = L.solve_params(tol=1e-10, inner=L.LQCD_F16, nrhs=2, check_every=8)
+    st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm)
+    assert st == L.LQCD_OK
+    for j, dims in enumerate(dims_list):
+        A = oracle.clover(dims, Us[j], kappa, csw)
+        for k in range(2):
+            assert oracle.true_residual(dims, Us[j], A, kappa, xs[j][k], bs[j][k]) <= 1e-10
+        x1 = np.zeros_like(bs[j])
+        st1, info1 = L.lqcd_solve(lats[j].ctx, x1, bs[j], prm)
+        assert np.array_equal(x1, xs[j]) and info1.iters == infos[j].iters
+    for lat in lats:
+        lat.close()
