@@ -79,6 +79,23 @@ __device__ __forceinline__ void load_spinor(const FieldRef &f, long Vh, int r, l
     for (int c = 0; c < 3; c++) psi[a][c] = mk<T>(sc * (T)to_f(raw[6 * a + 2 * c]), sc * (T)to_f(raw[6 * a + 2 * c + 1]));
 }
 
+// The same load without applying the FP16/BF16 scale: returns it instead, so
+// callers can fold it into an FMA they do anyway.
+template <typename S>
+__device__ __forceinline__ typename Math<S>::T load_spinor_raw(const FieldRef &f, long Vh, int r, long i,
+                                                               cx<typename Math<S>::T> (&psi)[4][3]) {
+  using T = typename Math<S>::T;
+  S raw[24];
+  load_reals<S, 24>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
+  T sc = (T)1;
+  if (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+  return sc;
+}
+
 template <typename S>
 __device__ __forceinline__ void store_spinor(void *base, float *scale, long rhs_words, long Vh, int r, long i,
                                              const cx<typename Math<S>::T> (&psi)[4][3]) {
@@ -120,11 +137,14 @@ template <> __device__ __forceinline__ void store_spinor<double>(void *base, flo
 }
 
 // Link U_mu at site i of one parity; 12-real form rebuilds row 2 = conj(row0 x row1).
+#ifndef LQCD_LINK_STREAM
+#define LQCD_LINK_STREAM true
+#endif
 template <typename S, int R>
 __device__ __forceinline__ void load_link(const void *base, long Vh, long i, cx<typename Math<S>::T> (&U)[3][3]) {
   using T = typename Math<S>::T;
   S raw[R];
-  load_reals<S, R, true>(base, Vh, i, raw);
+  load_reals<S, R, LQCD_LINK_STREAM>(base, Vh, i, raw);
 #pragma unroll
   for (int k = 0; k < R / 6; k++)
 #pragma unroll
@@ -159,8 +179,8 @@ __device__ __forceinline__ void herm6_mul(const T (&m)[36], const cx<T> (&v)[6],
 // Clover storage of one parity: two blocks of 36 reals, block-major,
 // [blk][words][Vh], plus one FP32 scale per site for FP16/BF16.
 template <typename S>
-__device__ __forceinline__ void load_clover_block(const void *base, const float *scale, long Vh, long i, int blk,
-                                                  typename Math<S>::T (&m)[36]) {
+__device__ __forceinline__ typename Math<S>::T load_clover_block(const void *base, const float *scale, long Vh,
+                                                                 long i, int blk, typename Math<S>::T (&m)[36]) {
   using T = typename Math<S>::T;
   using Wd = Words<S, 36>;
   S raw[36];
@@ -169,10 +189,12 @@ __device__ __forceinline__ void load_clover_block(const void *base, const float 
   T sc = (T)1;
   if (IsHalf<S>::value) sc = (T)__ldg(scale + i);
 #pragma unroll
-  for (int k = 0; k < 36; k++) m[k] = sc * (T)to_f(raw[k]);
+  for (int k = 0; k < 36; k++) m[k] = (T)to_f(raw[k]);
+  return sc;  // the FP16/BF16 scale, applied to the products by the caller
 }
 
-// out = M psi with M = diag(block+, block-) acting on (spins 0,1) and (2,3).
+// out = M psi with M = diag(block+, block-) acting on (spins 0,1) and (2,3);
+// the storage scale multiplies the 6 outputs of each block, not its 36 entries
 template <typename S, int NR>
 __device__ __forceinline__ void clover_apply(const void *base, const float *scale, long Vh, long i,
                                              cx<typename Math<S>::T> (&psi)[NR][4][3]) {
@@ -180,7 +202,7 @@ __device__ __forceinline__ void clover_apply(const void *base, const float *scal
 #pragma unroll
   for (int blk = 0; blk < 2; blk++) {
     T m[36];
-    load_clover_block<S>(base, scale, Vh, i, blk, m);
+    const T sc = load_clover_block<S>(base, scale, Vh, i, blk, m);
 #pragma unroll
     for (int r = 0; r < NR; r++) {
       cx<T> v[6], o[6];
@@ -188,7 +210,7 @@ __device__ __forceinline__ void clover_apply(const void *base, const float *scal
       for (int k = 0; k < 6; k++) v[k] = psi[r][2 * blk + k / 3][k % 3];
       herm6_mul<T>(m, v, o);
 #pragma unroll
-      for (int k = 0; k < 6; k++) psi[r][2 * blk + k / 3][k % 3] = o[k];
+      for (int k = 0; k < 6; k++) psi[r][2 * blk + k / 3][k % 3] = IsHalf<S>::value ? sc * o[k] : o[k];
     }
   }
 }
@@ -221,28 +243,31 @@ __device__ __forceinline__ void project(int mu, T s, const cx<T> (&p)[4][3], cx<
   }
 }
 
+// acc += f * reconstruct(h): f folds the storage scale of the neighbour and
+// the boundary sign into the FMAs of the accumulation
 template <typename T>
-__device__ __forceinline__ void reconstruct(int mu, T s, const cx<T> (&h)[2][3], cx<T> (&acc)[4][3]) {
+__device__ __forceinline__ void reconstruct(int mu, T s, T f, const cx<T> (&h)[2][3], cx<T> (&acc)[4][3]) {
+  const T fs = f * s;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    acc[0][c] = acc[0][c] + h[0][c];
-    acc[1][c] = acc[1][c] + h[1][c];
+    acc[0][c] = mk<T>(fma(f, h[0][c].r, acc[0][c].r), fma(f, h[0][c].i, acc[0][c].i));
+    acc[1][c] = mk<T>(fma(f, h[1][c].r, acc[1][c].r), fma(f, h[1][c].i, acc[1][c].i));
     switch (mu) {
-      case 0:  // s B^dag h, B^dag = [[0, -i], [-i, 0]]
-        acc[2][c] = acc[2][c] - s * times_i(h[1][c]);
-        acc[3][c] = acc[3][c] - s * times_i(h[0][c]);
+      case 0:  // s B^dag h, B^dag = [[0, -i], [-i, 0]]: lower0 -= s i h1, lower1 -= s i h0
+        acc[2][c] = mk<T>(fma(fs, h[1][c].i, acc[2][c].r), fma(-fs, h[1][c].r, acc[2][c].i));
+        acc[3][c] = mk<T>(fma(fs, h[0][c].i, acc[3][c].r), fma(-fs, h[0][c].r, acc[3][c].i));
         break;
-      case 1:  // B^dag = [[0, 1], [-1, 0]]
-        acc[2][c] = acc[2][c] + s * h[1][c];
-        acc[3][c] = acc[3][c] - s * h[0][c];
+      case 1:  // B^dag = [[0, 1], [-1, 0]]: lower0 += s h1, lower1 -= s h0
+        acc[2][c] = mk<T>(fma(fs, h[1][c].r, acc[2][c].r), fma(fs, h[1][c].i, acc[2][c].i));
+        acc[3][c] = mk<T>(fma(-fs, h[0][c].r, acc[3][c].r), fma(-fs, h[0][c].i, acc[3][c].i));
         break;
-      case 2:  // B^dag = [[-i, 0], [0, i]]
-        acc[2][c] = acc[2][c] - s * times_i(h[0][c]);
-        acc[3][c] = acc[3][c] + s * times_i(h[1][c]);
+      case 2:  // B^dag = [[-i, 0], [0, i]]: lower0 -= s i h0, lower1 += s i h1
+        acc[2][c] = mk<T>(fma(fs, h[0][c].i, acc[2][c].r), fma(-fs, h[0][c].r, acc[2][c].i));
+        acc[3][c] = mk<T>(fma(-fs, h[1][c].i, acc[3][c].r), fma(fs, h[1][c].r, acc[3][c].i));
         break;
-      default:
-        acc[2][c] = acc[2][c] + s * h[0][c];
-        acc[3][c] = acc[3][c] + s * h[1][c];
+      default:  // B^dag = 1
+        acc[2][c] = mk<T>(fma(fs, h[0][c].r, acc[2][c].r), fma(fs, h[0][c].i, acc[2][c].i));
+        acc[3][c] = mk<T>(fma(fs, h[1][c].r, acc[3][c].r), fma(fs, h[1][c].i, acc[3][c].i));
         break;
     }
   }
@@ -265,8 +290,42 @@ __device__ __forceinline__ void link_mul(const cx<T> (&U)[3][3], bool dag, const
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
+// Launch shape per storage type: threads per block and the minimum number
+// of resident blocks per SM promised to the register allocator.  The kernel
+// is latency-bound (long-scoreboard stalls dominate), so more resident warps
+// pay as long as the register cap causes no spills.
+#ifndef LQCD_T64
+#define LQCD_T64 128
+#endif
+#ifndef LQCD_M64
+#define LQCD_M64 1
+#endif
+#ifndef LQCD_T32
+#define LQCD_T32 64
+#endif
+#ifndef LQCD_M32
+#define LQCD_M32 10
+#endif
+#ifndef LQCD_T16
+#define LQCD_T16 64
+#endif
+#ifndef LQCD_M16
+#define LQCD_M16 16
+#endif
+// Kernels carrying several right-hand sides per thread need their registers:
+// they keep 128 threads and no cap.
+template <typename S, int NR> struct LaunchCfg {
+  static constexpr int threads = NR > 1 ? 128 : LQCD_T16, min_blocks = NR > 1 ? 1 : LQCD_M16;
+};
+template <int NR> struct LaunchCfg<float, NR> {
+  static constexpr int threads = NR > 1 ? 128 : LQCD_T32, min_blocks = NR > 1 ? 1 : LQCD_M32;
+};
+template <int NR> struct LaunchCfg<double, NR> {
+  static constexpr int threads = NR > 1 ? 128 : LQCD_T64, min_blocks = NR > 1 ? 1 : LQCD_M64;
+};
+
 template <typename S, int R, int MODE, int NR>
-__global__ void __launch_bounds__(128) dslash_kernel(const __grid_constant__ DslashParams P) {
+__global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::min_blocks) dslash_kernel(const __grid_constant__ DslashParams P) {
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int rg = blockIdx.y;  // right-hand-side group
@@ -304,7 +363,8 @@ __global__ void __launch_bounds__(128) dslash_kernel(const __grid_constant__ Dsl
 #pragma unroll
           for (int r = 0; r < NR; r++) {
             cx<T> psi[4][3];
-            load_spinor<S>(P.in, P.g.Vh, rg * NR + r, n, psi);
+            T f = load_spinor_raw<S>(P.in, P.g.Vh, rg * NR + r, n, psi);
+            if (wrap) f = -f;
             if (P.g5_in) {
 #pragma unroll
               for (int c = 0; c < 3; c++) {
@@ -315,13 +375,7 @@ __global__ void __launch_bounds__(128) dslash_kernel(const __grid_constant__ Dsl
             cx<T> hh[2][3], uh[2][3];
             project<T>(mu, s, psi, hh);
             link_mul<T>(U, dir < 0, hh, uh);
-            if (wrap) {
-#pragma unroll
-              for (int a = 0; a < 2; a++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) uh[a][c] = (T)-1 * uh[a][c];
-            }
-            reconstruct<T>(mu, s, uh, acc[r]);
+            reconstruct<T>(mu, s, f, uh, acc[r]);
           }
         }
       }

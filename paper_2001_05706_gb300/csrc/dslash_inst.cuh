@@ -6,12 +6,11 @@
 
 namespace lqcd {
 
-constexpr int kDslashThreads = 128;
-
 template <typename S, int R, int MODE, int NR>
 static cudaError_t launch_one(const DslashParams &P, cudaStream_t st) {
-  dim3 grid((unsigned)((P.g.Vh + kDslashThreads - 1) / kDslashThreads), (unsigned)(P.nrhs / NR));
-  dslash_kernel<S, R, MODE, NR><<<grid, kDslashThreads, 0, st>>>(P);
+  constexpr int T = LaunchCfg<S, NR>::threads;
+  dim3 grid((unsigned)((P.g.Vh + T - 1) / T), (unsigned)(P.nrhs / NR));
+  dslash_kernel<S, R, MODE, NR><<<grid, T, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,8 @@ lqcd_status get_clover(lqcd_ctx *c, lqcd_prec prec, CloverStore **cs) {
 }
 
 lqcd_status ensure_partials(lqcd_ctx *c, int nrhs) {
-  const size_t need = (size_t)((c->Vh + 127) / 128 + 1) * (size_t)(nrhs < 1 ? 1 : nrhs);
+  // one partial per block and quantity; blocks have at least 32 threads
+  const size_t need = (size_t)((c->Vh + 31) / 32 + 1) * (size_t)(nrhs < 1 ? 1 : nrhs);
   if (need <= c->partials_n) return LQCD_OK;
   if (c->partials) {
     LQ_CU(cudaStreamSynchronize(c->stream));
