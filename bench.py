@@ -13,6 +13,7 @@ spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
                   [--no-solve] [--no-batch] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
   python bench.py --overlap      (overlap set-up and 12-RHS solve on 16^3x32)
+  python bench.py --solve-lattice 48,48,48,96   (mixed vs FP64 solve only, on that lattice)
 
 --impl reference times the FP64 CPU oracle on the same workload (bounded
 time-slab samples per step).  --kernel-only runs just that kernel (for ncu).
@@ -142,6 +143,22 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_gbs(bytes_per_rank_step, ms, world):
+    """Whole-job GB/s of a weak-scaled step: every rank moves the same bytes and
+    the step takes the slowest rank's time."""
+    return world * bytes_per_rank_step / (ms * 1e-3) / 1e9
 
 
 def gpu_index(local_rank):
@@ -383,6 +400,26 @@ def run_batch(L, torch, stream):
     return res
 
 
+def run_solve_only(args):
+    """Mixed vs FP64 solve comparison on another lattice (config 3: 48^3x96)."""
+    global DIMS
+    import torch
+    import gen
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(0)
+    DIMS = tuple(int(v) for v in args.solve_lattice.split(","))
+    U = gen.gauge_field(DIMS, EPS, GAUGE_SEED)
+    oracle_AAi = None if args.no_cpu_baseline else oracle_setup(U)
+    with L.Lattice(DIMS, stream=torch.cuda.current_stream()) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(KAPPA, CSW)
+        res = run_solves(L, torch, lat, U, 0, oracle_AAi is not None, oracle_AAi)
+    print(json.dumps({"metric": "mixed vs FP64 solve time to 1e-10", "config": {
+        "workload": f"Wilson-clover even-odd CG, {'x'.join(map(str, DIMS))}, c_sw=1.0, kappa=0.125, eps 0.2, "
+                    f"one Gaussian RHS"}, "solve": res}))
+    return 0
+
+
 def run_overlap(args):
     """Config 5: overlap operator on 16^3x32 (eps 0.1, rho 1.5, m 0.05), 20
     exact low modes, Chebyshev sign to 1e-10, 12 RHS, mixed-precision CG."""
@@ -473,9 +510,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     # per-kernel launch durations (same stream, events around K launches)
     k2a_ms = time_ms(torch, lambda: L.lqcd_apply(ctx, L.LQCD_OP_K2A, 12, fy, fx), args.steps, stream)
     k2b_ms = time_ms(torch, lambda: L.lqcd_apply_schur(ctx, 12, 0, fz, fx, fy), args.steps, stream)
@@ -484,7 +519,7 @@ def run_gpu(args, rank, world, local_rank):
         L.lqcd_field_destroy(f)
 
     peak, peak_src = load_peaks()
-    gbs = world * Vh * mhat_bytes("f32", 12) / (ms * 1e-3) / 1e9
+    gbs = weak_gbs(Vh * mhat_bytes("f32", 12), ms, world)
     k2a_gbs = Vh * site_bytes("f32", 12, "k2a") / (k2a_ms * 1e-3) / 1e9
     k2b_gbs = Vh * site_bytes("f32", 12, "k2b") / (k2b_ms * 1e-3) / 1e9
     dom = "k2b" if k2b_ms >= k2a_ms else "k2a"
@@ -519,6 +554,8 @@ def run_gpu(args, rank, world, local_rank):
         L.lqcd_dslash(ctx, hout, hin, 1, L.LQCD_OP_MHAT, L.LQCD_F32, 12)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     nbytes = hin.numel() * 8
     e2e = {"value": world * Vh * mhat_bytes("f32", 12) / e2e_s / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s * 1e3,
@@ -528,10 +565,10 @@ def run_gpu(args, rank, world, local_rank):
     need_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
     oracle_AAi = oracle_setup(U) if need_oracle else None
     solve = None
-    if not args.no_solve:
+    if not args.no_solve and world == 1:
         solve = run_solves(L, torch, lat, U, rank, need_oracle, oracle_AAi)
     multi = None
-    if not args.no_batch:
+    if not args.no_batch and world == 1:
         multi = {"point_sources_32x32x32x64": run_multi_rhs(L, torch, lat, U, need_oracle, oracle_AAi),
                  "batch_24_lattices": run_batch(L, torch, stream)}
     cpu = None
@@ -581,6 +618,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
+    ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="f32")
@@ -598,6 +636,8 @@ def main():
         return kernel_only(args)
     if args.overlap:
         return run_overlap(args) if rank == 0 else 0
+    if args.solve_lattice:
+        return run_solve_only(args) if rank == 0 else 0
     return run_gpu(args, rank, world, local_rank)
 
 
