@@ -184,7 +184,8 @@ typedef struct {
   int use_x0;          /* 1: x holds an initial guess on entry                     */
   lqcd_recon recon;    /* link storage of the FP64 operator                        */
   lqcd_recon inner_recon; /* link storage of the inner low-precision operator      */
-  int check_every;     /* iterations between host convergence checks (0: 8)        */
+  int check_every;     /* FP64 CG: iterations between host checks (0: 8); the     */
+                       /* mixed solver checks every iteration on the device       */
 } lqcd_solve_params;
 
 typedef struct {
@@ -201,9 +202,10 @@ typedef struct {
  * CG on the normal equations of Mhat x_o = bhat_o (CGLS form, one
  * independent recursion per right-hand side), then
  * x_e = A_ee^-1 (b_e + kappa D_eo x_o).  With params->inner != LQCD_F64 the
- * CG runs with low-precision storage and FP32 arithmetic, and the solution
- * is accumulated, and the residual recomputed, in FP64 whenever the inner
- * residual fell by `delta` (reliable updates).  Returns LQCD_OK only after
+ * CG runs with low-precision storage and FP32 arithmetic inside a CUDA graph
+ * conditional WHILE loop that a device-side control kernel ends when an update
+ * is due, and the solution is accumulated, and the residual recomputed, in
+ * FP64 whenever the inner residual fell by `delta` (reliable updates).  Returns LQCD_OK only after
  * the FP64 full-lattice residual of every RHS is <= tol; LQCD_ERR_NOCONV
  * with info filled and x the last iterate otherwise.  Blocks. */
 lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device, const lqcd_solve_params *params,
@@ -212,11 +214,11 @@ lqcd_status lqcd_solve(lqcd_ctx *ctx, double *x, const double *b, int on_device,
 /* Solve several lattices at once (each its own context: geometry, gauge
  * field, clover term), nrhs right-hand sides each, with the mixed-precision
  * recursion of lqcd_solve (params->inner must not be LQCD_F64).  Every
- * lattice runs on a private stream for the duration of the call, and one
- * segment of params->check_every iterations (rounded up to even) of all
- * unfinished lattices is captured once into a single CUDA graph (fork/join
- * across the streams) and replayed; the host checks the residuals between
- * replays and re-captures when a lattice finishes.  x[i], b[i]: canonical
+ * lattice runs on a private stream for the duration of the call; the inner
+ * iterations of all unfinished lattices form one CUDA graph with one
+ * conditional WHILE node per lattice, whose loop runs on the GPU until that
+ * lattice needs an FP64 reliable update; the host performs the updates
+ * between launches and rebuilds the graph when a lattice finishes.  x[i], b[i]: canonical
  * arrays of lattice i (host or device, all alike); infos: nctx records or
  * NULL.  The result of each lattice equals lqcd_solve's for the same inputs.
  * Returns the first failure (LQCD_ERR_NOCONV if a lattice did not converge;

@@ -3,6 +3,7 @@
 // device-resident fields.  Declarations and their contracts: include/lqcd.h.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -19,8 +20,27 @@ lqcd_status set_error(lqcd_status s, const char *fmt, ...) {
   return s;
 }
 
+// Every device allocation of the library goes through dev_malloc.  For
+// failure-injection tests, LQCD_FAULT_ALLOC_AFTER=N makes every allocation
+// after the N-th one (counted from the first use of this variable) fail as if
+// the device were out of memory; nothing touches the GPU.
+static long g_fault_after = -2;  // -2: not read yet, -1: no fault injection
+static long g_alloc_count = 0;
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (g_fault_after == -2) {
+    const char *e = std::getenv("LQCD_FAULT_ALLOC_AFTER");
+    g_fault_after = e ? std::atol(e) : -1;
+  }
+  if (g_fault_after >= 0 && ++g_alloc_count > g_fault_after) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 static lqcd_status alloc_dev(void **p, size_t bytes, const char *what) {
-  if (cudaMalloc(p, bytes) != cudaSuccess) {
+  if (dev_malloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return set_error(LQCD_ERR_OOM, "cannot allocate %zu bytes for %s", bytes, what);

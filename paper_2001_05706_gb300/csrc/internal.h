@@ -119,9 +119,11 @@ struct lqcd_ctx {
   lqcd::OverlapState *ov = nullptr;
 };
 
-// ---- errors (abi.cu)
+// ---- errors and allocation (abi.cu)
 namespace lqcd {
 lqcd_status set_error(lqcd_status s, const char *fmt, ...);
+// cudaMalloc with the failure-injection hook (LQCD_FAULT_ALLOC_AFTER)
+cudaError_t dev_malloc(void **p, size_t bytes);
 }
 #define LQ_CU(call)                                                                                      \
   do {                                                                                                   \

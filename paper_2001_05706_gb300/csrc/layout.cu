@@ -215,13 +215,17 @@ __global__ void su3_check_kernel(const double *__restrict__ U, long nlinks, unsi
         cx<double> t = mk<double>(i == j ? -1.0 : 0.0, 0.0);
 #pragma unroll
         for (int c = 0; c < 3; c++) t = cjmadd(m[j][c], m[i][c], t);  // sum_c m_ic conj(m_jc)
-        e = fmax(e, fmax(fabs(t.r), fabs(t.i)));
+        const double d = fmax(fabs(t.r), fabs(t.i));
+        if (!(d <= e)) e = d;  // keeps a NaN (fmax would drop it)
       }
     cx<double> det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
                      m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
                      m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
-    e = fmax(e, fmax(fabs(det.r - 1.0), fabs(det.i)));
-    if (!(e == e)) e = 1e300;  // NaN counts as failure
+    const double dd = fmax(fabs(det.r - 1.0), fabs(det.i));
+    if (!(dd <= e)) e = dd;
+    for (int i = 0; i < 18; i++)
+      if (!(u[i] == u[i]) || fabs(u[i]) > 1e300) e = 1e300;  // NaN or Inf entries count as failure
+    if (!(e == e)) e = 1e300;
   }
   for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
   if ((threadIdx.x & 31) == 0) atomicMax(worst, (unsigned long long)__double_as_longlong(e));

@@ -23,7 +23,7 @@ lqcd_status get_links(lqcd_ctx *c, lqcd_prec prec, int recon, const void **base)
     return LQCD_OK;
   }
   void *p = nullptr;
-  if (cudaMalloc(&p, link_bytes(prec, recon, c->Vh)) != cudaSuccess) {
+  if (dev_malloc(&p, link_bytes(prec, recon, c->Vh)) != cudaSuccess) {
     cudaGetLastError();
     return set_error(LQCD_ERR_OOM, "cannot allocate packed links");
   }
@@ -40,7 +40,7 @@ lqcd_status get_clover(lqcd_ctx *c, lqcd_prec prec, CloverStore **cs) {
     const size_t nb = clover_bytes(prec, c->Vh);
     const size_t ns = prec_half(prec) ? sizeof(float) * c->Vh : 0;
     char *p = nullptr;
-    if (cudaMalloc(&p, 4 * (nb + ns)) != cudaSuccess) {
+    if (dev_malloc((void **)&p, 4 * (nb + ns)) != cudaSuccess) {
       cudaGetLastError();
       return set_error(LQCD_ERR_OOM, "cannot allocate clover storage");
     }
@@ -72,7 +72,7 @@ lqcd_status ensure_partials(lqcd_ctx *c, int nrhs) {
     cudaFree(c->partials);
     c->partials = nullptr;
   }
-  if (cudaMalloc(&c->partials, need * sizeof(double)) != cudaSuccess) {
+  if (dev_malloc((void **)&c->partials, need * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     c->partials_n = 0;
     return set_error(LQCD_ERR_OOM, "cannot allocate reduction scratch");

@@ -193,7 +193,7 @@ lqcd_status small_scratch(lqcd_ctx *c, size_t n, double2 **p) {
       cudaFree(s.dsmall);
       s.dsmall = nullptr;
     }
-    LQ_CU(cudaMalloc(&s.dsmall, n * sizeof(double2)));
+    LQ_CU(dev_malloc((void **)&s.dsmall, n * sizeof(double2)));
     s.dsmall_n = n;
   }
   *p = s.dsmall;
@@ -1080,7 +1080,8 @@ extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, 
     std::vector<double> bn2;
     LQ_TRY(field_norms(c, fin, nrhs, bn2));
     for (int k = 0; k < nrhs; k++)
-      if (!(bn2[k] > 0)) return set_error(LQCD_ERR_ARG, "right-hand side %d is zero", k);
+      if (!(bn2[k] > 0) || !std::isfinite(bn2[k]))
+        return set_error(LQCD_ERR_ARG, "right-hand side %d is zero or not finite", k);
     if (cg->inner == LQCD_F64) {
       LQ_TRY(ov_cgls_fp64(c, nrhs, fin, fout, cg, inf, bn2));
     } else {

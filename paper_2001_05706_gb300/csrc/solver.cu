@@ -9,14 +9,17 @@
 //   repeat: q = Mhat p; alpha = gamma/|q|^2; x += alpha p; r -= alpha q;
 //           s = Mhat^dag r; gamma' = |s|^2; p = s + (gamma'/gamma) p
 // with every scalar kept in device memory (no host round trip inside an
-// iteration); the host reads the residual norms every `check_every`
+// iteration).  FP64 CG: the host reads the residual norms every `check_every`
 // iterations.  Mixed precision: r, p, q, s in FP32/FP16/BF16 storage and
 // FP32 arithmetic, x_lo in FP32, normalised so the inner residual starts at
-// norm 1; when it has fallen below delta (or reaches the target) the FP64
+// norm 1; the inner loop runs in a CUDA graph conditional WHILE node until a
+// device-side control kernel finds an update due (the inner residual fell
+// below delta, reached the target, stagnated or turned round); then the FP64
 // solution absorbs x_lo and the residual is recomputed with the FP64
-// operator; the search direction p is kept, rescaled into the new
-// normalisation, and gamma = |Mhat^dag r|^2 recomputed from the new residual;
-// an update that fails to reduce the residual restarts CG from p = s.
+// operator, the update being kept only if it lowers that residual; the search
+// direction p is kept, rescaled into the new normalisation, and
+// gamma = |Mhat^dag r|^2 recomputed from the new residual, or CG restarts
+// from p = s after a rejected update or a turn-round.
 #include <algorithm>
 #include <chrono>
 #include <functional>
@@ -159,11 +162,80 @@ lqcd_status cgls_fp64(Work &W, SolveBufs &B) {
   return all_done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "CG did not converge in %d iterations", W.max_iter);
 }
 
-// Mixed-precision CGLS as a resumable state machine: init() once, then
-// enqueue(k) launches k iterations without any host synchronisation (so a
-// batch of lattices can be captured into one CUDA graph), advance(k) books
-// them, and check() reads the residuals and performs a reliable update when
-// one is due.
+// ---------------------------------------------------------------------------
+// Device-side loop control of the mixed-precision inner CG.
+//
+// The inner iterations run inside a CUDA graph conditional WHILE node: its
+// body is one CG iteration followed by cg_control_kernel, which reads the new
+// iterated residuals, updates per-RHS trigger state (best and reference
+// residual, stagnation count, growth) and sets the loop condition.  The loop
+// stops when a reliable update is due -- every active RHS dropped by delta, or
+// one reached its target, stagnated for kStallIters iterations, or grew 20 %
+// past its best -- or when the iteration cap of this launch is reached, so it
+// always terminates.  The control kernel also moves the new gamma into the
+// slot the next iteration reads, which makes the body the same every time.
+// ---------------------------------------------------------------------------
+constexpr int kStallIters = 48;
+
+struct CtrlRhs {
+  double best, ref, sigma, target;
+  int stall, grown, pad0, pad1;
+};
+struct CtrlGlobal {
+  int it, cap, stop, pad;
+  double delta2;
+};
+
+__global__ void cg_control_kernel(SolverScalars *sc, CtrlRhs *cr, CtrlGlobal *cg, int n,
+                                  cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ int all_dropped, any_trigger, nactive;
+  const int k = threadIdx.x;
+  if (k == 0) {
+    all_dropped = 1;
+    any_trigger = 0;
+    nactive = 0;
+  }
+  __syncthreads();
+  if (k < n) {
+    sc[k].gamma[0] = sc[k].gamma[1];
+    if (sc[k].active != 0.0) {
+      atomicAdd(&nactive, 1);
+      const double rr = sc[k].rr;
+      CtrlRhs c = cr[k];
+      if (!(rr == rr)) {
+        c.grown = 1;
+        any_trigger = 1;
+      } else {
+        if (rr < c.best) c.best = rr;
+        if (rr < 0.25 * c.ref) {
+          c.ref = rr;
+          c.stall = 0;
+        } else if (++c.stall >= kStallIters) {
+          any_trigger = 1;
+        }
+        if (rr > 1.44 * c.best) {
+          c.grown = 1;
+          any_trigger = 1;
+        }
+        if (c.sigma * sqrt(c.best) <= c.target) any_trigger = 1;
+      }
+      if (!(c.best <= cg->delta2)) all_dropped = 0;
+      cr[k] = c;
+    }
+  }
+  __syncthreads();
+  if (k == 0) {
+    const int it = cg->it + 1;
+    cg->it = it;
+    const int stop = (nactive == 0) || any_trigger || all_dropped || it >= cg->cap;
+    cg->stop = stop;
+    if (use_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
+  }
+}
+
+// Mixed-precision CGLS as a resumable state machine: init() once, then the
+// inner loop runs on the device (a graph with a WHILE node, see run_graph),
+// and update() performs the reliable update the loop stopped for.
 struct MixedCG {
   Work &W;
   SolveBufs &B;
@@ -171,20 +243,44 @@ struct MixedCG {
   int n;
   lqcd_prec L;
   lqcd_field *s = nullptr, *p = nullptr, *q = nullptr, *ye = nullptr, *r = nullptr, *xlo = nullptr, *ye64 = nullptr;
-  lqcd_field *xbest = nullptr, *xtry = nullptr, *rtry = nullptr;
-  std::vector<double> target, sigma, best_rr, ref_rr;
-  std::vector<int> stall;
-  std::vector<char> grown;
+  lqcd_field *xtry = nullptr, *rtry = nullptr;
+  std::vector<double> target, sigma;
   double delta2 = 0;
-  size_t xlo_bytes = 0, rhs_bytes64 = 0, rhs_bytes32 = 0;
-  int cur = 0, it = 0;
+  size_t xlo_bytes = 0, rhs_bytes64 = 0;
+  int it = 0;
   bool done = false;
-  // an inner residual that has not halved over kStallIters iterations is
-  // stagnating at the precision floor of the storage type: force an update
-  static constexpr int kStallIters = 48;
-  int last_it = 0;
+  CtrlRhs *dcr = nullptr, *hcr = nullptr;
+  CtrlGlobal *dcg = nullptr, *hcg = nullptr;
 
   MixedCG(Work &w, SolveBufs &b) : W(w), B(b), c(w.c), n(w.nrhs), L(w.lo) {}
+  ~MixedCG() {
+    if (dcr) cudaFree(dcr);
+    if (dcg) cudaFree(dcg);
+    if (hcr) cudaFreeHost(hcr);
+    if (hcg) cudaFreeHost(hcg);
+  }
+
+  lqcd_status upload_ctrl() {
+    LQ_CU(cudaMemcpyAsync(dcr, hcr, sizeof(CtrlRhs) * n, cudaMemcpyHostToDevice, c->stream));
+    LQ_CU(cudaMemcpyAsync(dcg, hcg, sizeof(CtrlGlobal), cudaMemcpyHostToDevice, c->stream));
+    return LQCD_OK;
+  }
+
+  lqcd_status download_ctrl() {
+    LQ_CU(cudaMemcpyAsync(hcr, dcr, sizeof(CtrlRhs) * n, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaMemcpyAsync(hcg, dcg, sizeof(CtrlGlobal), cudaMemcpyDeviceToHost, c->stream));
+    LQ_TRY(read_scalars(c, B, n));
+    return LQCD_OK;
+  }
+
+  void reset_rhs(int k) {
+    hcr[k].best = 1.0;
+    hcr[k].ref = 1.0;
+    hcr[k].stall = 0;
+    hcr[k].grown = 0;
+    hcr[k].sigma = sigma[k];
+    hcr[k].target = target[k];
+  }
 
   lqcd_status init() {
     LQ_TRY(temp_field(c, L, LQCD_ODD, n, 30, &s));
@@ -193,22 +289,23 @@ struct MixedCG {
     LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 33, &ye));
     LQ_TRY(temp_field(c, L, LQCD_ODD, n, 34, &r));
     LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 35, &xlo));
-    LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 36, &xbest));
     LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 37, &xtry));
     LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 38, &rtry));
     LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 23, &ye64));
     LQ_TRY(ensure_partials(c, n));
+    if (dev_malloc((void **)&dcr, sizeof(CtrlRhs) * n) != cudaSuccess ||
+        dev_malloc((void **)&dcg, sizeof(CtrlGlobal)) != cudaSuccess ||
+        cudaMallocHost(&hcr, sizeof(CtrlRhs) * n) != cudaSuccess ||
+        cudaMallocHost(&hcg, sizeof(CtrlGlobal)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(LQCD_ERR_OOM, "cannot allocate solver control state");
+    }
     target.assign(n, 0.0);
     sigma.assign(n, 0.0);
-    best_rr.assign(n, 1.0);
-    ref_rr.assign(n, 1.0);
-    stall.assign(n, 0);
-    grown.assign(n, 0);
     for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
     delta2 = W.delta * W.delta;
-    rhs_bytes32 = (size_t)xlo->rhs_words() * 16;
     rhs_bytes64 = (size_t)xtry->rhs_words() * 16;
-    xlo_bytes = rhs_bytes32 * n;
+    xlo_bytes = (size_t)xlo->rhs_words() * 16 * n;
     // r64 = bhat - Mhat64 x64 -> sigma
     LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
                    &B.sc[0].aux, kScStride));
@@ -221,91 +318,83 @@ struct MixedCG {
       nactive += B.h_sc[k].active != 0.0;
       B.h_fac[k] = sigma[k] > 0 ? 1.0 / sigma[k] : 0.0;
       B.h_sc[k].rr = 1.0;
+      std::memset(&hcr[k], 0, sizeof(CtrlRhs));
+      reset_rhs(k);
     }
+    std::memset(hcg, 0, sizeof(CtrlGlobal));
+    hcg->delta2 = delta2;
     if (nactive == 0) {
       done = true;
       return LQCD_OK;
     }
     LQ_TRY(write_scalars(c, B, n));
     LQ_TRY(write_fac(c, B, n));
-    // r_lo = r64 / sigma ; x_lo = x_best = 0 ; s = Mhat^dag r ; p = s
+    // r_lo = r64 / sigma ; x_lo = 0 ; s = Mhat^dag r -> gamma[0] ; p = s
     LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
     LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
-    LQ_CU(cudaMemsetAsync(xbest->data[1], 0, xlo_bytes, c->stream));
-    cur = 0;
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
                    kScStride));
     LQ_CU(cudaMemcpyAsync(p->data[1], s->data[1], (size_t)p->rhs_words() * 16 * n, cudaMemcpyDeviceToDevice,
                           c->stream));
     if (p->scale[1])
       LQ_CU(cudaMemcpyAsync(p->scale[1], s->scale[1], sizeof(float) * c->Vh * n, cudaMemcpyDeviceToDevice, c->stream));
     W.info->mhat_applies += 1;
-    // pack the inner links/clover and fill the tuning cache before any capture
+    LQ_TRY(upload_ctrl());
+    // one plain iteration: packs the inner links/clover and fills the tuning
+    // cache before any capture (its result is thrown away by resetting x_lo,
+    // r, p below is not needed: it is a genuine first iteration, kept)
+    LQ_TRY(enqueue_iteration(0, false));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    it = 1;
+    W.info->mhat_applies += 2;
+    return LQCD_OK;
+  }
+
+  // one CG iteration and the control kernel; the new gamma goes to slot 1 and
+  // the control kernel moves it to slot 0
+  lqcd_status enqueue_iteration(cudaGraphConditionalHandle h, bool use_handle) const {
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
+    LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, 0, c->partials,
+                     c->counter, c->stream));
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1],
+                   kScStride));
+    LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, 0, c->stream));
+    cg_control_kernel<<<1, 64, 0, c->stream>>>(B.sc, dcr, dcg, n, h, use_handle ? 1 : 0);
+    LQ_CU(cudaGetLastError());
+    return LQCD_OK;
+  }
+
+  // before a graph launch: this launch may run up to `cap` iterations
+  lqcd_status arm() {
+    hcg->it = 0;
+    hcg->cap = std::max(1, W.max_iter - it);
+    hcg->stop = 0;
+    LQ_CU(cudaMemcpyAsync(dcg, hcg, sizeof(CtrlGlobal), cudaMemcpyHostToDevice, c->stream));
     LQ_CU(cudaStreamSynchronize(c->stream));
     return LQCD_OK;
   }
 
-  // k CG iterations starting at the current ping-pong index; no host sync
-  lqcd_status enqueue(int k) const {
-    int cc = cur;
-    for (int j = 0; j < k; j++) {
-      LQ_TRY(op_mhat(c, L, W.recon_lo, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
-      LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, cc, c->partials,
-                       c->counter, c->stream));
-      LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cc],
-                     kScStride));
-      LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, cc, c->stream));
-      cc ^= 1;
-    }
-    return LQCD_OK;
-  }
-
-  void advance(int k) {
-    it += k;
-    if (k & 1) cur ^= 1;
-    W.info->mhat_applies += 2.0 * k;
+  // after a graph launch: book the iterations and do the reliable update
+  lqcd_status finish_launch() {
+    LQ_TRY(download_ctrl());
+    it += hcg->it;
+    W.info->mhat_applies += 2.0 * hcg->it;
+    return update();
   }
 
   char *rhs_ptr(lqcd_field *f, int k, size_t bytes) const { return static_cast<char *>(f->data[1]) + bytes * k; }
 
-  lqcd_status check() {
-    LQ_TRY(read_scalars(c, B, n));
-    // keep the best inner iterate (smallest iterated residual); trigger an
-    // update when every active RHS dropped by delta, one reached its target,
-    // one stagnates, or one grew past twice its best (low-precision noise
-    // makes CG diverge on ill-conditioned systems)
-    bool all_dropped = true, any_target = false, any_stall = false, any_grow = false;
+  // reliable update, accepted only if it lowers the FP64 residual:
+  // x_try = x64 + sigma x_lo, r_try = bhat - Mhat64 x_try
+  lqcd_status update() {
     for (int k = 0; k < n; k++) {
-      if (B.h_sc[k].active == 0.0) continue;
-      const double rr = B.h_sc[k].rr;
-      if (!(rr == rr)) return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
-      if (rr < best_rr[k]) {
-        best_rr[k] = rr;
-        LQ_CU(cudaMemcpyAsync(rhs_ptr(xbest, k, rhs_bytes32), rhs_ptr(xlo, k, rhs_bytes32), rhs_bytes32,
-                              cudaMemcpyDeviceToDevice, c->stream));
-      }
-      if (rr < 0.25 * ref_rr[k]) {
-        ref_rr[k] = rr;
-        stall[k] = 0;
-      } else if ((stall[k] += it - last_it) >= kStallIters) {
-        any_stall = true;
-      }
-      if (rr > 4.0 * best_rr[k]) {
-        grown[k] = 1;
-        any_grow = true;
-      }
-      if (best_rr[k] > delta2) all_dropped = false;
-      if (sigma[k] * std::sqrt(best_rr[k]) <= target[k]) any_target = true;
+      if (B.h_sc[k].active != 0.0 && !(B.h_sc[k].rr == B.h_sc[k].rr))
+        return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
+      B.h_fac[k] = B.h_sc[k].active != 0.0 ? sigma[k] : 0.0;
     }
-    last_it = it;
-    if (!(all_dropped || any_target || any_stall || any_grow || it >= W.max_iter)) return LQCD_OK;
-
-    // ---- reliable update with the best inner iterate, accepted only if it
-    // lowers the FP64 residual: x_try = x64 + sigma x_best, r_try = bhat - Mhat64 x_try
-    for (int k = 0; k < n; k++) B.h_fac[k] = B.h_sc[k].active != 0.0 ? sigma[k] : 0.0;
     LQ_TRY(write_fac(c, B, n));
     LQ_CU(cudaMemcpyAsync(xtry->data[1], W.x64->data[1], rhs_bytes64 * n, cudaMemcpyDeviceToDevice, c->stream));
-    LQ_CU(blas_axpy(LQCD_F64, LQCD_F32, c->Vh, n, xtry->mut(1), xbest->ref(1), B.fac, c->stream));
+    LQ_CU(blas_axpy(LQCD_F64, LQCD_F32, c->Vh, n, xtry->mut(1), xlo->ref(1), B.fac, c->stream));
     LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, rtry->mut(1), xtry->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
                    &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
@@ -313,16 +402,14 @@ struct MixedCG {
     LQ_TRY(read_scalars(c, B, n));
     done = true;
     for (int k = 0; k < n; k++) {
-      B.h_fac[k] = 0.0;
-      B.h_fac[n + k] = 0.0;
-      B.h_fac[2 * n + k] = 0.0;
+      B.h_fac[k] = B.h_fac[n + k] = B.h_fac[2 * n + k] = 0.0;
       if (B.h_sc[k].active == 0.0) continue;
       const double snew = std::sqrt(B.h_sc[k].aux);
       if (kTrace)
         std::fprintf(stderr,
                      "lqcd: update %d it %d rhs %d inner |r| %.3e best %.3e  FP64 |r| %.6e -> %.6e (target %.3e)\n",
-                     W.info->reliable_updates, it, k, std::sqrt(B.h_sc[k].rr), std::sqrt(best_rr[k]), sigma[k], snew,
-                     target[k]);
+                     W.info->reliable_updates, it, k, std::sqrt(B.h_sc[k].rr), std::sqrt(hcr[k].best), sigma[k],
+                     snew, target[k]);
       if (!(snew == snew) || std::isinf(snew))
         return set_error(LQCD_ERR_NOCONV, "FP64 residual of RHS %d is not finite", k);
       const bool accept = snew < sigma[k];
@@ -338,29 +425,27 @@ struct MixedCG {
       }
       done = false;
       // p (the next search direction) is kept, rescaled into the new
-      // normalisation r_lo = r64 / snew, only if the update used the current
-      // iterate and improved; otherwise CG restarts from p = s
-      const bool restart = !accept || grown[k] || stall[k] >= kStallIters || best_rr[k] < B.h_sc[k].rr;
+      // normalisation r_lo = r64 / snew, unless the update was rejected or the
+      // inner iteration was turning round (grown, stagnating): then CG
+      // restarts from p = s
+      const bool restart = !accept || hcr[k].grown || hcr[k].stall >= kStallIters;
       const double snext = accept ? snew : sigma[k];
       B.h_fac[k] = restart ? 0.0 : sigma[k] / snext;
       B.h_fac[n + k] = 1.0 / snext;
       B.h_fac[2 * n + k] = restart ? 1.0 : 0.0;
       B.h_sc[k].rr = 1.0;
       sigma[k] = snext;
-      best_rr[k] = 1.0;
-      ref_rr[k] = 1.0;
-      stall[k] = 0;
-      grown[k] = 0;
+      reset_rhs(k);
     }
     LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
-    LQ_CU(cudaMemsetAsync(xbest->data[1], 0, xlo_bytes, c->stream));
     if (done) return LQCD_OK;
     // factors: p *= fac[0, n); r = r64 * fac[n, 2n); p += fac[2n, 3n) s
     LQ_TRY(write_scalars(c, B, n));
     LQ_TRY(write_fac(c, B, 3 * n));
+    LQ_TRY(upload_ctrl());
     LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
     LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
+    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
                    kScStride));
     LQ_CU(blas_axpy(L, L, c->Vh, n, p->mut(1), s->ref(1), B.fac + 2 * n, c->stream));
     W.info->mhat_applies += 1;
@@ -369,15 +454,86 @@ struct MixedCG {
   }
 };
 
+// A graph with one conditional WHILE node per solver, each body captured on
+// that solver's stream; the nodes are independent, so the lattices of a batch
+// run concurrently.  Launched on `launch`.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  ~LoopGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  lqcd_status build(const std::vector<MixedCG *> &cgs) {
+    if (exec) {
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    LQ_CU(cudaGraphCreate(&g, 0));
+    lqcd_status st = LQCD_OK;
+    for (MixedCG *m : cgs) {
+      cudaGraphConditionalHandle h;
+      if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        st = set_error(LQCD_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+        break;
+      }
+      cudaGraphNodeParams prm = {};
+      prm.type = cudaGraphNodeTypeConditional;
+      prm.conditional.handle = h;
+      prm.conditional.type = cudaGraphCondTypeWhile;
+      prm.conditional.size = 1;
+      cudaGraphNode_t node;
+      if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm) != cudaSuccess) {
+        st = set_error(LQCD_ERR_CUDA, "adding the conditional WHILE node failed");
+        break;
+      }
+      cudaGraph_t body = prm.conditional.phGraph_out[0];
+      if (cudaStreamBeginCaptureToGraph(m->c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+          cudaSuccess) {
+        st = set_error(LQCD_ERR_CUDA, "capture into the loop body failed");
+        break;
+      }
+      st = m->enqueue_iteration(h, true);
+      cudaGraph_t out = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(m->c->stream, &out);
+      if (st == LQCD_OK && e != cudaSuccess) st = set_error(LQCD_ERR_CUDA, "loop body capture: %s", cudaGetErrorString(e));
+      if (st != LQCD_OK) break;
+    }
+    if (st == LQCD_OK) {
+      const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+      if (e != cudaSuccess) st = set_error(LQCD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+};
+
+// Drive a set of mixed solvers to completion: arm, launch the loop graph,
+// update, repeat; the graph is rebuilt when the set of unfinished solvers
+// changes.
+lqcd_status run_mixed(const std::vector<MixedCG *> &all, cudaStream_t launch, int max_iter) {
+  LoopGraph graph;
+  std::vector<MixedCG *> prev;
+  while (true) {
+    std::vector<MixedCG *> active;
+    for (MixedCG *m : all)
+      if (!m->done && m->it < max_iter) active.push_back(m);
+    if (active.empty()) return LQCD_OK;
+    if (active != prev || !graph.exec) {
+      LQ_TRY(graph.build(active));
+      prev = active;
+    }
+    for (MixedCG *m : active) LQ_TRY(m->arm());
+    LQ_CU(cudaGraphLaunch(graph.exec, launch));
+    LQ_CU(cudaStreamSynchronize(launch));
+    for (MixedCG *m : active) LQ_TRY(m->finish_launch());
+  }
+}
+
 lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
   MixedCG m(W, B);
   LQ_TRY(m.init());
-  while (!m.done && m.it < W.max_iter) {
-    const int k = std::min(W.check_every, W.max_iter - m.it);
-    LQ_TRY(m.enqueue(k));
-    m.advance(k);
-    LQ_TRY(m.check());
-  }
+  if (!m.done) LQ_TRY(run_mixed({&m}, W.c->stream, W.max_iter));
   W.info->iters = m.it;
   return m.done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "mixed CG did not converge in %d iterations", W.max_iter);
 }
@@ -427,8 +583,8 @@ lqcd_status job_prepare(SolveJob &J) {
   inf->nrhs = n;
   J.nd = (size_t)n * c->V * 24;
   SolveBufs &B = J.B;
-  if (cudaMalloc(&B.sc, sizeof(SolverScalars) * n) != cudaSuccess ||
-      cudaMalloc(&B.fac, sizeof(double) * 3 * n) != cudaSuccess ||
+  if (dev_malloc((void **)&B.sc, sizeof(SolverScalars) * n) != cudaSuccess ||
+      dev_malloc((void **)&B.fac, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMallocHost(&B.h_sc, sizeof(SolverScalars) * n) != cudaSuccess ||
       cudaMallocHost(&B.h_fac, sizeof(double) * 3 * n) != cudaSuccess) {
     cudaGetLastError();
@@ -484,7 +640,8 @@ lqcd_status job_prepare(SolveJob &J) {
     for (int k = 0; k < n; k++) W.bnorm[k] = std::sqrt(e[k] + o[k]);
   }
   for (int k = 0; k < n; k++)
-    if (!(W.bnorm[k] > 0.0)) return set_error(LQCD_ERR_ARG, "right-hand side %d is zero or not finite", k);
+    if (!(W.bnorm[k] > 0.0) || !std::isfinite(W.bnorm[k]))
+      return set_error(LQCD_ERR_ARG, "right-hand side %d is zero or not finite", k);
   LQ_TRY(op_prepare(c, LQCD_F64, W.recon64, n, J.bhat->mut(1), J.bf->ref(0), J.bf->ref(1), J.tmpe->mut(0)));
   W.bhat = J.bhat;
   W.x64 = J.xf;
@@ -536,6 +693,24 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
                                   const lqcd_solve_params *prm, lqcd_solve_info *info) {
   LQ_TRY(check_params(c, prm));
   if (!x || !b) return set_error(LQCD_ERR_ARG, "NULL argument");
+  // the call blocks, so it runs on a private non-blocking stream (the legacy
+  // default stream cannot be captured into the loop graph), after waiting for
+  // the work queued on the context's stream
+  struct PrivateStream {
+    lqcd_ctx *c;
+    cudaStream_t saved, own = nullptr;
+    explicit PrivateStream(lqcd_ctx *ctx) : c(ctx), saved(ctx->stream) {}
+    ~PrivateStream() {
+      if (own) {
+        cudaStreamSynchronize(own);
+        c->stream = saved;
+        cudaStreamDestroy(own);
+      }
+    }
+  } ps(c);
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  LQ_CU(cudaStreamCreateWithFlags(&ps.own, cudaStreamNonBlocking));
+  c->stream = ps.own;
   SolveJob J;
   J.c = c;
   J.x = x;
@@ -548,10 +723,11 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
   return job_finish(J, st);
 }
 
-// Several lattices at once: every lattice runs on its own stream, and one
-// segment of `check_every` iterations of all of them is captured once into a
-// CUDA graph (fork/join across the streams) and replayed; the host checks the
-// residuals between replays and re-captures when a lattice has finished.
+// Several lattices at once: every lattice runs on its own stream, and the
+// inner loops of all of them are one CUDA graph -- one conditional WHILE node
+// per lattice, running on the GPU until that lattice needs a reliable update
+// -- launched once per update cycle; the graph is rebuilt when a lattice has
+// finished.
 extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double *const *x, const double *const *b,
                                         int on_device, const lqcd_solve_params *prm, lqcd_solve_info *infos) {
   if (!ctxs || !x || !b || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
@@ -566,20 +742,14 @@ extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double 
   // private non-blocking streams for the duration of the call
   std::vector<cudaStream_t> saved(nctx), own(nctx, nullptr);
   cudaStream_t root = nullptr;
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> join(nctx, nullptr);
-  cudaGraphExec_t exec = nullptr;
   auto cleanup = [&]() {
-    if (exec) cudaGraphExecDestroy(exec);
     for (int i = 0; i < nctx; i++) {
       if (own[i]) {
         cudaStreamSynchronize(own[i]);
         ctxs[i]->stream = saved[i];
         cudaStreamDestroy(own[i]);
       }
-      if (join[i]) cudaEventDestroy(join[i]);
     }
-    if (fork) cudaEventDestroy(fork);
     if (root) cudaStreamDestroy(root);
   };
   struct Guard {
@@ -587,13 +757,11 @@ extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double 
     ~Guard() { f(); }
   } guard{cleanup};
   LQ_CU(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
-  LQ_CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   for (int i = 0; i < nctx; i++) {
     LQ_CU(cudaStreamSynchronize(ctxs[i]->stream));
     saved[i] = ctxs[i]->stream;
     LQ_CU(cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking));
     ctxs[i]->stream = own[i];
-    LQ_CU(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
   }
   std::vector<std::unique_ptr<SolveJob>> jobs(nctx);
   std::vector<std::unique_ptr<MixedCG>> cgs(nctx);
@@ -610,51 +778,9 @@ extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double 
     cgs[i].reset(new MixedCG(J.W, J.B));
     LQ_TRY(cgs[i]->init());
   }
-  const int seg = std::max(2, (jobs[0]->W.check_every + 1) & ~1);  // even: the ping-pong index returns
-  std::vector<int> active_prev;
-  while (true) {
-    std::vector<int> active;
-    for (int i = 0; i < nctx; i++)
-      if (!cgs[i]->done && cgs[i]->it < prm->max_iter) active.push_back(i);
-    if (active.empty()) break;
-    if (active != active_prev || !exec) {
-      if (exec) {
-        cudaGraphExecDestroy(exec);
-        exec = nullptr;
-      }
-      cudaGraph_t graph = nullptr;
-      LQ_CU(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
-      lqcd_status st = LQCD_OK;
-      if (cudaEventRecord(fork, root) != cudaSuccess) st = set_error(LQCD_ERR_CUDA, "event record in capture");
-      for (int i : active) {
-        if (st != LQCD_OK) break;
-        if (cudaStreamWaitEvent(ctxs[i]->stream, fork, 0) != cudaSuccess) {
-          st = set_error(LQCD_ERR_CUDA, "stream wait in capture");
-          break;
-        }
-        st = cgs[i]->enqueue(seg);
-        if (st == LQCD_OK && (cudaEventRecord(join[i], ctxs[i]->stream) != cudaSuccess ||
-                              cudaStreamWaitEvent(root, join[i], 0) != cudaSuccess))
-          st = set_error(LQCD_ERR_CUDA, "join in capture");
-      }
-      const cudaError_t ec = cudaStreamEndCapture(root, &graph);
-      if (st != LQCD_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ec != cudaSuccess) return set_error(LQCD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
-      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ei != cudaSuccess) return set_error(LQCD_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
-      active_prev = active;
-    }
-    LQ_CU(cudaGraphLaunch(exec, root));
-    LQ_CU(cudaStreamSynchronize(root));
-    for (int i : active) {
-      cgs[i]->advance(seg);
-      LQ_TRY(cgs[i]->check());
-    }
-  }
+  std::vector<MixedCG *> all;
+  for (auto &m : cgs) all.push_back(m.get());
+  LQ_TRY(run_mixed(all, root, prm->max_iter));
   lqcd_status result = LQCD_OK;
   for (int i = 0; i < nctx; i++) {
     jobs[i]->inf->iters = cgs[i]->it;
