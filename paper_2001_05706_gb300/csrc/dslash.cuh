@@ -26,7 +26,8 @@ enum DslashMode {
   MODE_HOP_AINV = 1,     // out = Ainv (beta * hop)
   MODE_LOCAL_IDENT = 2,  // out = alpha * x + beta * hop
   MODE_LOCAL_A = 3,      // out = alpha * A x + beta * hop
-  MODE_FOLDED_AINV = 4   // out = Ainv (alpha * x + beta * hop)
+  MODE_FOLDED_AINV = 4,  // out = Ainv (alpha * x + beta * hop)
+  MODE_CHEB = 5          // out = (g5) (alpha * x + beta * hop) + sum_k cz[k] zc[k]  (Chebyshev step)
 };
 
 struct FieldRef {
@@ -44,6 +45,8 @@ struct DslashParams {
   FieldRef in;    // hop input (other parity); data == nullptr or beta == 0: no hop
   FieldRef xloc;  // local term input (output parity)
   FieldRef z;     // optional xpay input (output parity)
+  FieldRef zc[3];  // MODE_CHEB: extra terms of the output parity (data == nullptr: absent)
+  double cz[3];
   const void *links[4][2];  // [mu][parity]
   const void *cmat;         // A^-1 of the output parity (packed blocks)
   const float *cmat_scale;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::m
     }
 
     // ---- epilogue -------------------------------------------------------
-    if (MODE == MODE_LOCAL_IDENT || MODE == MODE_FOLDED_AINV || MODE == MODE_LOCAL_A) {
+    if (MODE == MODE_LOCAL_IDENT || MODE == MODE_FOLDED_AINV || MODE == MODE_LOCAL_A || MODE == MODE_CHEB) {
       const T alpha = (T)P.alpha;
       cx<T> x[NR][4][3];
 #pragma unroll
@@ -415,7 +418,23 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::m
           acc[r][3][c] = (T)-1 * acc[r][3][c];
         }
     }
-    if (P.z.data != nullptr) {
+    if (MODE == MODE_CHEB) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        if (P.zc[k].data == nullptr) continue;
+        const T ck = (T)P.cz[k];
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+          cx<T> zz[4][3];
+          load_spinor<S>(P.zc[k], P.g.Vh, rg * NR + r, h, zz);
+#pragma unroll
+          for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[r][a][c] = acc[r][a][c] + ck * zz[a][c];
+        }
+      }
+    }
+    if (MODE != MODE_CHEB && P.z.data != nullptr) {
       const T gz = (T)P.gz;
 #pragma unroll
       for (int r = 0; r < NR; r++) {

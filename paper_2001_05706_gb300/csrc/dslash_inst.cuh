@@ -2,6 +2,8 @@
 // type by dslash_f64.cu, dslash_f32.cu, dslash_f16.cu and dslash_bf16.cu so
 // the instantiations compile in parallel.
 #pragma once
+#include <type_traits>
+
 #include "dslash.cuh"
 
 namespace lqcd {
@@ -32,6 +34,11 @@ static cudaError_t launch_mode(const DslashParams &P, int mode, int nr, cudaStre
     case MODE_LOCAL_IDENT: return launch_nr<S, R, MODE_LOCAL_IDENT>(P, nr, st);
     case MODE_LOCAL_A: return launch_nr<S, R, MODE_LOCAL_A>(P, nr, st);
     case MODE_FOLDED_AINV: return launch_nr<S, R, MODE_FOLDED_AINV>(P, nr, st);
+    case MODE_CHEB:
+      // the Chebyshev step runs in the overlap's FP64 and FP32 sign functions only
+      if constexpr (std::is_same<S, double>::value || std::is_same<S, float>::value)
+        return launch_nr<S, R, MODE_CHEB>(P, nr, st);
+      break;
   }
   return cudaErrorInvalidValue;
 }

@@ -149,7 +149,8 @@ lqcd_status ensure_partials(lqcd_ctx *c, int nrhs);
 // one launch of the generic dslash kernel on output parity out_p
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
                        FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
-                       int g5_total, double *norm_result, int norm_stride);
+                       int g5_total, double *norm_result, int norm_stride, const FieldRef *zc = nullptr,
+                       const double *cz = nullptr);
 // y_e = A_ee^-1 D_eo x_o (g5 on the input if dagger)
 lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o);
 // z_o = [zf +gz*] (A_oo x_o - kappa^2 [g5] D_oe y_e), optional norm
@@ -170,6 +171,10 @@ lqcd_status op_reconstruct(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, Mut
 // out_p = g5 [(4 - rho) x_p - D x_{1-p} / 2] on both parities
 lqcd_status op_hw(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double *norm_result,
                   int norm_stride);
+// one Chebyshev (Clenshaw) step fused into the second H_W application:
+// out_p = t H_W x + sum_k cz[k] z[k]_p on both parities (z[k][p].data == nullptr: term absent)
+lqcd_status op_hw_cheb(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double t,
+                       const FieldRef z[3][2], const double cz[3]);
 }  // namespace lqcd
 
 namespace lqcd {

@@ -174,7 +174,7 @@ static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon
 
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
                        FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
-                       int g5_total, double *norm_result, int norm_stride) {
+                       int g5_total, double *norm_result, int norm_stride, const FieldRef *zc, const double *cz) {
   DslashParams P{};
   P.g = c->geom;
   P.out_parity = out_p;
@@ -205,6 +205,13 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
   P.g5_in = g5_in;
   P.g5_hop = g5_hop;
   P.g5_total = g5_total;
+  if (mode == MODE_CHEB) {
+    if (!zc || !cz) return set_error(LQCD_ERR_ARG, "Chebyshev step without its terms");
+    for (int k = 0; k < 3; k++) {
+      P.zc[k] = zc[k];
+      P.cz[k] = cz[k];
+    }
+  }
   if (norm_result) {
     LQ_TRY(ensure_partials(c, nrhs));
     P.norm_partials = c->partials;
@@ -276,6 +283,18 @@ lqcd_status op_hw(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out
   for (int p = 0; p < 2; p++)
     LQ_TRY(run_dslash(c, prec, recon, MODE_LOCAL_IDENT, p, nrhs, out[p], x[1 - p], x[p], kNone, 4.0 - c->rho, -0.5, 0.0,
                       0, 0, 1, norm_result ? norm_result + p : nullptr, norm_stride));
+  return LQCD_OK;
+}
+
+lqcd_status op_hw_cheb(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double t,
+                       const FieldRef z[3][2], const double cz[3]) {
+  if (!c->have_rho) return set_error(LQCD_ERR_STATE, "rho not set (call lqcd_set_rho)");
+  if (prec != LQCD_F64 && prec != LQCD_F32) return set_error(LQCD_ERR_ARG, "Chebyshev step needs FP64 or FP32");
+  for (int p = 0; p < 2; p++) {
+    const FieldRef zp[3] = {z[0][p], z[1][p], z[2][p]};
+    LQ_TRY(run_dslash(c, prec, recon, MODE_CHEB, p, nrhs, out[p], x[1 - p], x[p], kNone, t * (4.0 - c->rho),
+                      -0.5 * t, 0.0, 0, 0, 1, nullptr, 0, zp, cz));
+  }
   return LQCD_OK;
 }
 

@@ -15,8 +15,8 @@
 //    P the Chebyshev interpolant of 1/sqrt(y) on [a, b], evaluated by the
 //    Clenshaw recurrence b_k = c_k w + 2 T b_{k+1} - b_{k+2},
 //    T = (2 H_W^2 - a - b)/(b - a); each step is two H_W applications (the
-//    dslash kernel, all right-hand sides per launch) and one fused
-//    three-term kernel.
+//    dslash kernel, all right-hand sides per launch), the second of which
+//    adds the three-term update in its epilogue (MODE_CHEB).
 //  * D_ov(m) = f (1 + g5 eps) + m with f = (1 - m/(2 rho)) rho, and CG on its
 //    normal equations for the inverse.
 #include <cublas_v2.h>
@@ -359,6 +359,18 @@ lqcd_status hw(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in) {
   return op_hw(c, out->prec, out->prec == LQCD_F64 ? 18 : 12, nrhs, o, x, nullptr, 0);
 }
 
+// out = t H_W in + c1 z1 + c2 z2 + c3 z3 (z3 may be null), FULL fields
+lqcd_status hw_cheb(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in, double t, const lqcd_field *z1,
+                    double c1, const lqcd_field *z2, double c2, const lqcd_field *z3, double c3) {
+  MutField o[2] = {out->mut(0), out->mut(1)};
+  FieldRef x[2] = {in->ref(0), in->ref(1)};
+  const FieldRef none{nullptr, nullptr, 0};
+  const FieldRef z[3][2] = {{z1->ref(0), z1->ref(1)}, {z2->ref(0), z2->ref(1)},
+                            {z3 ? z3->ref(0) : none, z3 ? z3->ref(1) : none}};
+  const double cz[3] = {c1, c2, z3 ? c3 : 0.0};
+  return op_hw_cheb(c, out->prec, out->prec == LQCD_F64 ? 18 : 12, nrhs, o, x, t, z, cz);
+}
+
 // dst = src converted between precisions (FULL fields, first nrhs RHS)
 lqcd_status convert_full(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs) {
   for (int p = 0; p < 2; p++)
@@ -530,22 +542,20 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
   const int n = S.degree;
   // b_n = c_n w
   LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[n], 0.0, 0.0, 0.0));
+  // b_k = c_k w + 2 T b_{k+1} - b_{k+2} (k = n-1 .. 1), then P w = c_0 w + T b_1 - b_2
+  // (n = 0: P w = c_0 w = b_0),
+  // T = s2 H^2 + s0: the second H_W of each step carries the three-term update
+  // in its epilogue; three buffers rotate so no launch writes what it reads
   bool b2_zero = true;
-  for (int k = n - 1; k >= 1; k--) {
+  for (int k = n - 1; k >= 0; k--) {
+    const double t = k > 0 ? 2.0 : 1.0;
     LQ_TRY(hw(c, nrhs, h, b1));
-    LQ_TRY(hw(c, nrhs, hh, h));
-    LQ_TRY(clenshaw(c, nrhs, b2, w, hh, b1, b2_zero ? nullptr : b2, S.coef[k], 2.0, s2, s0));
+    LQ_TRY(hw_cheb(c, nrhs, hh, h, t * s2, w, S.coef[k], b1, t * s0, b2_zero ? nullptr : b2, -1.0));
     b2_zero = false;
-    std::swap(b1, b2);
-  }
-  // P w = c0 w + T b1 - b2
-  if (n >= 1) {
-    LQ_TRY(hw(c, nrhs, h, b1));
-    LQ_TRY(hw(c, nrhs, hh, h));
-    LQ_TRY(clenshaw(c, nrhs, b2, w, hh, b1, b2_zero ? nullptr : b2, S.coef[0], 1.0, s2, s0));
-    std::swap(b1, b2);
-  } else {
-    LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[0], 0.0, 0.0, 0.0));
+    lqcd_field *o = hh;
+    hh = b2;
+    b2 = b1;
+    b1 = o;
   }
   LQ_TRY(hw(c, nrhs, out, b1));  // H P(H^2) w
   if (nl > 0) {
@@ -696,14 +706,29 @@ lqcd_status ov_cgls_fp64(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field 
 // Mixed precision: CG on the normal equations of D_ov with FP32 storage and
 // arithmetic (FP32 sign function) on the residual normalised to 1; the FP64
 // solution absorbs the inner one and the residual is recomputed with the FP64
-// operator whenever the inner residual fell below delta (or stagnated); the
-// search direction is kept across updates, rescaled, unless the update failed
-// to reduce the residual.
+// operator when every active inner residual fell below delta or reached its
+// target (a right-hand side that reached it is parked: it stops updating
+// until the FP64 check), or one stagnated (no 4x drop of |r|^2 in
+// kOvStallIters iterations) or grew 20 % past its best.  The update is accepted only if it lowers the FP64
+// residual; the search direction is kept across accepted updates, rescaled,
+// and CG restarts from p = s after a rejected, grown or stagnated one (the
+// same policy as the Wilson-clover mixed solver).
+constexpr int kOvStallIters = 48;
+
+lqcd_status copy_rhs(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int k) {
+  const size_t bytes = (size_t)cwords(src) * celem(src);
+  for (int p = 0; p < 2; p++)
+    LQ_CU(cudaMemcpyAsync(static_cast<char *>(dst->data[p]) + bytes * k,
+                          static_cast<const char *>(src->data[p]) + bytes * k, bytes, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  return LQCD_OK;
+}
+
 lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field *x, const lqcd_solve_params *cg,
                           lqcd_solve_info *inf, const std::vector<double> &bn2) {
   FieldGuard g;
-  lqcd_field *r64, *t64, *xlo, *r, *s, *p, *q;
-  for (lqcd_field **f : {&r64, &t64}) {
+  lqcd_field *r64, *t64, *xtry, *xlo, *r, *s, *p, *q;
+  for (lqcd_field **f : {&r64, &t64, &xtry}) {
     LQ_TRY(new_full(c, nrhs, f));
     g.f.push_back(*f);
   }
@@ -717,9 +742,9 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
     LQ_CU(cudaMemsetAsync(x->data[par], 0, bytes64, c->stream));
     LQ_CU(cudaMemsetAsync(xlo->data[par], 0, bytes32, c->stream));
   }
-  std::vector<double> target(nrhs), sigma(nrhs), inv(nrhs), gam, qq, rr, best(nrhs, 1.0);
+  std::vector<double> target(nrhs), sigma(nrhs), inv(nrhs), gam, qq, rr, best(nrhs, 1.0), ref(nrhs, 1.0);
   std::vector<int> stall(nrhs, 0);
-  std::vector<char> active(nrhs, 1);
+  std::vector<char> active(nrhs, 1), grown(nrhs, 0), parked(nrhs, 0);
   for (int k = 0; k < nrhs; k++) {
     target[k] = 0.5 * cg->tol * std::sqrt(bn2[k]);
     sigma[k] = std::sqrt(bn2[k]);
@@ -737,61 +762,72 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
     LQ_TRY(field_norms(c, q, nrhs, qq));
     std::vector<double> al(nrhs), nal(nrhs);
     for (int k = 0; k < nrhs; k++) {
-      al[k] = active[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
+      al[k] = active[k] && !parked[k] && qq[k] > 0 ? gam[k] / qq[k] : 0.0;
       nal[k] = -al[k];
     }
     LQ_TRY(axpy_full(c, xlo, p, al, nrhs));
     LQ_TRY(axpy_full(c, r, q, nal, nrhs));
     LQ_TRY(field_norms(c, r, nrhs, rr));
     it++;
-    bool all_dropped = true, any_target = false, any_stall = false;
+    bool all_dropped = true, trigger = false;
     for (int k = 0; k < nrhs; k++) {
-      if (!active[k]) continue;
+      if (!active[k] || parked[k]) continue;
       if (!(rr[k] == rr[k])) return set_error(LQCD_ERR_NOCONV, "overlap inner residual is NaN");
-      if (rr[k] > delta * delta) all_dropped = false;
-      if (sigma[k] * std::sqrt(rr[k]) <= target[k]) any_target = true;
-      if (rr[k] < 0.25 * best[k]) {
-        best[k] = rr[k];
-        stall[k] = 0;
-      } else if (++stall[k] >= 16) {
-        any_stall = true;
+      if (sigma[k] * std::sqrt(rr[k]) <= target[k]) {
+        parked[k] = 1;  // waits, unchanged, for the next FP64 update to confirm it
+        continue;
       }
+      if (rr[k] < best[k]) best[k] = rr[k];
+      if (rr[k] < 0.25 * ref[k]) {
+        ref[k] = rr[k];
+        stall[k] = 0;
+      } else if (++stall[k] >= kOvStallIters) {
+        trigger = true;
+      }
+      if (rr[k] > 1.44 * best[k]) {
+        grown[k] = 1;
+        trigger = true;
+      }
+      if (!(best[k] <= delta * delta)) all_dropped = false;
     }
-    if (all_dropped || any_target || any_stall || it >= cg->max_iter) {
-      // reliable update in FP64
-      std::vector<double> fx(nrhs), mone(nrhs, -1.0), r2;
+    if (all_dropped || trigger || it >= cg->max_iter) {
+      // reliable update in FP64: x_try = x + sigma x_lo, r_try = b - D_ov x_try
+      std::vector<double> fx(nrhs), r2;
       for (int k = 0; k < nrhs; k++) fx[k] = active[k] ? sigma[k] : 0.0;
-      LQ_TRY(axpy_full(c, x, xlo, fx, nrhs));
+      LQ_TRY(copy_field(c, xtry, x, nrhs));
+      LQ_TRY(axpy_full(c, xtry, xlo, fx, nrhs));
       for (int par = 0; par < 2; par++) LQ_CU(cudaMemsetAsync(xlo->data[par], 0, bytes32, c->stream));
-      LQ_TRY(dov_apply(c, nrhs, x, t64, 0));
-      LQ_TRY(copy_field(c, r64, b, nrhs));
-      LQ_TRY(axpy_full(c, r64, t64, mone, nrhs));
-      LQ_TRY(field_norms(c, r64, nrhs, r2));
+      LQ_TRY(dov_apply(c, nrhs, xtry, t64, 0));
+      LQ_TRY(combine(c, nrhs, t64, b, t64, 1.0, -1.0, 0));  // element-wise, in place
+      LQ_TRY(field_norms(c, t64, nrhs, r2));
       inf->reliable_updates++;
       inf->mhat_applies += 1;
       done = true;
-      std::vector<double> fp(nrhs), fr(nrhs), fs(nrhs, 0.0);
+      std::vector<double> fp(nrhs, 0.0), fr(nrhs, 0.0), fs(nrhs, 0.0);
       for (int k = 0; k < nrhs; k++) {
-        if (!active[k]) {
-          fp[k] = 0.0;
-          fr[k] = 0.0;
-          continue;
-        }
+        if (!active[k]) continue;
         const double snew = std::sqrt(r2[k]);
-        if (!(snew == snew)) return set_error(LQCD_ERR_NOCONV, "overlap FP64 residual is NaN");
-        if (snew <= target[k]) {
-          active[k] = 0;
-          fp[k] = fr[k] = 0.0;
-          continue;
+        if (!(snew == snew) || std::isinf(snew)) return set_error(LQCD_ERR_NOCONV, "overlap FP64 residual is not finite");
+        const bool accept = snew < sigma[k];
+        if (accept) {
+          LQ_TRY(copy_rhs(c, x, xtry, k));
+          LQ_TRY(copy_rhs(c, r64, t64, k));
+          if (snew <= target[k]) {
+            active[k] = 0;
+            continue;
+          }
         }
         done = false;
-        const bool restart = snew >= sigma[k] || stall[k] >= 16;
-        fp[k] = restart ? 0.0 : sigma[k] / snew;
+        const bool restart = !accept || grown[k] || parked[k] || stall[k] >= kOvStallIters;
+        const double snext = accept ? snew : sigma[k];
+        fp[k] = restart ? 0.0 : sigma[k] / snext;
         fs[k] = restart ? 1.0 : 0.0;
-        fr[k] = 1.0 / snew;
-        sigma[k] = snew;
-        best[k] = 1.0;
+        fr[k] = 1.0 / snext;
+        sigma[k] = snext;
+        best[k] = ref[k] = 1.0;
         stall[k] = 0;
+        grown[k] = 0;
+        parked[k] = 0;
       }
       if (done) break;
       LQ_TRY(scale_full(c, p, p, fp, nrhs));
@@ -808,9 +844,10 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
     std::vector<double> gn, be(nrhs), one(nrhs);
     LQ_TRY(field_norms(c, s, nrhs, gn));
     for (int k = 0; k < nrhs; k++) {
-      be[k] = active[k] && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
-      one[k] = active[k] ? 1.0 : 0.0;
-      if (active[k]) gam[k] = gn[k];
+      const bool on = active[k] && !parked[k];
+      be[k] = on && gam[k] > 0 ? gn[k] / gam[k] : 1.0;
+      one[k] = on ? 1.0 : 0.0;
+      if (on) gam[k] = gn[k];
     }
     LQ_TRY(scale_full(c, p, p, be, nrhs));
     LQ_TRY(axpy_full(c, p, s, one, nrhs));
