@@ -63,9 +63,16 @@ typedef enum {
 } lqcd_status;
 
 /* Storage precision of a field.  Arithmetic is FP64 for LQCD_F64 and FP32
- * for the others; FP16 and BF16 spinors and clover terms carry one FP32
- * scale per site, links are stored unscaled. */
-typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3 } lqcd_prec;
+ * for F32, F16 and BF16; FP16 and BF16 spinors and clover terms carry one
+ * FP32 scale per site, links are stored unscaled.  LQCD_DF64 ("double-float",
+ * no counterpart in the paper) stores every real as two FP32 numbers hi + lo
+ * (eight bytes, the FP64 layout) and computes on the FP32 pipes with
+ * error-free transformations: a 48-bit significand (relative rounding about
+ * 2^-47 per operation against FP64's 2^-53), the FP32 exponent range (values
+ * below ~1e-30 in magnitude lose low-order bits, above ~3e38 overflow), and
+ * several times the throughput of FP64 on a GPU whose FP64 rate is 1/64 of
+ * its FP32 rate. */
+typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3, LQCD_DF64 = 4 } lqcd_prec;
 
 /* Link storage: all 18 reals, or rows 0 and 1 only (12 reals) with row 2
  * rebuilt as conj(row0 x row1) in registers (Table 2's caption). */
@@ -178,7 +185,8 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *ctx, const lqcd_field *field, double *res
 typedef struct {
   double tol;          /* target ||b - M x|| / ||b|| on the full lattice, > 0     */
   int max_iter;        /* cap on CG iterations (inner iterations when mixed)       */
-  lqcd_prec inner;     /* LQCD_F64: plain FP64 CG; else mixed with this storage    */
+  lqcd_prec inner;     /* LQCD_F64 / LQCD_DF64: plain CG in that precision; else  */
+                       /* mixed with this storage (F32, F16, BF16)                */
   double delta;        /* reliable-update trigger: inner ||r|| < delta * ||r_0||   */
   int nrhs;            /* right-hand sides stored back to back in x and b          */
   int use_x0;          /* 1: x holds an initial guess on entry                     */
@@ -186,6 +194,9 @@ typedef struct {
   lqcd_recon inner_recon; /* link storage of the inner low-precision operator      */
   int check_every;     /* FP64 CG: iterations between host checks (0: 8); the     */
                        /* mixed solver checks every iteration on the device       */
+  lqcd_prec outer;     /* mixed solver: precision of the reliable updates and of  */
+                       /* the accumulated solution, LQCD_F64 (0, the default) or  */
+                       /* LQCD_DF64; the final residual check is FP64 either way  */
 } lqcd_solve_params;
 
 typedef struct {

@@ -31,13 +31,13 @@ _lib = ctypes.CDLL(_build.LIB)
 LQCD_OK = 0
 LQCD_ERR_ARG, LQCD_ERR_CUDA, LQCD_ERR_OOM, LQCD_ERR_NOCONV = -1, -2, -3, -4
 LQCD_ERR_TIMEOUT, LQCD_ERR_STATE, LQCD_ERR_NOT_SU3, LQCD_ERR_SINGULAR = -5, -6, -7, -8
-LQCD_F64, LQCD_F32, LQCD_F16, LQCD_BF16 = 0, 1, 2, 3
+LQCD_F64, LQCD_F32, LQCD_F16, LQCD_BF16, LQCD_DF64 = 0, 1, 2, 3, 4
 LQCD_RECON_18, LQCD_RECON_12 = 18, 12
 LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
 (LQCD_OP_M, LQCD_OP_MHAT, LQCD_OP_MHAT_DAG, LQCD_OP_MHAT_NORMAL, LQCD_OP_HOP_EO, LQCD_OP_HOP_OE, LQCD_OP_HW,
  LQCD_OP_K2A, LQCD_OP_M_DAG) = range(9)
 
-PREC = {"f64": LQCD_F64, "f32": LQCD_F32, "f16": LQCD_F16, "bf16": LQCD_BF16}
+PREC = {"f64": LQCD_F64, "f32": LQCD_F32, "f16": LQCD_F16, "bf16": LQCD_BF16, "df64": LQCD_DF64}
 OPS = {"M": LQCD_OP_M, "MHAT": LQCD_OP_MHAT, "MHAT_DAG": LQCD_OP_MHAT_DAG, "MHAT_NORMAL": LQCD_OP_MHAT_NORMAL,
        "HOP_EO": LQCD_OP_HOP_EO, "HOP_OE": LQCD_OP_HOP_OE, "HW": LQCD_OP_HW, "K2A": LQCD_OP_K2A,
        "M_DAG": LQCD_OP_M_DAG}
@@ -46,7 +46,8 @@ OPS = {"M": LQCD_OP_M, "MHAT": LQCD_OP_MHAT, "MHAT_DAG": LQCD_OP_MHAT_DAG, "MHAT
 class lqcd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("use_x0", ctypes.c_int),
-                ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("outer", ctypes.c_int)]
 
 
 class lqcd_overlap_params(ctypes.Structure):
@@ -293,8 +294,8 @@ def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):
 
 
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,
-                 inner_recon=LQCD_RECON_12, check_every=8):
-    return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every)
+                 inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64):
+    return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every, outer)
 
 
 # ---- convenience ------------------------------------------------------------
@@ -350,6 +351,8 @@ class Lattice:
         if nrhs is None:
             nrhs = b.size // (12 * self.V)
         x = np.zeros_like(b)
+        if isinstance(kw.get("outer"), str):
+            kw["outer"] = PREC[kw["outer"]]
         prm = solve_params(tol=tol, inner=PREC[inner] if isinstance(inner, str) else inner, nrhs=nrhs, **kw)
         st, info = lqcd_solve(self.ctx, x, b, prm, raise_on_noconv=False)
         return x, st, info

@@ -54,7 +54,7 @@ static void free_links(lqcd_ctx *c) {
 }
 
 static void free_clover(lqcd_ctx *c) {
-  for (int p = 0; p < 4; p++) {
+  for (int p = 0; p < 5; p++) {
     if (c->clov[p].alloc) cudaFree(c->clov[p].alloc);
     c->clov[p] = CloverStore{};
   }
@@ -258,7 +258,7 @@ lqcd_status lqcd_field_create(lqcd_ctx *c, lqcd_prec prec, lqcd_subset subset, i
   LQ_TRY(check_ctx(c));
   if (!field) return set_error(LQCD_ERR_ARG, "field is NULL");
   *field = nullptr;
-  if ((int)prec < 0 || (int)prec > 3) return set_error(LQCD_ERR_ARG, "bad precision %d", (int)prec);
+  if ((int)prec < 0 || (int)prec > 4) return set_error(LQCD_ERR_ARG, "bad precision %d", (int)prec);
   if ((int)subset < 0 || (int)subset > 2) return set_error(LQCD_ERR_ARG, "bad subset %d", (int)subset);
   if (nrhs < 1 || nrhs > 4096) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..4096");
   lqcd_field *f = new lqcd_field();
@@ -457,7 +457,7 @@ lqcd_status lqcd_dslash(lqcd_ctx *c, double *out, const double *in, int nrhs, lq
   if (!out || !in) return set_error(LQCD_ERR_ARG, "NULL buffer");
   if (out == in) return set_error(LQCD_ERR_ARG, "out and in must not alias");
   if (nrhs < 1 || nrhs > 4096) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..4096");
-  if ((int)prec < 0 || (int)prec > 3) return set_error(LQCD_ERR_ARG, "bad precision");
+  if ((int)prec < 0 || (int)prec > 4) return set_error(LQCD_ERR_ARG, "bad precision");
   if ((int)op < 0 || (int)op > 8) return set_error(LQCD_ERR_ARG, "bad op");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   const size_t n = (size_t)nrhs * c->V * 24;

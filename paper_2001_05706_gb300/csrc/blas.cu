@@ -35,18 +35,16 @@ __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x
     load_spinor<SX>(x.ref(), Vh, k, h, xv);
     const TV a = (TV)alpha;
     const TX ax = (TX)alpha;
-    double n2 = 0.0;
 #pragma unroll
     for (int sp = 0; sp < 4; sp++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        xv[sp][c] = mk<TX>(xv[sp][c].r + ax * (TX)pv[sp][c].r, xv[sp][c].i + ax * (TX)pv[sp][c].i);
-        rv[sp][c] = mk<TV>(rv[sp][c].r - a * qv[sp][c].r, rv[sp][c].i - a * qv[sp][c].i);
-        n2 += (double)rv[sp][c].r * rv[sp][c].r + (double)rv[sp][c].i * rv[sp][c].i;
+        xv[sp][c] = mk<TX>(fma(ax, (TX)pv[sp][c].r, xv[sp][c].r), fma(ax, (TX)pv[sp][c].i, xv[sp][c].i));
+        rv[sp][c] = mk<TV>(fma(-a, qv[sp][c].r, rv[sp][c].r), fma(-a, qv[sp][c].i, rv[sp][c].i));
       }
     store_spinor<SX>(x.data, x.scale, x.rhs_words, Vh, k, h, xv);
     store_spinor<SV>(r.data, r.scale, r.rhs_words, Vh, k, h, rv);
-    nrm[0] = n2;
+    nrm[0] = site_norm2<TV>(rv);
   }
   // an inactive right-hand side reduces zeros: its rr reads 0 from then on
   grid_reduce<1>(nrm, partials, counter, &sc[0].rr, k, nrhs, (int)(sizeof(SolverScalars) / 8));
@@ -68,7 +66,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_p_kernel(long Vh, MutField p,
 #pragma unroll
   for (int sp = 0; sp < 4; sp++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) pv[sp][c] = mk<TV>(ss[sp][c].r + beta * pv[sp][c].r, ss[sp][c].i + beta * pv[sp][c].i);
+    for (int c = 0; c < 3; c++) pv[sp][c] = mk<TV>(fma(beta, pv[sp][c].r, ss[sp][c].r), fma(beta, pv[sp][c].i, ss[sp][c].i));
   store_spinor<SV>(p.data, p.scale, p.rhs_words, Vh, k, h, pv);
 }
 
@@ -83,26 +81,24 @@ __global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v
   if (h < Vh) {
     cx<T> a[4][3];
     load_spinor<S>(v, Vh, k, h, a);
-    double n2 = 0.0;
-#pragma unroll
-    for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-      for (int c = 0; c < 3; c++) n2 += (double)a[sp][c].r * a[sp][c].r + (double)a[sp][c].i * a[sp][c].i;
-    nrm[0] = n2;
+    nrm[0] = site_norm2<T>(a);
   }
   grid_reduce<1>(nrm, partials, counter, result, k, nrhs, stride);
 }
 
-// y += f_k x  (per right-hand side factor f[k], in FP64; y may be FP64 and x lower)
+// y += f_k x  (per right-hand side factor f[k]; arithmetic in the wider of
+// the two types: FP32 unless y or x is FP64 or DF64)
 template <typename SY, typename SX>
 __global__ void __launch_bounds__(kBlasThreads) axpy_kernel(long Vh, MutField y, FieldRef x, const double *f) {
   using TY = typename Math<SY>::T;
   using TX = typename Math<SX>::T;
+  using W = typename Wide<TY, TX>::type;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (h >= Vh) return;
   const double a = f[k];
   if (a == 0.0) return;
+  const W aw = (W)a;
   cx<TY> yv[4][3];
   cx<TX> xv[4][3];
   load_spinor<SY>(y.ref(), Vh, k, h, yv);
@@ -111,16 +107,17 @@ __global__ void __launch_bounds__(kBlasThreads) axpy_kernel(long Vh, MutField y,
   for (int sp = 0; sp < 4; sp++)
 #pragma unroll
     for (int c = 0; c < 3; c++)
-      yv[sp][c] = mk<TY>((TY)((double)yv[sp][c].r + a * (double)xv[sp][c].r),
-                         (TY)((double)yv[sp][c].i + a * (double)xv[sp][c].i));
+      yv[sp][c] = mk<TY>((TY)fma(aw, (W)xv[sp][c].r, (W)yv[sp][c].r), (TY)fma(aw, (W)xv[sp][c].i, (W)yv[sp][c].i));
   store_spinor<SY>(y.data, y.scale, y.rhs_words, Vh, k, h, yv);
 }
 
-// y = f_k x with per-RHS factors (precision conversion included)
+// y = f_k x with per-RHS factors (precision conversion included; arithmetic
+// in the wider of the two types)
 template <typename SY, typename SX>
 __global__ void __launch_bounds__(kBlasThreads) scale_kernel(long Vh, MutField y, FieldRef x, const double *f) {
   using TY = typename Math<SY>::T;
   using TX = typename Math<SX>::T;
+  using W = typename Wide<TY, TX>::type;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (h >= Vh) return;
@@ -131,7 +128,7 @@ __global__ void __launch_bounds__(kBlasThreads) scale_kernel(long Vh, MutField y
 #pragma unroll
   for (int sp = 0; sp < 4; sp++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) yv[sp][c] = mk<TY>((TY)(a * (double)xv[sp][c].r), (TY)(a * (double)xv[sp][c].i));
+    for (int c = 0; c < 3; c++) yv[sp][c] = mk<TY>((TY)((W)a * (W)xv[sp][c].r), (TY)((W)a * (W)xv[sp][c].i));
   store_spinor<SY>(y.data, y.scale, y.rhs_words, Vh, k, h, yv);
 }
 
@@ -145,6 +142,7 @@ long blas_blocks(long Vh) { return (Vh + kBlasThreads - 1) / kBlasThreads; }
     case LQCD_F32: { using SV = float; CALL; } break;              \
     case LQCD_F16: { using SV = __half; CALL; } break;             \
     case LQCD_BF16: { using SV = __nv_bfloat16; CALL; } break;     \
+    case LQCD_DF64: { using SV = df; CALL; } break;                \
   }
 
 cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, MutField r, FieldRef q,
@@ -152,6 +150,8 @@ cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x
   dim3 g = bgrid(Vh, nrhs);
   if (px == LQCD_F64 && pv == LQCD_F64) {
     cg_xr_kernel<double, double><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs);
+  } else if (px == LQCD_DF64 && pv == LQCD_DF64) {
+    cg_xr_kernel<df, df><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs);
   } else if (px == LQCD_F32) {
     LQ_DISPATCH_V(pv, (cg_xr_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs)));
   } else {
@@ -179,6 +179,8 @@ cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y,
   dim3 g = bgrid(Vh, nrhs);
   if (py == LQCD_F64) {
     LQ_DISPATCH_V(px, (axpy_kernel<double, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
+  } else if (py == LQCD_DF64) {
+    LQ_DISPATCH_V(px, (axpy_kernel<df, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
   } else if (py == LQCD_F32) {
     LQ_DISPATCH_V(px, (axpy_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
   } else if (py == LQCD_F16 && px == LQCD_F16) {
@@ -201,6 +203,7 @@ cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y
     case LQCD_BF16:
       LQ_DISPATCH_V(px, (scale_kernel<__nv_bfloat16, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f)));
       break;
+    case LQCD_DF64: LQ_DISPATCH_V(px, (scale_kernel<df, SV><<<g, kBlasThreads, 0, st>>>(Vh, y, x, f))); break;
   }
   return cudaGetLastError();
 }

@@ -10,16 +10,19 @@
 #include <stdint.h>
 
 #include "../../include/lqcd.h"
+#include "df64.cuh"
 
 namespace lqcd {
 
 // ---------------------------------------------------------------------------
-// Storage precisions.  Arithmetic is FP64 for FP64 storage and FP32 for the
-// three others; FP16 and BF16 spinors and clover terms carry one FP32 scale
-// per site (the largest |component|), links are stored unscaled (|U_ij|<=1).
+// Storage precisions.  Arithmetic is FP64 for FP64 storage, double-float for
+// DF64 storage (df, two FP32 numbers per real) and FP32 for the three others;
+// FP16 and BF16 spinors and clover terms carry one FP32 scale per site (the
+// largest |component|), links are stored unscaled (|U_ij|<=1).
 // ---------------------------------------------------------------------------
 template <typename S> struct Math { using T = float; };
 template <> struct Math<double> { using T = double; };
+template <> struct Math<df> { using T = df; };
 
 template <typename S> struct IsHalf { static constexpr bool value = false; };
 template <> struct IsHalf<__half> { static constexpr bool value = true; };
@@ -41,6 +44,7 @@ template <> __device__ __forceinline__ __half from_d<__half>(double v) { return 
 template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
   return __float2bfloat16_rn((float)v);
 }
+template <> __device__ __forceinline__ df from_d<df>(double v) { return df(v); }
 
 // ---------------------------------------------------------------------------
 // Word layout.  A field of N reals of type S per site is stored as NW words
@@ -122,6 +126,35 @@ template <typename T> __device__ __forceinline__ cx<T> cjmadd(cx<T> a, cx<T> b, 
 }
 // multiply by i * s for s = +-1
 template <typename T> __device__ __forceinline__ cx<T> times_i(cx<T> a) { return {-a.i, a.r}; }
+
+// |psi|^2 of one site, accumulated in the arithmetic type of the data (FP64,
+// double-float, or FP32 for FP32 and FP16/BF16 data) and returned as a
+// double; sums over sites are FP64.  GB300 executes FP64 at 1/64 of its FP32
+// rate, so a per-site FP64 sum would make the norms fused into the FP32 and
+// half-precision kernels FP64-bound.
+template <typename T> __device__ __forceinline__ double site_norm2(const cx<T> (&a)[4][3]) {
+  T s = (T)0;
+#pragma unroll
+  for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      s = fma(a[sp][c].r, a[sp][c].r, s);
+      s = fma(a[sp][c].i, a[sp][c].i, s);
+    }
+  return (double)s;
+}
+
+// arithmetic type of a binary operation between fields of compute types A, B:
+// double-float if either is, else FP64 if either is, else FP32
+template <typename A, typename B> struct Wide { using type = float; };
+template <typename A> struct Wide<A, double> { using type = double; };
+template <typename B> struct Wide<double, B> { using type = double; };
+template <> struct Wide<double, double> { using type = double; };
+template <typename A> struct Wide<A, df> { using type = df; };
+template <typename B> struct Wide<df, B> { using type = df; };
+template <> struct Wide<df, df> { using type = df; };
+template <> struct Wide<df, double> { using type = df; };
+template <> struct Wide<double, df> { using type = df; };
 
 // ---------------------------------------------------------------------------
 // Geometry of one parity.  Sites are numbered lexicographically,

@@ -74,12 +74,19 @@ __device__ __forceinline__ void load_spinor(const FieldRef &f, long Vh, int r, l
   using T = typename Math<S>::T;
   S raw[24];
   load_reals<S, 24, STREAM>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
-  T sc = (T)1;
-  if (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
+  if constexpr (IsHalf<S>::value) {
+    const T sc = (T)__ldg(f.scale + (long)r * Vh + i);
 #pragma unroll
-  for (int a = 0; a < 4; a++)
+    for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) psi[a][c] = mk<T>(sc * (T)to_f(raw[6 * a + 2 * c]), sc * (T)to_f(raw[6 * a + 2 * c + 1]));
+      for (int c = 0; c < 3; c++)
+        psi[a][c] = mk<T>(sc * (T)to_f(raw[6 * a + 2 * c]), sc * (T)to_f(raw[6 * a + 2 * c + 1]));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+  }
 }
 
 // The same load without applying the FP16/BF16 scale: returns it instead, so
@@ -91,7 +98,7 @@ __device__ __forceinline__ typename Math<S>::T load_spinor_raw(const FieldRef &f
   S raw[24];
   load_reals<S, 24>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
   T sc = (T)1;
-  if (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
+  if constexpr (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -105,7 +112,7 @@ __device__ __forceinline__ void store_spinor(void *base, float *scale, long rhs_
   using T = typename Math<S>::T;
   S raw[24];
   T inv = (T)1;
-  if (IsHalf<S>::value) {
+  if constexpr (IsHalf<S>::value) {
     T m = (T)0;
 #pragma unroll
     for (int a = 0; a < 4; a++)
@@ -137,6 +144,20 @@ template <> __device__ __forceinline__ void store_spinor<double>(void *base, flo
     }
   void *b = reinterpret_cast<char *>(base) + (long)r * rhs_words * Words<double, 24>::W;
   store_reals<double, 24>(b, Vh, i, raw);
+}
+
+template <> __device__ __forceinline__ void store_spinor<df>(void *base, float *, long rhs_words, long Vh, int r, long i,
+                                                             const cx<df> (&psi)[4][3]) {
+  df raw[24];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      raw[6 * a + 2 * c] = psi[a][c].r;
+      raw[6 * a + 2 * c + 1] = psi[a][c].i;
+    }
+  void *b = reinterpret_cast<char *>(base) + (long)r * rhs_words * Words<df, 24>::W;
+  store_reals<df, 24>(b, Vh, i, raw);
 }
 
 // Link U_mu at site i of one parity; 12-real form rebuilds row 2 = conj(row0 x row1).
@@ -190,7 +211,7 @@ __device__ __forceinline__ typename Math<S>::T load_clover_block(const void *bas
   const void *b = reinterpret_cast<const char *>(base) + (long)blk * Wd::NW * Vh * Wd::W;
   load_reals<S, 36, true>(b, Vh, i, raw);
   T sc = (T)1;
-  if (IsHalf<S>::value) sc = (T)__ldg(scale + i);
+  if constexpr (IsHalf<S>::value) sc = (T)__ldg(scale + i);
 #pragma unroll
   for (int k = 0; k < 36; k++) m[k] = (T)to_f(raw[k]);
   return sc;  // the FP16/BF16 scale, applied to the products by the caller
@@ -326,6 +347,15 @@ template <int NR> struct LaunchCfg<float, NR> {
 template <int NR> struct LaunchCfg<double, NR> {
   static constexpr int threads = NR > 1 ? 128 : LQCD_T64, min_blocks = NR > 1 ? 1 : LQCD_M64;
 };
+#ifndef LQCD_TDF
+#define LQCD_TDF 128
+#endif
+#ifndef LQCD_MDF
+#define LQCD_MDF 1
+#endif
+template <int NR> struct LaunchCfg<df, NR> {
+  static constexpr int threads = NR > 1 ? 128 : LQCD_TDF, min_blocks = NR > 1 ? 1 : LQCD_MDF;
+};
 
 template <typename S, int R, int MODE, int NR>
 __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::min_blocks) dslash_kernel(const __grid_constant__ DslashParams P) {
@@ -450,14 +480,7 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::m
 #pragma unroll
     for (int r = 0; r < NR; r++) {
       store_spinor<S>(P.out, P.out_scale, out_words, P.g.Vh, rg * NR + r, h, acc[r]);
-      if (P.norm_partials) {
-        double s2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-          for (int c = 0; c < 3; c++) s2 += (double)acc[r][a][c].r * acc[r][a][c].r + (double)acc[r][a][c].i * acc[r][a][c].i;
-        nrm[r] = s2;
-      }
+      if (P.norm_partials) nrm[r] = site_norm2<T>(acc[r]);
     }
   }
   if (P.norm_partials) grid_reduce<NR>(nrm, P.norm_partials, P.norm_counter, P.norm_result, rg * NR, P.nrhs, P.norm_stride);

@@ -8,6 +8,7 @@ cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon,
     case LQCD_F32: return launch_dslash<float>(P, recon, mode, nr, st);
     case LQCD_F16: return launch_dslash<__half>(P, recon, mode, nr, st);
     case LQCD_BF16: return launch_dslash<__nv_bfloat16>(P, recon, mode, nr, st);
+    case LQCD_DF64: return launch_dslash<df>(P, recon, mode, nr, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -21,7 +21,9 @@ static cudaError_t launch_nr(const DslashParams &P, int nr, cudaStream_t st) {
   if (nr == 1) return launch_one<S, R, MODE, 1>(P, st);
   if constexpr (MODE != MODE_FOLDED_AINV) {
     if (nr == 2) return launch_one<S, R, MODE, 2>(P, st);
-    if (nr == 4) return launch_one<S, R, MODE, 4>(P, st);
+    // double-float accumulators for four right-hand sides exceed the register file
+    if constexpr (!std::is_same<S, df>::value)
+      if (nr == 4) return launch_one<S, R, MODE, 4>(P, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -35,18 +37,20 @@ static cudaError_t launch_mode(const DslashParams &P, int mode, int nr, cudaStre
     case MODE_LOCAL_A: return launch_nr<S, R, MODE_LOCAL_A>(P, nr, st);
     case MODE_FOLDED_AINV: return launch_nr<S, R, MODE_FOLDED_AINV>(P, nr, st);
     case MODE_CHEB:
-      // the Chebyshev step runs in the overlap's FP64 and FP32 sign functions only
-      if constexpr (std::is_same<S, double>::value || std::is_same<S, float>::value)
+      // the Chebyshev step runs in the overlap's FP64, DF64 and FP32 sign functions only
+      if constexpr (std::is_same<S, double>::value || std::is_same<S, float>::value || std::is_same<S, df>::value)
         return launch_nr<S, R, MODE_CHEB>(P, nr, st);
       break;
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename S, bool WITH18>
+template <typename S, bool WITH18, bool WITH12 = true>
 static cudaError_t launch_dslash_impl(const DslashParams &P, int recon, int mode, int nr, cudaStream_t st) {
   if (P.nrhs % nr != 0) return cudaErrorInvalidValue;
-  if (recon == 12) return launch_mode<S, 12>(P, mode, nr, st);
+  if constexpr (WITH12) {
+    if (recon == 12) return launch_mode<S, 12>(P, mode, nr, st);
+  }
   if constexpr (WITH18) {
     if (recon == 18) return launch_mode<S, 18>(P, mode, nr, st);
   }

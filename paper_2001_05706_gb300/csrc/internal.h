@@ -52,7 +52,7 @@ cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y
 // ---- dslash_<type>.cu
 cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);
 
-inline int prec_bytes(lqcd_prec p) { return p == LQCD_F64 ? 8 : p == LQCD_F32 ? 4 : 2; }
+inline int prec_bytes(lqcd_prec p) { return (p == LQCD_F64 || p == LQCD_DF64) ? 8 : p == LQCD_F32 ? 4 : 2; }
 inline bool prec_half(lqcd_prec p) { return p == LQCD_F16 || p == LQCD_BF16; }
 // 16-byte words of one spinor site (24 reals) in precision p
 inline long spinor_words(lqcd_prec p) { return 24L * prec_bytes(p) / 16; }
@@ -101,7 +101,7 @@ struct lqcd_ctx {
   double kappa = 0, csw = 0;
   bool have_kappa = false;
   bool clover_on = false;  // csw != 0 and built
-  CloverStore clov[4];
+  CloverStore clov[5];  // indexed by lqcd_prec
   double rho = 0;
   bool have_rho = false;
   // reduction scratch

@@ -103,6 +103,7 @@ cudaError_t pack_spinor(lqcd_prec prec, const Geom &g, int p, const double *cano
     case LQCD_F32: return pack_spinor_t<float>(g, p, canon, nrhs, out, scale, rhs_words, st);
     case LQCD_F16: return pack_spinor_t<__half>(g, p, canon, nrhs, out, scale, rhs_words, st);
     case LQCD_BF16: return pack_spinor_t<__nv_bfloat16>(g, p, canon, nrhs, out, scale, rhs_words, st);
+    case LQCD_DF64: return pack_spinor_t<df>(g, p, canon, nrhs, out, scale, rhs_words, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -114,6 +115,7 @@ cudaError_t unpack_spinor(lqcd_prec prec, const Geom &g, int p, const void *in, 
     case LQCD_F32: return unpack_spinor_t<float>(g, p, in, scale, rhs_words, nrhs, canon, st);
     case LQCD_F16: return unpack_spinor_t<__half>(g, p, in, scale, rhs_words, nrhs, canon, st);
     case LQCD_BF16: return unpack_spinor_t<__nv_bfloat16>(g, p, in, scale, rhs_words, nrhs, canon, st);
+    case LQCD_DF64: return unpack_spinor_t<df>(g, p, in, scale, rhs_words, nrhs, canon, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -134,6 +136,7 @@ static cudaError_t convert_from(lqcd_prec po, long Vh, int nrhs, const void *in,
     case LQCD_BF16:
       convert_spinor_kernel<SI, __nv_bfloat16><<<gr, 128, 0, st>>>(Vh, in, is, irw, out, os, orw, f);
       break;
+    case LQCD_DF64: convert_spinor_kernel<SI, df><<<gr, 128, 0, st>>>(Vh, in, is, irw, out, os, orw, f); break;
   }
   return cudaGetLastError();
 }
@@ -145,6 +148,7 @@ cudaError_t convert_spinor(lqcd_prec pi, lqcd_prec po, long Vh, int nrhs, const 
     case LQCD_F32: return convert_from<float>(po, Vh, nrhs, in, is, irw, out, os, orw, factor, st);
     case LQCD_F16: return convert_from<__half>(po, Vh, nrhs, in, is, irw, out, os, orw, factor, st);
     case LQCD_BF16: return convert_from<__nv_bfloat16>(po, Vh, nrhs, in, is, irw, out, os, orw, factor, st);
+    case LQCD_DF64: return convert_from<df>(po, Vh, nrhs, in, is, irw, out, os, orw, factor, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -168,8 +172,7 @@ __global__ void pack_links_kernel(Geom g, const double *__restrict__ U, void *ou
 }
 
 size_t link_bytes(lqcd_prec prec, int recon, long Vh) {
-  int b = prec == LQCD_F64 ? 8 : prec == LQCD_F32 ? 4 : 2;
-  return (size_t)8 * Vh * recon * b;
+  return (size_t)8 * Vh * recon * prec_bytes(prec);
 }
 
 template <typename S>
@@ -188,6 +191,7 @@ cudaError_t pack_links(lqcd_prec prec, const Geom &g, const double *U, int recon
     case LQCD_F32: return pack_links_t<float>(g, U, recon, out, st);
     case LQCD_F16: return pack_links_t<__half>(g, U, recon, out, st);
     case LQCD_BF16: return pack_links_t<__nv_bfloat16>(g, U, recon, out, st);
+    case LQCD_DF64: return pack_links_t<df>(g, U, recon, out, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -273,8 +277,7 @@ __global__ void pack_clover_kernel(long Vh, const double *__restrict__ in, void 
 }
 
 size_t clover_bytes(lqcd_prec prec, long Vh) {
-  int b = prec == LQCD_F64 ? 8 : prec == LQCD_F32 ? 4 : 2;
-  return (size_t)72 * b * Vh;
+  return (size_t)72 * prec_bytes(prec) * Vh;
 }
 
 cudaError_t pack_clover(lqcd_prec prec, long Vh, const double *in, void *out, float *scale, cudaStream_t st) {
@@ -284,6 +287,7 @@ cudaError_t pack_clover(lqcd_prec prec, long Vh, const double *in, void *out, fl
     case LQCD_F32: pack_clover_kernel<float><<<gr, 128, 0, st>>>(Vh, in, out, scale); break;
     case LQCD_F16: pack_clover_kernel<__half><<<gr, 128, 0, st>>>(Vh, in, out, scale); break;
     case LQCD_BF16: pack_clover_kernel<__nv_bfloat16><<<gr, 128, 0, st>>>(Vh, in, out, scale); break;
+    case LQCD_DF64: pack_clover_kernel<df><<<gr, 128, 0, st>>>(Vh, in, out, scale); break;
   }
   return cudaGetLastError();
 }

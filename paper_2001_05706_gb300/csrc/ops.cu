@@ -118,7 +118,7 @@ static void tune_store(const TuneKey &k, int nr) {
 
 static int default_nr(lqcd_prec prec, int mode, int nrhs) {
   if (mode == MODE_FOLDED_AINV) return 1;
-  if (prec == LQCD_F64) return nrhs % 2 == 0 ? 2 : 1;
+  if (prec == LQCD_F64 || prec == LQCD_DF64) return nrhs % 2 == 0 ? 2 : 1;
   if (nrhs % 4 == 0) return 4;
   if (nrhs % 2 == 0) return 2;
   return 1;
@@ -175,6 +175,8 @@ static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
                        FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
                        int g5_total, double *norm_result, int norm_stride, const FieldRef *zc, const double *cz) {
+  if (prec == LQCD_DF64 && recon != 18) return set_error(LQCD_ERR_ARG, "DF64 operators use 18-real links");
+  if (prec_half(prec) && recon != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 operators use 12-real links");
   DslashParams P{};
   P.g = c->geom;
   P.out_parity = out_p;
@@ -289,7 +291,8 @@ lqcd_status op_hw(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out
 lqcd_status op_hw_cheb(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out[2], FieldRef x[2], double t,
                        const FieldRef z[3][2], const double cz[3]) {
   if (!c->have_rho) return set_error(LQCD_ERR_STATE, "rho not set (call lqcd_set_rho)");
-  if (prec != LQCD_F64 && prec != LQCD_F32) return set_error(LQCD_ERR_ARG, "Chebyshev step needs FP64 or FP32");
+  if (prec != LQCD_F64 && prec != LQCD_F32 && prec != LQCD_DF64)
+    return set_error(LQCD_ERR_ARG, "Chebyshev step needs FP64, DF64 or FP32");
   for (int p = 0; p < 2; p++) {
     const FieldRef zp[3] = {z[0][p], z[1][p], z[2][p]};
     LQ_TRY(run_dslash(c, prec, recon, MODE_CHEB, p, nrhs, out[p], x[1 - p], x[p], kNone, t * (4.0 - c->rho),

@@ -85,19 +85,20 @@ struct Work {
   int nrhs;
   int recon64, recon_lo;
   lqcd_prec lo;
+  lqcd_prec hp;  // precision of the CG (plain) or of the reliable updates (mixed): FP64 or DF64
   double tol, delta;
   int max_iter, check_every;
   std::vector<double> bnorm;  // ||b|| full lattice per RHS
-  lqcd_field *bhat, *x64, *r64;  // FP64: bhat_o, x (full), r_o
+  lqcd_field *bhat, *x64, *r64;  // precision hp: bhat_o, x (odd part used), r_o
   lqcd_solve_info *info;
 };
 
-// FP64 CGLS: iterate until every RHS has ||r|| <= target, where r is
-// recomputed as bhat - Mhat x before a right-hand side is accepted.
-lqcd_status cgls_fp64(Work &W, SolveBufs &B) {
+// Plain CGLS in FP64 or DF64: iterate until every RHS has ||r|| <= target,
+// where r is recomputed as bhat - Mhat x before a right-hand side is accepted.
+lqcd_status cgls_plain(Work &W, SolveBufs &B) {
   lqcd_ctx *c = W.c;
   const int n = W.nrhs;
-  const lqcd_prec P = LQCD_F64;
+  const lqcd_prec P = W.hp;
   lqcd_field *s, *p, *q, *ye;
   LQ_TRY(temp_field(c, P, LQCD_ODD, n, 20, &s));
   LQ_TRY(temp_field(c, P, LQCD_ODD, n, 21, &p));
@@ -289,9 +290,9 @@ struct MixedCG {
     LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 33, &ye));
     LQ_TRY(temp_field(c, L, LQCD_ODD, n, 34, &r));
     LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 35, &xlo));
-    LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 37, &xtry));
-    LQ_TRY(temp_field(c, LQCD_F64, LQCD_ODD, n, 38, &rtry));
-    LQ_TRY(temp_field(c, LQCD_F64, LQCD_EVEN, n, 23, &ye64));
+    LQ_TRY(temp_field(c, W.hp, LQCD_ODD, n, 37, &xtry));
+    LQ_TRY(temp_field(c, W.hp, LQCD_ODD, n, 38, &rtry));
+    LQ_TRY(temp_field(c, W.hp, LQCD_EVEN, n, 23, &ye64));
     LQ_TRY(ensure_partials(c, n));
     if (dev_malloc((void **)&dcr, sizeof(CtrlRhs) * n) != cudaSuccess ||
         dev_malloc((void **)&dcg, sizeof(CtrlGlobal)) != cudaSuccess ||
@@ -307,7 +308,7 @@ struct MixedCG {
     rhs_bytes64 = (size_t)xtry->rhs_words() * 16;
     xlo_bytes = (size_t)xlo->rhs_words() * 16 * n;
     // r64 = bhat - Mhat64 x64 -> sigma
-    LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
+    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
                    &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
     LQ_TRY(read_scalars(c, B, n));
@@ -330,7 +331,7 @@ struct MixedCG {
     LQ_TRY(write_scalars(c, B, n));
     LQ_TRY(write_fac(c, B, n));
     // r_lo = r64 / sigma ; x_lo = 0 ; s = Mhat^dag r -> gamma[0] ; p = s
-    LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
+    LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
     LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
     LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
                    kScStride));
@@ -394,8 +395,8 @@ struct MixedCG {
     }
     LQ_TRY(write_fac(c, B, n));
     LQ_CU(cudaMemcpyAsync(xtry->data[1], W.x64->data[1], rhs_bytes64 * n, cudaMemcpyDeviceToDevice, c->stream));
-    LQ_CU(blas_axpy(LQCD_F64, LQCD_F32, c->Vh, n, xtry->mut(1), xlo->ref(1), B.fac, c->stream));
-    LQ_TRY(op_mhat(c, LQCD_F64, W.recon64, 0, n, rtry->mut(1), xtry->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
+    LQ_CU(blas_axpy(W.hp, LQCD_F32, c->Vh, n, xtry->mut(1), xlo->ref(1), B.fac, c->stream));
+    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, rtry->mut(1), xtry->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
                    &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
     W.info->reliable_updates += 1;
@@ -444,7 +445,7 @@ struct MixedCG {
     LQ_TRY(write_fac(c, B, 3 * n));
     LQ_TRY(upload_ctrl());
     LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
-    LQ_CU(blas_scale(L, LQCD_F64, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
+    LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
     LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
                    kScStride));
     LQ_CU(blas_axpy(L, L, c->Vh, n, p->mut(1), s->ref(1), B.fac + 2 * n, c->stream));
@@ -556,14 +557,19 @@ struct SolveJob {
   std::chrono::steady_clock::time_point t0;
 };
 
+// inner FP64 or DF64: the plain CG in that precision, no reliable updates
+bool plain_cg(const lqcd_solve_params *prm) { return prm->inner == LQCD_F64 || prm->inner == LQCD_DF64; }
+
 lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
   if (!c) return set_error(LQCD_ERR_ARG, "context is NULL");
   if (!prm) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (!(prm->tol > 0.0)) return set_error(LQCD_ERR_ARG, "tol must be > 0");
   if (prm->max_iter < 1) return set_error(LQCD_ERR_ARG, "max_iter must be >= 1");
   if (prm->nrhs < 1 || prm->nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
-  if ((int)prm->inner < 0 || (int)prm->inner > 3) return set_error(LQCD_ERR_ARG, "bad inner precision");
-  if (prm->inner != LQCD_F64 && !(prm->delta > 0.0 && prm->delta < 1.0))
+  if ((int)prm->inner < 0 || (int)prm->inner > 4) return set_error(LQCD_ERR_ARG, "bad inner precision");
+  if (prm->outer != LQCD_F64 && prm->outer != LQCD_DF64)
+    return set_error(LQCD_ERR_ARG, "outer precision must be LQCD_F64 or LQCD_DF64");
+  if (!plain_cg(prm) && !(prm->delta > 0.0 && prm->delta < 1.0))
     return set_error(LQCD_ERR_ARG, "delta must be in (0, 1)");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
@@ -626,6 +632,7 @@ lqcd_status job_prepare(SolveJob &J) {
   W.recon64 = prm->recon == 12 ? 12 : 18;
   W.recon_lo = prm->inner_recon == 18 ? 18 : 12;
   W.lo = prm->inner;
+  W.hp = prm->inner == LQCD_F64 ? LQCD_F64 : prm->inner == LQCD_DF64 ? LQCD_DF64 : prm->outer;
   W.tol = prm->tol;
   W.delta = prm->delta;
   W.max_iter = prm->max_iter;
@@ -646,6 +653,19 @@ lqcd_status job_prepare(SolveJob &J) {
   W.bhat = J.bhat;
   W.x64 = J.xf;
   W.r64 = J.r64;
+  if (W.hp == LQCD_DF64) {  // the recursion's own copies in double-float
+    lqcd_field *bh, *xh, *rh;
+    LQ_TRY(temp_field(c, LQCD_DF64, LQCD_ODD, n, 16, &bh));
+    LQ_TRY(temp_field(c, LQCD_DF64, LQCD_ODD, n, 17, &xh));
+    LQ_TRY(temp_field(c, LQCD_DF64, LQCD_ODD, n, 18, &rh));
+    LQ_CU(convert_spinor(LQCD_F64, LQCD_DF64, c->Vh, n, J.bhat->data[1], nullptr, J.bhat->rhs_words(), bh->data[1],
+                         nullptr, bh->rhs_words(), 1.0, c->stream));
+    LQ_CU(convert_spinor(LQCD_F64, LQCD_DF64, c->Vh, n, J.xf->data[1], nullptr, J.xf->rhs_words(), xh->data[1],
+                         nullptr, xh->rhs_words(), 1.0, c->stream));
+    W.bhat = bh;
+    W.x64 = xh;
+    W.r64 = rh;
+  }
   return LQCD_OK;
 }
 
@@ -654,6 +674,9 @@ lqcd_status job_finish(SolveJob &J, lqcd_status solve_status) {
   const int n = J.prm.nrhs;
   lqcd_solve_info *inf = J.inf;
   const int recon64 = J.W.recon64;
+  if (J.W.hp == LQCD_DF64)
+    LQ_CU(convert_spinor(LQCD_DF64, LQCD_F64, c->Vh, n, J.W.x64->data[1], nullptr, J.W.x64->rhs_words(),
+                         J.xf->data[1], nullptr, J.xf->rhs_words(), 1.0, c->stream));
   // reconstruct x_e, then the FP64 full-lattice residual b - M x
   LQ_TRY(op_reconstruct(c, LQCD_F64, recon64, n, J.xf->mut(0), J.bf->ref(0), J.xf->ref(1)));
   {
@@ -719,7 +742,7 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
   J.prm = *prm;
   J.inf = info;
   LQ_TRY(job_prepare(J));
-  const lqcd_status st = prm->inner == LQCD_F64 ? cgls_fp64(J.W, J.B) : cgls_mixed(J.W, J.B);
+  const lqcd_status st = plain_cg(prm) ? cgls_plain(J.W, J.B) : cgls_mixed(J.W, J.B);
   return job_finish(J, st);
 }
 
@@ -732,7 +755,7 @@ extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double 
                                         int on_device, const lqcd_solve_params *prm, lqcd_solve_info *infos) {
   if (!ctxs || !x || !b || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (nctx < 1 || nctx > 256) return set_error(LQCD_ERR_ARG, "nctx must be in 1..256");
-  if (prm->inner == LQCD_F64) return set_error(LQCD_ERR_ARG, "batched solves run the mixed-precision recursion");
+  if (plain_cg(prm)) return set_error(LQCD_ERR_ARG, "batched solves run the mixed-precision recursion");
   for (int i = 0; i < nctx; i++) {
     LQ_TRY(check_params(ctxs[i], prm));
     if (!x[i] || !b[i]) return set_error(LQCD_ERR_ARG, "NULL buffer for lattice %d", i);

@@ -1,7 +1,9 @@
 """GPU parity of the operator kernels against the FP64 oracle, through the C ABI.
 
-Tolerances (relative 2-norm over the output sites): 1e-12 for FP64 storage,
-1e-5 for FP32, 1e-2 for FP16/BF16 storage with FP32 arithmetic."""
+Tolerances (relative 2-norm over the output sites): 1e-12 for FP64 storage
+and for double-float (DF64: two FP32 numbers per real, ~2^-47 relative
+rounding per operation, a few hundred operations per output), 1e-5 for FP32,
+1e-2 for FP16/BF16 storage with FP32 arithmetic."""
 import numpy as np
 import pytest
 
@@ -11,7 +13,7 @@ from helpers import rel
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-2, "bf16": 1e-2}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-5, "f16": 1e-2, "bf16": 1e-2}
 KAPPA, CSW, RHO = 0.12, 1.0, 1.5
 
 
@@ -73,7 +75,8 @@ def clover_lattice(lib):
 
 
 @pytest.mark.parametrize("op", OPS)
-@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("df64", 18), ("f32", 18), ("f32", 12), ("f16", 12),
+                                        ("bf16", 12)])
 def test_ops_clover(clover_lattice, op, prec, recon):
     lat, U, A, Ai = clover_lattice
     psi = gen.gaussian_spinor(DIMS, 2001)[0]
@@ -83,23 +86,23 @@ def test_ops_clover(clover_lattice, op, prec, recon):
 
 
 @pytest.mark.parametrize("op", ["K2A", "MHAT", "MHAT_DAG", "M"])
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "bf16"])
 def test_ops_wilson(lib, op, prec):
     dims = (4, 4, 6, 8)
     lat, U, A, Ai = _setup(lib, dims, 0.3, 7, csw=0.0)
     psi = gen.gaussian_spinor(dims, 8)[0]
-    recon = 12
+    recon = 18 if prec == "df64" else 12  # DF64 keeps all 18 reals of a link
     out = lat.dslash(psi, op, prec, recon)
     assert rel(out, _oracle_op(op, dims, U, None, None, psi)) < TOL[prec]
     lat.close()
 
 
 @pytest.mark.parametrize("nrhs", [2, 3, 4, 12])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 def test_multi_rhs(clover_lattice, nrhs, prec):
     lat, U, A, Ai = clover_lattice
     psi = gen.gaussian_spinor(DIMS, 3000 + nrhs, nrhs=nrhs)
-    out = lat.dslash(psi, "MHAT", prec, 12)
+    out = lat.dslash(psi, "MHAT", prec, 18 if prec == "df64" else 12)
     for k in range(nrhs):
         assert rel(out[k], _oracle_op("MHAT", DIMS, U, A, Ai, psi[k])) < TOL[prec]
 
@@ -217,7 +220,7 @@ def _mhat_at_sites(dims, U, kappa, csw, x, sites):
     return np.stack([As[k] @ xf[s] - kappa**2 * Dy[k].reshape(12) for k, s in enumerate(sites)])
 
 
-@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f64", 18), ("f16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f64", 18), ("df64", 18), ("f16", 12)])
 def test_full_size_sampled(lib, prec, recon):
     L = lib
     dims = (32, 32, 32, 64)
@@ -252,3 +255,24 @@ def test_full_size_sampled(lib, prec, recon):
     expect = _mhat_at_sites(dims, U, kappa, csw, psi, sites)
     got = z.reshape(V, 12)[sites]
     assert rel(got, expect) < TOL[prec]
+
+
+def test_df64_rejects_12_real_links(clover_lattice, lib):
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 2001)[0]
+    with pytest.raises(lib.LqcdError) as e:
+        lat.dslash(psi, "MHAT", "df64", 12)
+    assert e.value.status == lib.LQCD_ERR_ARG and "18-real" in str(e.value)
+
+
+def test_df64_beats_fp32_and_tracks_fp64(clover_lattice):
+    """DF64 is not FP32 in disguise: its error against the oracle is orders
+    of magnitude below FP32's and within a small factor of FP64's."""
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 2011)[0]
+    expect = _oracle_op("MHAT", DIMS, U, A, Ai, psi)
+    e32 = rel(lat.dslash(psi, "MHAT", "f32", 18), expect)
+    e64 = rel(lat.dslash(psi, "MHAT", "f64", 18), expect)
+    edf = rel(lat.dslash(psi, "MHAT", "df64", 18), expect)
+    assert edf < 1e-5 * e32
+    assert edf < 1e-13 and e64 < 1e-14

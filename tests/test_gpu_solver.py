@@ -55,6 +55,59 @@ def test_mixed_clover(lib, inner):
     lat.close()
 
 
+def test_df64_cg_matches_fp64(lib):
+    """Plain CGLS in double-float arithmetic reaches the same 1e-10 true
+    residual (checked by the oracle) and the same solution as FP64 CGLS."""
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    xd, st, info = lat.solve(b, tol=1e-10, inner="df64", recon=18)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    x64, st64, info64 = lat.solve(b, tol=1e-10, inner="f64", recon=18)
+    assert st64 == lib.LQCD_OK
+    A = oracle.clover(dims, U, kappa, csw)
+    assert oracle.true_residual(dims, U, A, kappa, xd, b) <= 1e-10
+    assert rel(xd, x64) < 1e-8
+    # same recursion up to rounding: the iteration counts agree closely
+    assert abs(info.iters - info64.iters) <= 0.05 * info64.iters + 8
+    lat.close()
+
+
+@pytest.mark.parametrize("inner", ["f16", "bf16"])
+def test_mixed_with_df64_updates(lib, inner):
+    """Mixed solve whose reliable updates and accumulated solution are DF64."""
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003, nrhs=2)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner=inner, delta=0.1, recon=18, inner_recon=12, outer="df64")
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(2):
+        assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+    assert info.reliable_updates >= 1
+    lat.close()
+
+
+def test_solver_rejects_bad_outer(lib):
+    dims = (4, 4, 4, 4)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(gen.gauge_field(dims, 0.2, 5).view(np.float64))
+    lat.clover(0.12, 1.0)
+    b = gen.gaussian_spinor(dims, 6)[0]
+    with pytest.raises(lib.LqcdError) as e:
+        lat.solve(b, inner="f32", outer="f32")
+    assert e.value.status == lib.LQCD_ERR_ARG
+    lat.close()
+
+
 def test_multi_rhs_point_sources(lib):
     """12 point sources, mixed FP16 inner solver, every one to 1e-10."""
     dims = (8, 8, 8, 8)
