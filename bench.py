@@ -12,7 +12,7 @@ spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
                   [--no-solve] [--no-batch] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
-  python bench.py --overlap      (overlap set-up and 12-RHS solve on 16^3x32)
+  python bench.py --overlap [--high df64]   (overlap set-up and 12-RHS solve on 16^3x32)
   python bench.py --solve-lattice 48,48,48,96   (mixed vs FP64 solve only, on that lattice)
 
 --impl reference times the FP64 CPU oracle on the same workload (bounded
@@ -434,13 +434,14 @@ def run_overlap(args):
     dims = (16, 16, 16, 32)
     U = gen.gauge_field(dims, 0.1, 1005)
     b = gen.gaussian_spinor(dims, 2005, nrhs=12)
-    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "config": {
+    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "high": args.high, "config": {
         "workload": "overlap D_ov(m) = rho[1 + g5 sign(H_W)] + ..., 16^3x32, eps 0.1, rho 1.5, m 0.05, 20 low modes, "
                     "sign to 1e-10, 12 Gaussian RHS, CG on the normal equations with FP32 sign inside and FP64 "
                     "reliable updates"}}
     with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
         lat.load_gauge(U.view(np.float64))
-        prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400)
+        prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400,
+                               high=args.high)
         t0 = time.perf_counter()
         st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
         out["setup"] = {"seconds": time.perf_counter() - t0, "status": "ok" if st == 0 else L.lqcd_last_error(),
@@ -623,6 +624,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
+    ap.add_argument("--high", default="f64", choices=["f64", "df64"],
+                    help="--overlap: arithmetic of the FP64 parts (FP64 or double-float)")
     ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="f32")

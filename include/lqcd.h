@@ -257,6 +257,10 @@ typedef struct {
   double eig_tol;    /* target ||H_W v - lam v|| of every low mode (absolute, |v| = 1)   */
   int max_filter;    /* cap on subspace-iteration sweeps of the low-mode solver          */
   unsigned long long seed; /* seed of the random start block of the low-mode solver     */
+  lqcd_prec high;    /* arithmetic of the FP64 parts (the low-mode filter once it leaves   */
+                     /* FP32, the FP64 sign function and so D_ov, its CG and the mixed   */
+                     /* CG's reliable updates): LQCD_F64 (0, the default) or LQCD_DF64;  */
+                     /* fields, projections and Gram matrices stay FP64 either way       */
 } lqcd_overlap_params;
 
 typedef struct {

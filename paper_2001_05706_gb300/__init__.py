@@ -53,7 +53,7 @@ class lqcd_solve_params(ctypes.Structure):
 class lqcd_overlap_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("mass", ctypes.c_double), ("n_low", ctypes.c_int),
                 ("max_degree", ctypes.c_int), ("sign_tol", ctypes.c_double), ("eig_tol", ctypes.c_double),
-                ("max_filter", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("max_filter", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("high", ctypes.c_int)]
 
 
 class lqcd_overlap_info(ctypes.Structure):
@@ -263,8 +263,10 @@ def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):
 
 
 def overlap_params(rho=1.5, mass=0.0, n_low=20, max_degree=4000, sign_tol=1e-10, eig_tol=1e-11, max_filter=200,
-                   seed=7):
-    return lqcd_overlap_params(rho, mass, n_low, max_degree, sign_tol, eig_tol, max_filter, seed)
+                   seed=7, high=LQCD_F64):
+    if isinstance(high, str):
+        high = PREC[high]
+    return lqcd_overlap_params(rho, mass, n_low, max_degree, sign_tol, eig_tol, max_filter, seed, high)
 
 
 def lqcd_overlap_setup(ctx, params, raise_on_noconv=True):

@@ -90,7 +90,44 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
 
 __device__ __forceinline__ df to_f(df v) { return v; }
 
+// Compensated dot-product accumulator (the Dot2 scheme of Ogita, Rump and
+// Oishi, 2005, with double-float operands): the leading FP32 sum s takes each
+// exact leading product through TwoSum, while the rounding errors and the
+// low-order product terms collect in e; one renormalisation at the end.  The
+// dependency chain through s is one addition per product instead of a full
+// double-float fma, and each product costs 12 FP32 operations instead of 15.
+struct dfacc {
+  float s, e;
+};
+
+__device__ __forceinline__ void dfacc_madd(dfacc &a, df x, df y) {  // a += x * y
+  const float p = __fmul_rn(x.hi, y.hi);
+  float pe = __fmaf_rn(x.hi, y.hi, -p);
+  pe = __fmaf_rn(x.hi, y.lo, pe);
+  pe = __fmaf_rn(x.lo, y.hi, pe);
+  const df t = df_two_sum(a.s, p);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, pe));
+}
+
+__device__ __forceinline__ df dfacc_value(dfacc a) {
+  const df t = df_two_sum(a.s, a.e);
+  return t;
+}
+
+// acc + x with the low parts summed lazily: TwoSum of the leading parts, no
+// renormalisation (|lo| may grow to a few ulp of hi over a handful of
+// additions; the next multiplication or df operation absorbs it)
+__device__ __forceinline__ df df_lazy_add(df acc, df x) {
+  const df t = df_two_sum(acc.hi, x.hi);
+  return df(t.hi, __fadd_rn(acc.lo, __fadd_rn(t.lo, x.lo)));
+}
+
+// s * a for s = +-1 (or any power of two): exact, two multiplications
+__device__ __forceinline__ df sgn_mul(df s, df a) { return df(__fmul_rn(s.hi, a.hi), __fmul_rn(s.hi, a.lo)); }
+
 }  // namespace dfmath
 using dfmath::df;
+using dfmath::dfacc;
 
 }  // namespace lqcd

@@ -16,6 +16,8 @@
 // contraction, so this runs on the CUDA cores; it is HBM-bound for FP32 and
 // half storage and FP64-ALU-bound for FP64 on GB300.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -200,6 +202,36 @@ __device__ __forceinline__ void herm6_mul(const T (&m)[36], const cx<T> (&v)[6],
     }
 }
 
+// The same product in double-float, with compensated accumulators for the
+// six outputs (each a sum of eleven real products per component).
+__device__ __forceinline__ void herm6_mul(const df (&m)[36], const cx<df> (&v)[6], cx<df> (&o)[6]) {
+  dfacc re[6], im[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    re[i] = dfacc{0.0f, 0.0f};
+    im[i] = dfacc{0.0f, 0.0f};
+    dfacc_madd(re[i], m[i], v[i].r);
+    dfacc_madd(im[i], m[i], v[i].i);
+  }
+#pragma unroll
+  for (int i = 1; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      const int k = 6 + 2 * (i * (i - 1) / 2 + j);
+      const df lr = m[k], li = m[k + 1];
+      dfacc_madd(re[i], lr, v[j].r);  // L_ij v_j
+      dfacc_madd(re[i], -li, v[j].i);
+      dfacc_madd(im[i], lr, v[j].i);
+      dfacc_madd(im[i], li, v[j].r);
+      dfacc_madd(re[j], lr, v[i].r);  // conj(L_ij) v_i
+      dfacc_madd(re[j], li, v[i].i);
+      dfacc_madd(im[j], lr, v[i].i);
+      dfacc_madd(im[j], -li, v[i].r);
+    }
+#pragma unroll
+  for (int i = 0; i < 6; i++) o[i] = mk<df>(dfacc_value(re[i]), dfacc_value(im[i]));
+}
+
 // Clover storage of one parity: two blocks of 36 reals, block-major,
 // [blk][words][Vh], plus one FP32 scale per site for FP16/BF16.
 template <typename S>
@@ -232,7 +264,7 @@ __device__ __forceinline__ void clover_apply(const void *base, const float *scal
       cx<T> v[6], o[6];
 #pragma unroll
       for (int k = 0; k < 6; k++) v[k] = psi[r][2 * blk + k / 3][k % 3];
-      herm6_mul<T>(m, v, o);
+      herm6_mul(m, v, o);
 #pragma unroll
       for (int k = 0; k < 6; k++) psi[r][2 * blk + k / 3][k % 3] = IsHalf<S>::value ? sc * o[k] : o[k];
     }
@@ -242,26 +274,30 @@ __device__ __forceinline__ void clover_apply(const void *base, const float *scal
 // ---------------------------------------------------------------------------
 // spin projection and reconstruction, (1 + s g_mu), s = +-1
 // ---------------------------------------------------------------------------
+// s * a for the sign s = +-1 (double-float: two exact multiplications)
+template <typename T> __device__ __forceinline__ T sgn_mul(T s, T a) { return s * a; }
+template <typename T> __device__ __forceinline__ cx<T> sgn_mul(T s, cx<T> a) { return {sgn_mul(s, a.r), sgn_mul(s, a.i)}; }
+
 template <typename T>
 __device__ __forceinline__ void project(int mu, T s, const cx<T> (&p)[4][3], cx<T> (&h)[2][3]) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     switch (mu) {
       case 0:  // B = [[0, i], [i, 0]]
-        h[0][c] = p[0][c] + s * times_i(p[3][c]);
-        h[1][c] = p[1][c] + s * times_i(p[2][c]);
+        h[0][c] = p[0][c] + sgn_mul(s, times_i(p[3][c]));
+        h[1][c] = p[1][c] + sgn_mul(s, times_i(p[2][c]));
         break;
       case 1:  // B = [[0, -1], [1, 0]]
-        h[0][c] = p[0][c] - s * p[3][c];
-        h[1][c] = p[1][c] + s * p[2][c];
+        h[0][c] = p[0][c] - sgn_mul(s, p[3][c]);
+        h[1][c] = p[1][c] + sgn_mul(s, p[2][c]);
         break;
       case 2:  // B = [[i, 0], [0, -i]]
-        h[0][c] = p[0][c] + s * times_i(p[2][c]);
-        h[1][c] = p[1][c] - s * times_i(p[3][c]);
+        h[0][c] = p[0][c] + sgn_mul(s, times_i(p[2][c]));
+        h[1][c] = p[1][c] - sgn_mul(s, times_i(p[3][c]));
         break;
       default:  // B = 1
-        h[0][c] = p[0][c] + s * p[2][c];
-        h[1][c] = p[1][c] + s * p[3][c];
+        h[0][c] = p[0][c] + sgn_mul(s, p[2][c]);
+        h[1][c] = p[1][c] + sgn_mul(s, p[3][c]);
         break;
     }
   }
@@ -297,6 +333,37 @@ __device__ __forceinline__ void reconstruct(int mu, T s, T f, const cx<T> (&h)[2
   }
 }
 
+// The same in double-float for f = +-1 (df storage carries no scale): sign
+// flips are exact, and the sixteen additions into each accumulator over the
+// eight directions take the lazy TwoSum form (8 FP32 operations, not 15)
+__device__ __forceinline__ void reconstruct(int mu, df s, df f, const cx<df> (&h)[2][3], cx<df> (&acc)[4][3]) {
+  const df fs = sgn_mul(f, s);
+  auto add = [](cx<df> &a, df xr, df xi) { a = mk<df>(df_lazy_add(a.r, xr), df_lazy_add(a.i, xi)); };
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    add(acc[0][c], sgn_mul(f, h[0][c].r), sgn_mul(f, h[0][c].i));
+    add(acc[1][c], sgn_mul(f, h[1][c].r), sgn_mul(f, h[1][c].i));
+    switch (mu) {
+      case 0:
+        add(acc[2][c], sgn_mul(fs, h[1][c].i), -sgn_mul(fs, h[1][c].r));
+        add(acc[3][c], sgn_mul(fs, h[0][c].i), -sgn_mul(fs, h[0][c].r));
+        break;
+      case 1:
+        add(acc[2][c], sgn_mul(fs, h[1][c].r), sgn_mul(fs, h[1][c].i));
+        add(acc[3][c], -sgn_mul(fs, h[0][c].r), -sgn_mul(fs, h[0][c].i));
+        break;
+      case 2:
+        add(acc[2][c], sgn_mul(fs, h[0][c].i), -sgn_mul(fs, h[0][c].r));
+        add(acc[3][c], -sgn_mul(fs, h[1][c].i), sgn_mul(fs, h[1][c].r));
+        break;
+      default:
+        add(acc[2][c], sgn_mul(fs, h[0][c].r), sgn_mul(fs, h[0][c].i));
+        add(acc[3][c], sgn_mul(fs, h[1][c].r), sgn_mul(fs, h[1][c].i));
+        break;
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void link_mul(const cx<T> (&U)[3][3], bool dag, const cx<T> (&h)[2][3],
                                          cx<T> (&o)[2][3]) {
@@ -309,6 +376,157 @@ __device__ __forceinline__ void link_mul(const cx<T> (&U)[3][3], bool dag, const
       for (int c = 0; c < 3; c++) t = dag ? cjmadd(U[c][r], h[a][c], t) : cmadd(U[r][c], h[a][c], t);
       o[a][r] = t;
     }
+}
+
+// The same product in double-float with compensated accumulators.
+__device__ __forceinline__ void link_mul(const cx<df> (&U)[3][3], bool dag, const cx<df> (&h)[2][3],
+                                         cx<df> (&o)[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      dfacc re{0.0f, 0.0f}, im{0.0f, 0.0f};
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const cx<df> u = dag ? U[c][r] : U[r][c];
+        const cx<df> v = h[a][c];
+        dfacc_madd(re, u.r, v.r);
+        dfacc_madd(re, dag ? u.i : -u.i, v.i);
+        dfacc_madd(im, u.r, v.i);
+        dfacc_madd(im, dag ? -u.i : u.i, v.r);
+      }
+      o[a][r] = mk<df>(dfacc_value(re), dfacc_value(im));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Software-pipelined neighbour gathers (LQCD_PIPE): the link and neighbour
+// spinor of direction k + 2 are copied global -> shared by cp.async (LDGSTS)
+// while direction k is computed, so the loads in flight hold no registers.
+// Every thread owns its staging slots; no block barrier is involved.
+// ---------------------------------------------------------------------------
+#ifndef LQCD_PIPE
+#define LQCD_PIPE 0
+#endif
+
+// global -> shared copy of B bytes; `dep` is an unused operand that makes the
+// copy wait for a value combined from every word of the slot's previous
+// contents, so the reads of that slot are complete before it is overwritten
+template <int B>
+__device__ __forceinline__ void cp_async_after(void *smem, const void *gmem, unsigned dep) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B), "r"(dep) : "memory");
+}
+template <typename W> __device__ __forceinline__ unsigned first_bits(const W &v) {
+  return *reinterpret_cast<const unsigned *>(&v);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename S, int R, int TB> struct HopStage {
+  using WS = Words<S, 24>;
+  using WL = Words<S, R>;
+  typename WordT<WS::W>::type sp[2][WS::NW][TB];
+  typename WordT<WL::W>::type ln[2][WL::NW][TB];
+  float sc[2][TB];
+};
+
+// the hop sum of one right-hand side (NR = 1) with a two-deep cp.async pipeline
+template <typename S, int R, int TB>
+__device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int p, int rg, const Coords &xc,
+                                              cx<typename Math<S>::T> (&acc)[4][3]) {
+  using T = typename Math<S>::T;
+  using St = HopStage<S, R, TB>;
+  using WS = typename St::WS;
+  using WL = typename St::WL;
+  __shared__ St st;
+  const int tid = threadIdx.x;
+  const long Vh = P.g.Vh;
+  const char *spb = reinterpret_cast<const char *>(rhs_base<S>(P.in.data, P.in.rhs_words, rg));
+  const float *scb = IsHalf<S>::value ? P.in.scale + (long)rg * Vh : nullptr;
+  auto issue = [&](int k, unsigned dep) {
+    const int mu = k >> 1, b = k & 1;
+    const long n = neighbour(P.g, xc, h, mu, (k & 1) ? -1 : +1);
+#pragma unroll
+    for (int w = 0; w < WS::NW; w++) cp_async_after<WS::W>(&st.sp[b][w][tid], spb + ((long)w * Vh + n) * WS::W, dep);
+    if constexpr (IsHalf<S>::value) cp_async_after<4>(&st.sc[b][tid], scb + n, dep);
+    const char *lb = reinterpret_cast<const char *>((k & 1) ? P.links[mu][1 - p] : P.links[mu][p]);
+    const long li = (k & 1) ? n : h;
+#pragma unroll
+    for (int w = 0; w < WL::NW; w++) cp_async_after<WL::W>(&st.ln[b][w][tid], lb + ((long)w * Vh + li) * WL::W, dep);
+    cp_async_commit();
+  };
+  issue(0, 0u);
+  issue(1, 0u);
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const int mu = k >> 1, dir = (k & 1) ? -1 : +1, b = k & 1;
+    if (k < 7)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    S raw[24];
+    unsigned dep = 0;
+#pragma unroll
+    for (int w = 0; w < WS::NW; w++) {
+      const auto v = st.sp[b][w][tid];
+      dep |= first_bits(v);
+      const S *q = reinterpret_cast<const S *>(&v);
+#pragma unroll
+      for (int j = 0; j < WS::PER; j++) raw[w * WS::PER + j] = q[j];
+    }
+    S lraw[R];
+#pragma unroll
+    for (int w = 0; w < WL::NW; w++) {
+      const auto v = st.ln[b][w][tid];
+      dep |= first_bits(v);
+      const S *q = reinterpret_cast<const S *>(&v);
+#pragma unroll
+      for (int j = 0; j < WL::PER; j++) lraw[w * WL::PER + j] = q[j];
+    }
+    T f = (T)1;
+    if constexpr (IsHalf<S>::value) {
+      f = (T)st.sc[b][tid];
+      dep |= __float_as_uint(f);
+    }
+    cx<T> psi[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+    cx<T> U[3][3];
+#pragma unroll
+    for (int r = 0; r < R / 6; r++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) U[r][c] = mk<T>((T)to_f(lraw[6 * r + 2 * c]), (T)to_f(lraw[6 * r + 2 * c + 1]));
+    if (R == 12) {
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const int a = (j + 1) % 3, bb = (j + 2) % 3;
+        cx<T> t = U[0][a] * U[1][bb] - U[0][bb] * U[1][a];
+        U[2][j] = conjg(t);
+      }
+    }
+    // the slot is free once its values are in registers: the next copy into it
+    // depends on all of its words
+    if (k + 2 < 8) issue(k + 2, dep);
+    const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
+    if (wrap) f = -f;
+    if (P.g5_in) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        psi[2][c] = (T)-1 * psi[2][c];
+        psi[3][c] = (T)-1 * psi[3][c];
+      }
+    }
+    const T s = dir > 0 ? (T)-1 : (T)1;
+    cx<T> hh[2][3], uh[2][3];
+    project<T>(mu, s, psi, hh);
+    link_mul(U, dir < 0, hh, uh);
+    reconstruct(mu, s, f, uh, acc);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -338,27 +556,30 @@ __device__ __forceinline__ void link_mul(const cx<T> (&U)[3][3], bool dag, const
 #endif
 // Kernels carrying several right-hand sides per thread need their registers:
 // they keep 128 threads and no cap.
-template <typename S, int NR> struct LaunchCfg {
+template <typename S, int NR, int MODE> struct LaunchCfg {
   static constexpr int threads = NR > 1 ? 128 : LQCD_T16, min_blocks = NR > 1 ? 1 : LQCD_M16;
 };
-template <int NR> struct LaunchCfg<float, NR> {
+template <int NR, int MODE> struct LaunchCfg<float, NR, MODE> {
   static constexpr int threads = NR > 1 ? 128 : LQCD_T32, min_blocks = NR > 1 ? 1 : LQCD_M32;
 };
-template <int NR> struct LaunchCfg<double, NR> {
+template <int NR, int MODE> struct LaunchCfg<double, NR, MODE> {
   static constexpr int threads = NR > 1 ? 128 : LQCD_T64, min_blocks = NR > 1 ? 1 : LQCD_M64;
 };
-#ifndef LQCD_TDF
-#define LQCD_TDF 128
-#endif
-#ifndef LQCD_MDF
-#define LQCD_MDF 1
-#endif
-template <int NR> struct LaunchCfg<df, NR> {
-  static constexpr int threads = NR > 1 ? 128 : LQCD_TDF, min_blocks = NR > 1 ? 1 : LQCD_MDF;
+// Double-float keeps ~200 live FP32 registers per site; measured at 32^3x64
+// (K2a / K2b ms): 255 registers, 8 warps per SM: 1.89 / 1.92; 168 registers
+// (three 128-thread blocks): 1.31 / 1.40; 128 registers (four 128-thread
+// blocks): 1.20 / 1.61, the hop-only kernel tolerating its ~400 B of spills
+// while the clover-and-local kernel's 650 B cost more than the extra warps
+// gain; 204 registers (five 64-thread blocks): 1.30 / 1.39.  Hop-only modes
+// take 128 registers, modes with a local term 204.
+template <int NR, int MODE> struct LaunchCfg<df, NR, MODE> {
+  static constexpr bool hop_only = MODE == MODE_HOP || MODE == MODE_HOP_AINV;
+  static constexpr int threads = NR > 1 ? 128 : (hop_only ? 128 : 64);
+  static constexpr int min_blocks = NR > 1 ? 1 : (hop_only ? 4 : 5);
 };
 
 template <typename S, int R, int MODE, int NR>
-__global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::min_blocks) dslash_kernel(const __grid_constant__ DslashParams P) {
+__global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, NR, MODE>::min_blocks) dslash_kernel(const __grid_constant__ DslashParams P) {
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int rg = blockIdx.y;  // right-hand-side group
@@ -378,7 +599,11 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::m
         for (int c = 0; c < 3; c++) acc[r][a][c] = mk<T>(0, 0);
 
     const bool hop = P.in.data != nullptr && P.beta != 0.0;
-    if (hop) {
+    constexpr bool kPipe = LQCD_PIPE && NR == 1 && (std::is_same<S, float>::value || IsHalf<S>::value);
+    if (hop && kPipe) {
+      const Coords xc = site_coords(P.g, h, p);
+      hop_pipelined<S, R, LaunchCfg<S, NR, MODE>::threads>(P, h, p, rg, xc, acc[0]);
+    } else if (hop) {
       const Coords xc = site_coords(P.g, h, p);
 #pragma unroll
       for (int mu = 0; mu < 4; mu++) {
@@ -407,11 +632,13 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR>::threads, LaunchCfg<S, NR>::m
             }
             cx<T> hh[2][3], uh[2][3];
             project<T>(mu, s, psi, hh);
-            link_mul<T>(U, dir < 0, hh, uh);
-            reconstruct<T>(mu, s, f, uh, acc[r]);
+            link_mul(U, dir < 0, hh, uh);
+            reconstruct(mu, s, f, uh, acc[r]);
           }
         }
       }
+    }
+    if (hop) {
       const T beta = (T)P.beta;
 #pragma unroll
       for (int r = 0; r < NR; r++)

@@ -25,6 +25,8 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -45,6 +47,7 @@ struct OverlapState {
   double a = 0, b = 0;
   int degree = 0;
   cublasHandle_t blas = nullptr;
+  bool df = false;            // FP64 parts computed in double-float (prm.high == LQCD_DF64)
   double2 *dsmall = nullptr;  // device scratch for small matrices
   size_t dsmall_n = 0;
 };
@@ -63,6 +66,8 @@ void overlap_free(lqcd_ctx *c) {
 namespace {
 
 constexpr int kT = 256;
+// LQCD_OVERLAP_TRACE=1 prints one line per low-mode sweep to stderr
+const bool kOvTrace = std::getenv("LQCD_OVERLAP_TRACE") != nullptr;
 
 // ---- kernels on FULL FP64 fields: grid (blocks over words*Vh, nrhs, parity) --
 
@@ -201,7 +206,7 @@ lqcd_status small_scratch(lqcd_ctx *c, size_t n, double2 **p) {
 }
 
 long cwords(const lqcd_field *f) { return 12L * f->Vh; }  // complex numbers per RHS per parity
-size_t celem(const lqcd_field *f) { return f->prec == LQCD_F64 ? 16 : 8; }  // bytes per complex number
+size_t celem(const lqcd_field *f) { return 2 * (size_t)prec_bytes(f->prec); }  // bytes per complex number
 
 void *col(const lqcd_field *f, int p, int k) {
   return reinterpret_cast<char *>(f->data[p]) + (size_t)k * cwords(f) * celem(f);
@@ -341,6 +346,10 @@ lqcd_status to_dev(lqcd_ctx *c, const std::vector<zc> &h, double2 *d) {
 }
 
 lqcd_status new_full(lqcd_ctx *c, int nrhs, lqcd_field **f) { return lqcd_field_create(c, LQCD_F64, LQCD_FULL, nrhs, f); }
+lqcd_status new_prec(lqcd_ctx *c, lqcd_prec prec, int nrhs, lqcd_field **f) {
+  return lqcd_field_create(c, prec, LQCD_FULL, nrhs, f);
+}
+
 lqcd_status new_like(lqcd_ctx *c, const lqcd_field *ref, int nrhs, lqcd_field **f) {
   return lqcd_field_create(c, ref->prec, LQCD_FULL, nrhs, f);
 }
@@ -353,29 +362,34 @@ struct FieldGuard {
   }
 };
 
+// links of the H_W kernel: all 18 reals for FP64 and DF64, 12 for FP32
+int hw_recon(lqcd_prec p) { return (p == LQCD_F64 || p == LQCD_DF64) ? 18 : 12; }
+
 lqcd_status hw(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in) {
   MutField o[2] = {out->mut(0), out->mut(1)};
   FieldRef x[2] = {in->ref(0), in->ref(1)};
-  return op_hw(c, out->prec, out->prec == LQCD_F64 ? 18 : 12, nrhs, o, x, nullptr, 0);
+  return op_hw(c, out->prec, hw_recon(out->prec), nrhs, o, x, nullptr, 0);
 }
 
-// out = t H_W in + c1 z1 + c2 z2 + c3 z3 (z3 may be null), FULL fields
+// out = t H_W in + c1 z1 + c2 z2 + c3 z3 (a null z drops its term), FULL fields
 lqcd_status hw_cheb(lqcd_ctx *c, int nrhs, lqcd_field *out, const lqcd_field *in, double t, const lqcd_field *z1,
                     double c1, const lqcd_field *z2, double c2, const lqcd_field *z3, double c3) {
   MutField o[2] = {out->mut(0), out->mut(1)};
   FieldRef x[2] = {in->ref(0), in->ref(1)};
   const FieldRef none{nullptr, nullptr, 0};
-  const FieldRef z[3][2] = {{z1->ref(0), z1->ref(1)}, {z2->ref(0), z2->ref(1)},
-                            {z3 ? z3->ref(0) : none, z3 ? z3->ref(1) : none}};
-  const double cz[3] = {c1, c2, z3 ? c3 : 0.0};
-  return op_hw_cheb(c, out->prec, out->prec == LQCD_F64 ? 18 : 12, nrhs, o, x, t, z, cz);
+  const lqcd_field *zs[3] = {z1, z2, z3};
+  FieldRef z[3][2];
+  for (int k = 0; k < 3; k++)
+    for (int p = 0; p < 2; p++) z[k][p] = zs[k] ? zs[k]->ref(p) : none;
+  const double cz[3] = {z1 ? c1 : 0.0, z2 ? c2 : 0.0, z3 ? c3 : 0.0};
+  return op_hw_cheb(c, out->prec, hw_recon(out->prec), nrhs, o, x, t, z, cz);
 }
 
-// dst = src converted between precisions (FULL fields, first nrhs RHS)
-lqcd_status convert_full(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs) {
+// dst = factor * src converted between precisions (FULL fields, first nrhs RHS)
+lqcd_status convert_full(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int nrhs, double factor = 1.0) {
   for (int p = 0; p < 2; p++)
     LQ_CU(convert_spinor(src->prec, dst->prec, c->Vh, nrhs, src->data[p], src->scale[p], src->rhs_words(),
-                         dst->data[p], dst->scale[p], dst->rhs_words(), 1.0, c->stream));
+                         dst->data[p], dst->scale[p], dst->rhs_words(), factor, c->stream));
   return LQCD_OK;
 }
 
@@ -520,10 +534,14 @@ int cheb_degree(double a, double b, double tol, int nmax, std::vector<double> &c
 lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *out) {
   OverlapState &S = *c->ov;
   const bool f64 = in->prec == LQCD_F64;
+  // the recurrence of an FP64 sign function runs in double-float on request
+  const lqcd_prec rp = (f64 && S.df) ? LQCD_DF64 : in->prec;
   FieldGuard g;
-  lqcd_field *w, *b1, *b2, *h, *hh;
-  for (lqcd_field **q : {&w, &b1, &b2, &h, &hh}) {
-    LQ_TRY(new_like(c, in, nrhs, q));
+  lqcd_field *w, *wr, *b1, *b2, *h, *hh;
+  LQ_TRY(new_like(c, in, nrhs, &w));
+  g.f.push_back(w);
+  for (lqcd_field **q : {&b1, &b2, &h, &hh}) {
+    LQ_TRY(new_prec(c, rp, nrhs, q));
     g.f.push_back(*q);
   }
   LQ_TRY(copy_field(c, w, in, nrhs));
@@ -540,8 +558,16 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
   const double a = S.a, b = S.b;
   const double s2 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
   const int n = S.degree;
-  // b_n = c_n w
-  LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[n], 0.0, 0.0, 0.0));
+  // b_n = c_n w  (and w in the recurrence's precision)
+  if (rp != in->prec) {
+    LQ_TRY(new_prec(c, rp, nrhs, &wr));
+    g.f.push_back(wr);
+    LQ_TRY(convert_full(c, wr, w, nrhs));
+    LQ_TRY(convert_full(c, b1, w, nrhs, S.coef[n]));
+  } else {
+    wr = w;
+    LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[n], 0.0, 0.0, 0.0));
+  }
   // b_k = c_k w + 2 T b_{k+1} - b_{k+2} (k = n-1 .. 1), then P w = c_0 w + T b_1 - b_2
   // (n = 0: P w = c_0 w = b_0),
   // T = s2 H^2 + s0: the second H_W of each step carries the three-term update
@@ -550,14 +576,19 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
   for (int k = n - 1; k >= 0; k--) {
     const double t = k > 0 ? 2.0 : 1.0;
     LQ_TRY(hw(c, nrhs, h, b1));
-    LQ_TRY(hw_cheb(c, nrhs, hh, h, t * s2, w, S.coef[k], b1, t * s0, b2_zero ? nullptr : b2, -1.0));
+    LQ_TRY(hw_cheb(c, nrhs, hh, h, t * s2, wr, S.coef[k], b1, t * s0, b2_zero ? nullptr : b2, -1.0));
     b2_zero = false;
     lqcd_field *o = hh;
     hh = b2;
     b2 = b1;
     b1 = o;
   }
-  LQ_TRY(hw(c, nrhs, out, b1));  // H P(H^2) w
+  if (rp != in->prec) {  // H P(H^2) w, back to FP64
+    LQ_TRY(hw(c, nrhs, h, b1));
+    LQ_TRY(convert_full(c, out, h, nrhs));
+  } else {
+    LQ_TRY(hw(c, nrhs, out, b1));  // H P(H^2) w
+  }
   if (nl > 0) {
     double *dsg = c->results + 512;
     std::vector<double> sg(nl);
@@ -869,6 +900,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   if (prm->n_low < 0 || prm->n_low > 64) return set_error(LQCD_ERR_ARG, "n_low must be in 0..64");
   if (!(prm->sign_tol > 0) || !(prm->eig_tol > 0)) return set_error(LQCD_ERR_ARG, "tolerances must be > 0");
   if (prm->max_degree < 1 || prm->max_filter < 1) return set_error(LQCD_ERR_ARG, "max_degree, max_filter >= 1");
+  if (prm->high != LQCD_F64 && prm->high != LQCD_DF64) return set_error(LQCD_ERR_ARG, "high must be LQCD_F64 or LQCD_DF64");
   const auto t0 = std::chrono::steady_clock::now();
   lqcd_overlap_info local{};
   lqcd_overlap_info *inf = info ? info : &local;
@@ -877,6 +909,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   LQ_TRY(ensure_state(c));
   OverlapState &S = *c->ov;
   S.prm = *prm;
+  S.df = prm->high == LQCD_DF64;
   LQ_TRY(lqcd_set_rho(c, prm->rho));
   const long N = 12L * c->V;
   const int want = std::max(1, prm->n_low);
@@ -914,7 +947,8 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   int sweep = 0, kneed = want;
   bool fp32_phase = true;
   double prev_worst = 1e300;
-  lqcd_field *Xs = nullptr, *Ys = nullptr, *Hs = nullptr, *Ts = nullptr, *Zs = nullptr;  // FP32 filter block
+  lqcd_field *Bs[4] = {nullptr, nullptr, nullptr, nullptr};  // FP32 filter block
+  lqcd_field *Bd[4] = {nullptr, nullptr, nullptr, nullptr};  // double-float filter block
   bool converged = false;
   for (;; sweep++) {
     // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
@@ -969,37 +1003,43 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     // FP32 filtering injects ~1e-7 relative noise: use it only while the
     // residuals are large and still falling, FP64 from then on
     if (fp32_phase && (worst < 1e-4 || worst > 0.5 * prev_worst)) fp32_phase = false;
+    if (kOvTrace)
+      std::fprintf(stderr, "lqcd overlap: sweep %d worst %.3e kneed %d mu[kneed-1] %.6f mu[m-1] %.6f %s\n", sweep,
+                   worst, kneed, mus[kneed - 1], mus[m - 1], fp32_phase ? "fp32" : (S.df ? "df64" : "fp64"));
     prev_worst = worst;
     const bool low = fp32_phase;
     const double lo = std::min(std::max(mus[m - 1], 1.02 * mus[kneed - 1]), 0.9 * bmax), hi = bmax;
     const double s2 = 2.0 / (hi - lo), s0 = -(hi + lo) / (hi - lo);
     const int deg = 16;
-    lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T, *fZ = Z;
-    if (low) {
-      if (!Xs) {
-        for (lqcd_field **q : {&Xs, &Ys, &Hs, &Ts, &Zs}) {
-          LQ_TRY(lqcd_field_create(c, LQCD_F32, LQCD_FULL, m, q));
-          g.f.push_back(*q);
+    // the filter runs on a copy of X in FP32 (early sweeps) or double-float
+    // (on request), in place in FP64 otherwise
+    const lqcd_prec fp = low ? LQCD_F32 : S.df ? LQCD_DF64 : LQCD_F64;
+    lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T;
+    if (fp != LQCD_F64) {
+      lqcd_field **blk = fp == LQCD_F32 ? Bs : Bd;
+      if (!blk[0]) {
+        for (int q = 0; q < 4; q++) {
+          LQ_TRY(lqcd_field_create(c, fp, LQCD_FULL, m, &blk[q]));
+          g.f.push_back(blk[q]);
         }
       }
-      LQ_TRY(convert_full(c, Xs, X, m));
-      fX = Xs, fY = Ys, fH = Hs, fT = Ts, fZ = Zs;
+      LQ_TRY(convert_full(c, blk[0], X, m));
+      fX = blk[0], fY = blk[1], fH = blk[2], fT = blk[3];
     }
-    // Y0 = X, Y1 = T(X) into Y, Y_{k+1} = 2 T(Y_k) - Y_{k-1}
+    // Y0 = X, Y1 = T(X), Y_{k+1} = 2 T(Y_k) - Y_{k-1} with T = s2 H^2 + s0: the
+    // second H_W of each step carries the update in its epilogue
     LQ_TRY(hw(c, m, fT, fX));
-    LQ_TRY(hw(c, m, fZ, fT));
-    LQ_TRY(clenshaw(c, m, fY, nullptr, fZ, fX, nullptr, 0.0, 1.0, s2, s0));
+    LQ_TRY(hw_cheb(c, m, fY, fT, s2, fX, s0, nullptr, 0.0, nullptr, 0.0));
     lqcd_field *prev = fX, *cur = fY, *nxt = fH;
     for (int k = 1; k < deg; k++) {
       LQ_TRY(hw(c, m, fT, cur));
-      LQ_TRY(hw(c, m, fZ, fT));
-      LQ_TRY(clenshaw(c, m, nxt, nullptr, fZ, cur, prev, 0.0, 2.0, s2, s0));
+      LQ_TRY(hw_cheb(c, m, nxt, fT, 2.0 * s2, cur, 2.0 * s0, prev, -1.0, nullptr, 0.0));
       lqcd_field *t = prev;
       prev = cur;
       cur = nxt;
       nxt = t;
     }
-    if (low) {
+    if (fp != LQCD_F64) {
       LQ_TRY(convert_full(c, X, cur, m));
     } else if (cur != X) {  // the filtered block becomes X; the other two are scratch
       lqcd_field *others[3] = {X, Y, HX};

@@ -2,7 +2,8 @@
 eigh), the polynomial sign function and D_ov (vs the oracle's evaluation with
 the same projected modes and interval), the free-field closed form, the
 Ginsparg-Wilson relation and the overlap solve (true residual recomputed by
-the oracle)."""
+the oracle).  Each runs with the FP64 parts in FP64 and in double-float
+(high = LQCD_DF64), to the same tolerances."""
 import numpy as np
 import pytest
 
@@ -24,10 +25,10 @@ def lib():
     return L
 
 
-def _setup(L, dims, U, n_low, mass=0.0, sign_tol=1e-12):
+def _setup(L, dims, U, n_low, mass=0.0, sign_tol=1e-12, high="f64"):
     lat = L.Lattice(dims)
     lat.load_gauge(U.view(np.float64))
-    prm = L.overlap_params(rho=RHO, mass=mass, n_low=n_low, sign_tol=sign_tol, eig_tol=1e-11)
+    prm = L.overlap_params(rho=RHO, mass=mass, n_low=n_low, sign_tol=sign_tol, eig_tol=1e-11, high=high)
     st, info = L.lqcd_overlap_setup(lat.ctx, prm)
     vecs = np.zeros((n_low,) + oracle.spinor_shape(dims), dtype=np.complex128)
     if n_low:
@@ -42,11 +43,11 @@ def _ov(L, lat, psi, op, nrhs=1, cg=None):
     return out
 
 
-@pytest.fixture(scope="module")
-def rough(lib):
+@pytest.fixture(scope="module", params=["f64", "df64"])
+def rough(lib, request):
     dims = (4, 4, 4, 4)
     U = gen.gauge_field(dims, 0.3, 23)
-    lat, info, lam, vecs = _setup(lib, dims, U, 8)
+    lat, info, lam, vecs = _setup(lib, dims, U, 8, high=request.param)
     yield dims, U, lat, info, lam, vecs
     lat.close()
 
@@ -101,11 +102,12 @@ def test_multi_rhs_sign(rough, lib):
         assert rel(out[k], _ov(L, lat, psi[k], L.LQCD_OV_SIGN)) < 1e-12
 
 
-def test_free_field_closed_form(lib):
+@pytest.mark.parametrize("high", ["f64", "df64"])
+def test_free_field_closed_form(lib, high):
     L = lib
     dims = (4, 4, 4, 4)
     U = gen.unit_gauge(dims)
-    lat, info, lam, vecs = _setup(L, dims, U, 4, mass=0.05)
+    lat, info, lam, vecs = _setup(L, dims, U, 4, mass=0.05, high=high)
     g = [oracle.gamma(mu) for mu in range(4)]
     m = 0.05
     rng = np.random.default_rng(2)
@@ -120,13 +122,13 @@ def test_free_field_closed_form(lib):
     lat.close()
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32"])
-def test_overlap_solve(lib, inner):
+@pytest.mark.parametrize("inner,high", [("f64", "f64"), ("f32", "f64"), ("f64", "df64"), ("f32", "df64")])
+def test_overlap_solve(lib, inner, high):
     L = lib
     dims = (4, 4, 4, 8)
     U = gen.gauge_field(dims, 0.1, 5)
     m = 0.05
-    lat, info, lam, vecs = _setup(L, dims, U, 6, mass=m)
+    lat, info, lam, vecs = _setup(L, dims, U, 6, mass=m, high=high)
     b = gen.gaussian_spinor(dims, 2005, nrhs=2)
     cg = L.solve_params(tol=1e-10, max_iter=2000, nrhs=2, inner=L.PREC[inner], delta=0.1)
     x = np.zeros_like(b)
