@@ -1,6 +1,7 @@
 // The C ABI: argument checking, context and field lifetime, gauge and
 // clover set-up, and operator application on canonical arrays and on
 // device-resident fields.  Declarations and their contracts: include/lqcd.h.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -164,6 +165,11 @@ lqcd_status lqcd_destroy(lqcd_ctx *c) {
   if (c->h_results) cudaFreeHost(c->h_results);
   for (int k = 0; k < 2; k++)
     if (c->canon[k]) cudaFree(c->canon[k]);
+  for (int k = 0; k < 2; k++) {
+    if (c->copy_stream[k]) cudaStreamDestroy(c->copy_stream[k]);
+    for (cudaEvent_t &e : c->chunk_event[k])
+      if (e) cudaEventDestroy(e);
+  }
   cudaGetLastError();
   delete c;
   return LQCD_OK;
@@ -451,6 +457,90 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *c, const lqcd_field *f, double *result) {
   return LQCD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Mhat on host canonical arrays, pipelined over chunks of whole time slices
+// (contiguous in the canonical t-slowest order): chunk copies in on one copy
+// stream, out on another, while the context's stream packs the odd sites of
+// each arrived chunk, runs K2a on a chunk once its neighbour chunks are in,
+// K2b once K2a has covered its neighbours, and unpacks it.  Chunks arrive in
+// the order last, 0, 1, ..., so the periodic wrap is available early; the
+// host link carries both directions at once.
+lqcd_status mhat_host_pipelined(lqcd_ctx *c, double *out, const double *in, int nrhs, lqcd_prec prec, int recon,
+                                int nch) {
+  const size_t n = (size_t)nrhs * c->V * 24;
+  double *din, *dout;
+  LQ_TRY(staging(c, 0, n, &din));
+  LQ_TRY(staging(c, 1, n, &dout));
+  lqcd_field *fin, *fy, *fout;
+  LQ_TRY(temp_field(c, prec, LQCD_ODD, nrhs, 2, &fin));
+  LQ_TRY(temp_field(c, prec, LQCD_EVEN, nrhs, 0, &fy));
+  LQ_TRY(temp_field(c, prec, LQCD_ODD, nrhs, 3, &fout));
+  for (int k = 0; k < 2; k++) {
+    if (!c->copy_stream[k]) LQ_CU(cudaStreamCreateWithFlags(&c->copy_stream[k], cudaStreamNonBlocking));
+    for (int j = 0; j < nch; j++)
+      if (!c->chunk_event[k][j]) LQ_CU(cudaEventCreateWithFlags(&c->chunk_event[k][j], cudaEventDisableTiming));
+  }
+  cudaStream_t sin = c->copy_stream[0], sout = c->copy_stream[1];
+  const long slab = c->V / nch;  // sites per chunk
+  const long hs = slab / 2;      // sites per parity per chunk
+  const size_t bytes = (size_t)slab * 24 * sizeof(double);
+  // the copies may not start before earlier work on the context's stream is done with the staging buffers
+  LQ_CU(cudaEventRecord(c->chunk_event[1][0], c->stream));
+  LQ_CU(cudaStreamWaitEvent(sin, c->chunk_event[1][0], 0));
+  LQ_CU(cudaStreamWaitEvent(sout, c->chunk_event[1][0], 0));
+  auto order = [&](int i) { return i == 0 ? nch - 1 : i - 1; };
+  for (int i = 0; i < nch; i++) {
+    const int ch = order(i);
+    for (int r = 0; r < nrhs; r++) {
+      const size_t off = ((size_t)r * c->V + (size_t)ch * slab) * 24;
+      LQ_CU(cudaMemcpyAsync(din + off, in + off, bytes, cudaMemcpyHostToDevice, sin));
+    }
+    LQ_CU(cudaEventRecord(c->chunk_event[0][ch], sin));
+  }
+  auto k2a = [&](int ch) {
+    return op_k2a(c, prec, recon, 0, nrhs, fy->mut(0), fin->ref(1), ch * hs, (ch + 1) * hs);
+  };
+  auto k2b_out = [&](int ch) -> lqcd_status {
+    const FieldRef none{nullptr, nullptr, 0};
+    LQ_TRY(op_k2b(c, prec, recon, 0, nrhs, fout->mut(1), fin->ref(1), fy->ref(0), none, 0.0, nullptr, 0, ch * hs,
+                  (ch + 1) * hs));
+    LQ_CU(unpack_spinor(prec, c->geom, 1, fout->data[1], fout->scale[1], fout->rhs_words(), nrhs, dout, c->stream,
+                        ch * hs, (ch + 1) * hs));
+    LQ_CU(zero_parity(c->geom, 0, dout, nrhs, c->stream, ch * hs, (ch + 1) * hs));
+    LQ_CU(cudaEventRecord(c->chunk_event[1][ch], c->stream));
+    LQ_CU(cudaStreamWaitEvent(sout, c->chunk_event[1][ch], 0));
+    for (int r = 0; r < nrhs; r++) {
+      const size_t off = ((size_t)r * c->V + (size_t)ch * slab) * 24;
+      LQ_CU(cudaMemcpyAsync(out + off, dout + off, bytes, cudaMemcpyDeviceToHost, sout));
+    }
+    return LQCD_OK;
+  };
+  // arrival i brings chunk i-1 (i >= 1): then K2a of chunk i-2 has both
+  // neighbours, and K2b of chunk i-3 has K2a on both of its neighbours
+  for (int i = 0; i < nch; i++) {
+    const int ch = order(i);
+    LQ_CU(cudaStreamWaitEvent(c->stream, c->chunk_event[0][ch], 0));
+    LQ_CU(pack_spinor(prec, c->geom, 1, din, nrhs, fin->data[1], fin->scale[1], fin->rhs_words(), c->stream, ch * hs,
+                      (ch + 1) * hs));
+    if (i >= 2) LQ_TRY(k2a(i - 2));
+    if (i >= 4) LQ_TRY(k2b_out(i - 3));
+  }
+  LQ_TRY(k2a(nch - 2));
+  LQ_TRY(k2a(nch - 1));
+  for (int ch = std::max(1, nch - 3); ch < nch; ch++) LQ_TRY(k2b_out(ch));
+  LQ_TRY(k2b_out(0));
+  LQ_CU(cudaStreamSynchronize(sout));
+  LQ_CU(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 lqcd_status lqcd_dslash(lqcd_ctx *c, double *out, const double *in, int nrhs, lqcd_op op, lqcd_prec prec,
                         lqcd_recon recon, int on_device) {
   LQ_TRY(check_ctx(c));
@@ -460,6 +550,12 @@ lqcd_status lqcd_dslash(lqcd_ctx *c, double *out, const double *in, int nrhs, lq
   if ((int)prec < 0 || (int)prec > 4) return set_error(LQCD_ERR_ARG, "bad precision");
   if ((int)op < 0 || (int)op > 8) return set_error(LQCD_ERR_ARG, "bad op");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
+  if (!on_device && op == LQCD_OP_MHAT && c->have_kappa && !std::getenv("LQCD_NO_PIPELINE")) {
+    // chunks of whole time slices, at least 4 of them, at most 16
+    int nch = 16;
+    while (nch >= 4 && c->dims[3] % nch != 0) nch /= 2;
+    if (nch >= 4) return mhat_host_pipelined(c, out, in, nrhs, prec, (int)recon, nch);
+  }
   const size_t n = (size_t)nrhs * c->V * 24;
   const double *din = in;
   double *dout = out;

@@ -40,6 +40,7 @@ struct FieldRef {
 
 struct DslashParams {
   Geom g;
+  long h0, h1;  // output sites [h0, h1) of the parity (a whole parity: 0, Vh)
   int out_parity;
   int nrhs;
   void *out;
@@ -406,7 +407,7 @@ __device__ __forceinline__ void link_mul(const cx<df> (&U)[3][3], bool dag, cons
 // Every thread owns its staging slots; no block barrier is involved.
 // ---------------------------------------------------------------------------
 #ifndef LQCD_PIPE
-#define LQCD_PIPE 0
+#define LQCD_PIPE 1
 #endif
 
 // global -> shared copy of B bytes; `dep` is an unused operand that makes the
@@ -533,9 +534,13 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
 // the kernel
 // ---------------------------------------------------------------------------
 // Launch shape per storage type: threads per block and the minimum number
-// of resident blocks per SM promised to the register allocator.  The kernel
-// is latency-bound (long-scoreboard stalls dominate), so more resident warps
-// pay as long as the register cap causes no spills.
+// of resident blocks per SM promised to the register allocator.  Without the
+// cp.async pipeline the kernel was latency-bound (long-scoreboard stalls) and
+// ran best with many small register-capped blocks (FP32: ten 64-thread blocks
+// per SM, K2a/K2b 0.147/0.162 ms at 32^3x64; FP16: sixteen, 0.117/0.128).
+// With the gathers staged through shared memory the loads in flight cost no
+// registers, and a looser cap pays: FP32 eight blocks (128 registers)
+// 0.137/0.150, FP16 ten (102 registers) 0.105/0.113, BF16 0.116/0.122.
 #ifndef LQCD_T64
 #define LQCD_T64 128
 #endif
@@ -546,13 +551,13 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
 #define LQCD_T32 64
 #endif
 #ifndef LQCD_M32
-#define LQCD_M32 10
+#define LQCD_M32 8
 #endif
 #ifndef LQCD_T16
 #define LQCD_T16 64
 #endif
 #ifndef LQCD_M16
-#define LQCD_M16 16
+#define LQCD_M16 10
 #endif
 // Kernels carrying several right-hand sides per thread need their registers:
 // they keep 128 threads and no cap.
@@ -581,9 +586,9 @@ template <int NR, int MODE> struct LaunchCfg<df, NR, MODE> {
 template <typename S, int R, int MODE, int NR>
 __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, NR, MODE>::min_blocks) dslash_kernel(const __grid_constant__ DslashParams P) {
   using T = typename Math<S>::T;
-  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long h = P.h0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int rg = blockIdx.y;  // right-hand-side group
-  const bool valid = h < P.g.Vh;
+  const bool valid = h < P.h1;
   const int p = P.out_parity;
   double nrm[NR];
 #pragma unroll

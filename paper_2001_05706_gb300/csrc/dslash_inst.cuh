@@ -11,7 +11,7 @@ namespace lqcd {
 template <typename S, int R, int MODE, int NR>
 static cudaError_t launch_one(const DslashParams &P, cudaStream_t st) {
   constexpr int T = LaunchCfg<S, NR, MODE>::threads;
-  dim3 grid((unsigned)((P.g.Vh + T - 1) / T), (unsigned)(P.nrhs / NR));
+  dim3 grid((unsigned)((P.h1 - P.h0 + T - 1) / T), (unsigned)(P.nrhs / NR));
   dslash_kernel<S, R, MODE, NR><<<grid, T, 0, st>>>(P);
   return cudaGetLastError();
 }

@@ -18,11 +18,12 @@ struct MutField {
 };
 
 // ---- layout.cu
+// [h0, h1): the sites of parity p converted (h1 < 0: to the end of the parity)
 cudaError_t pack_spinor(lqcd_prec prec, const Geom &g, int p, const double *canon, int nrhs, void *out, float *scale,
-                        long rhs_words, cudaStream_t st);
+                        long rhs_words, cudaStream_t st, long h0 = 0, long h1 = -1);
 cudaError_t unpack_spinor(lqcd_prec prec, const Geom &g, int p, const void *in, const float *scale, long rhs_words,
-                          int nrhs, double *canon, cudaStream_t st);
-cudaError_t zero_parity(const Geom &g, int p, double *canon, int nrhs, cudaStream_t st);
+                          int nrhs, double *canon, cudaStream_t st, long h0 = 0, long h1 = -1);
+cudaError_t zero_parity(const Geom &g, int p, double *canon, int nrhs, cudaStream_t st, long h0 = 0, long h1 = -1);
 cudaError_t convert_spinor(lqcd_prec pi, lqcd_prec po, long Vh, int nrhs, const void *in, const float *is, long irw,
                            void *out, float *os, long orw, double factor, cudaStream_t st);
 size_t link_bytes(lqcd_prec prec, int recon, long Vh);
@@ -113,6 +114,9 @@ struct lqcd_ctx {
   // canonical staging for host <-> device transfers
   double *canon[2] = {nullptr, nullptr};
   size_t canon_n[2] = {0, 0};
+  // copy streams and per-chunk events of the pipelined host-buffer dslash
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};
+  cudaEvent_t chunk_event[2][64] = {};
   // cached intermediate fields (key: 10*prec + nrhs*1000 + slot)
   std::map<long, lqcd_field *> temps;
   // overlap operator state (low modes, Chebyshev coefficients), overlap.cu
@@ -150,12 +154,14 @@ lqcd_status ensure_partials(lqcd_ctx *c, int nrhs);
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
                        FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
                        int g5_total, double *norm_result, int norm_stride, const FieldRef *zc = nullptr,
-                       const double *cz = nullptr);
+                       const double *cz = nullptr, long h0 = 0, long h1 = -1);
 // y_e = A_ee^-1 D_eo x_o (g5 on the input if dagger)
-lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o);
+lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o,
+                   long h0 = 0, long h1 = -1);
 // z_o = [zf +gz*] (A_oo x_o - kappa^2 [g5] D_oe y_e), optional norm
 lqcd_status op_k2b(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
-                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride);
+                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride, long h0 = 0,
+                   long h1 = -1);
 // out_o = Mhat x_o or Mhat^dag x_o, y_e scratch
 lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
                     MutField y_e, FieldRef zf, double gz, double *norm_result, int norm_stride);

@@ -17,10 +17,10 @@ __device__ __forceinline__ long lex_of(const Geom &g, long h, int p) {
 // ---------------------------------------------------------------------------
 template <typename S>
 __global__ void pack_spinor_kernel(Geom g, int p, const double *__restrict__ canon, long V, void *out, float *scale,
-                                   long rhs_words) {
-  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                                   long rhs_words, long h0, long h1) {
+  const long h = h0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (h >= g.Vh) return;
+  if (h >= h1) return;
   const long s = lex_of(g, h, p);
   const double2 *src = reinterpret_cast<const double2 *>(canon + ((long)r * V + s) * 24);
   using T = typename Math<S>::T;
@@ -35,10 +35,10 @@ __global__ void pack_spinor_kernel(Geom g, int p, const double *__restrict__ can
 
 template <typename S>
 __global__ void unpack_spinor_kernel(Geom g, int p, const void *in, const float *scale, long rhs_words,
-                                     double *__restrict__ canon, long V) {
-  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                                     double *__restrict__ canon, long V, long h0, long h1) {
+  const long h = h0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (h >= g.Vh) return;
+  if (h >= h1) return;
   const long s = lex_of(g, h, p);
   FieldRef f{in, scale, rhs_words};
   using T = typename Math<S>::T;
@@ -50,10 +50,10 @@ __global__ void unpack_spinor_kernel(Geom g, int p, const void *in, const float 
 }
 
 // zero the sites of parity p in a canonical array (nrhs fields)
-__global__ void zero_parity_kernel(Geom g, int p, double *canon, long V) {
-  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void zero_parity_kernel(Geom g, int p, double *canon, long V, long h0, long h1) {
+  const long h = h0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (h >= g.Vh) return;
+  if (h >= h1) return;
   const long s = lex_of(g, h, p);
   double2 *dst = reinterpret_cast<double2 *>(canon + ((long)r * V + s) * 24);
 #pragma unroll
@@ -83,45 +83,53 @@ static dim3 grid2(long n, int y, int t) { return dim3((unsigned)((n + t - 1) / t
 
 template <typename S>
 static cudaError_t pack_spinor_t(const Geom &g, int p, const double *canon, int nrhs, void *out, float *scale,
-                                 long rhs_words, cudaStream_t st) {
+                                 long rhs_words, cudaStream_t st, long h0, long h1) {
   long V = 2 * g.Vh;
-  pack_spinor_kernel<S><<<grid2(g.Vh, nrhs, 128), 128, 0, st>>>(g, p, canon, V, out, scale, rhs_words);
+  pack_spinor_kernel<S><<<grid2(h1 - h0, nrhs, 128), 128, 0, st>>>(g, p, canon, V, out, scale, rhs_words, h0, h1);
   return cudaGetLastError();
 }
 template <typename S>
 static cudaError_t unpack_spinor_t(const Geom &g, int p, const void *in, const float *scale, long rhs_words,
-                                   int nrhs, double *canon, cudaStream_t st) {
+                                   int nrhs, double *canon, cudaStream_t st, long h0, long h1) {
   long V = 2 * g.Vh;
-  unpack_spinor_kernel<S><<<grid2(g.Vh, nrhs, 128), 128, 0, st>>>(g, p, in, scale, rhs_words, canon, V);
+  unpack_spinor_kernel<S><<<grid2(h1 - h0, nrhs, 128), 128, 0, st>>>(g, p, in, scale, rhs_words, canon, V, h0, h1);
   return cudaGetLastError();
 }
 
+static bool bad_range(const Geom &g, long &h0, long &h1) {
+  if (h1 < 0) h1 = g.Vh;
+  return h0 < 0 || h1 > g.Vh || h0 >= h1;
+}
+
 cudaError_t pack_spinor(lqcd_prec prec, const Geom &g, int p, const double *canon, int nrhs, void *out, float *scale,
-                        long rhs_words, cudaStream_t st) {
+                        long rhs_words, cudaStream_t st, long h0, long h1) {
+  if (bad_range(g, h0, h1)) return cudaErrorInvalidValue;
   switch (prec) {
-    case LQCD_F64: return pack_spinor_t<double>(g, p, canon, nrhs, out, scale, rhs_words, st);
-    case LQCD_F32: return pack_spinor_t<float>(g, p, canon, nrhs, out, scale, rhs_words, st);
-    case LQCD_F16: return pack_spinor_t<__half>(g, p, canon, nrhs, out, scale, rhs_words, st);
-    case LQCD_BF16: return pack_spinor_t<__nv_bfloat16>(g, p, canon, nrhs, out, scale, rhs_words, st);
-    case LQCD_DF64: return pack_spinor_t<df>(g, p, canon, nrhs, out, scale, rhs_words, st);
+    case LQCD_F64: return pack_spinor_t<double>(g, p, canon, nrhs, out, scale, rhs_words, st, h0, h1);
+    case LQCD_F32: return pack_spinor_t<float>(g, p, canon, nrhs, out, scale, rhs_words, st, h0, h1);
+    case LQCD_F16: return pack_spinor_t<__half>(g, p, canon, nrhs, out, scale, rhs_words, st, h0, h1);
+    case LQCD_BF16: return pack_spinor_t<__nv_bfloat16>(g, p, canon, nrhs, out, scale, rhs_words, st, h0, h1);
+    case LQCD_DF64: return pack_spinor_t<df>(g, p, canon, nrhs, out, scale, rhs_words, st, h0, h1);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t unpack_spinor(lqcd_prec prec, const Geom &g, int p, const void *in, const float *scale, long rhs_words,
-                          int nrhs, double *canon, cudaStream_t st) {
+                          int nrhs, double *canon, cudaStream_t st, long h0, long h1) {
+  if (bad_range(g, h0, h1)) return cudaErrorInvalidValue;
   switch (prec) {
-    case LQCD_F64: return unpack_spinor_t<double>(g, p, in, scale, rhs_words, nrhs, canon, st);
-    case LQCD_F32: return unpack_spinor_t<float>(g, p, in, scale, rhs_words, nrhs, canon, st);
-    case LQCD_F16: return unpack_spinor_t<__half>(g, p, in, scale, rhs_words, nrhs, canon, st);
-    case LQCD_BF16: return unpack_spinor_t<__nv_bfloat16>(g, p, in, scale, rhs_words, nrhs, canon, st);
-    case LQCD_DF64: return unpack_spinor_t<df>(g, p, in, scale, rhs_words, nrhs, canon, st);
+    case LQCD_F64: return unpack_spinor_t<double>(g, p, in, scale, rhs_words, nrhs, canon, st, h0, h1);
+    case LQCD_F32: return unpack_spinor_t<float>(g, p, in, scale, rhs_words, nrhs, canon, st, h0, h1);
+    case LQCD_F16: return unpack_spinor_t<__half>(g, p, in, scale, rhs_words, nrhs, canon, st, h0, h1);
+    case LQCD_BF16: return unpack_spinor_t<__nv_bfloat16>(g, p, in, scale, rhs_words, nrhs, canon, st, h0, h1);
+    case LQCD_DF64: return unpack_spinor_t<df>(g, p, in, scale, rhs_words, nrhs, canon, st, h0, h1);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t zero_parity(const Geom &g, int p, double *canon, int nrhs, cudaStream_t st) {
-  zero_parity_kernel<<<grid2(g.Vh, nrhs, 128), 128, 0, st>>>(g, p, canon, 2 * g.Vh);
+cudaError_t zero_parity(const Geom &g, int p, double *canon, int nrhs, cudaStream_t st, long h0, long h1) {
+  if (bad_range(g, h0, h1)) return cudaErrorInvalidValue;
+  zero_parity_kernel<<<grid2(h1 - h0, nrhs, 128), 128, 0, st>>>(g, p, canon, 2 * g.Vh, h0, h1);
   return cudaGetLastError();
 }
 

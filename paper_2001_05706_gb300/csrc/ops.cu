@@ -174,11 +174,15 @@ static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon
 
 lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out_p, int nrhs, MutField out, FieldRef in,
                        FieldRef xloc, FieldRef z, double alpha, double beta, double gz, int g5_in, int g5_hop,
-                       int g5_total, double *norm_result, int norm_stride, const FieldRef *zc, const double *cz) {
+                       int g5_total, double *norm_result, int norm_stride, const FieldRef *zc, const double *cz,
+                       long h0, long h1) {
   if (prec == LQCD_DF64 && recon != 18) return set_error(LQCD_ERR_ARG, "DF64 operators use 18-real links");
   if (prec_half(prec) && recon != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 operators use 12-real links");
   DslashParams P{};
   P.g = c->geom;
+  P.h0 = h0;
+  P.h1 = h1 < 0 ? c->Vh : h1;
+  if (P.h0 < 0 || P.h1 > c->Vh || P.h0 >= P.h1) return set_error(LQCD_ERR_ARG, "bad site range [%ld, %ld)", h0, h1);
   P.out_parity = out_p;
   P.nrhs = nrhs;
   P.out = out.data;
@@ -228,18 +232,20 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
 
 static const FieldRef kNone{nullptr, nullptr, 0};
 
-lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o) {
+lqcd_status op_k2a(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField y_e, FieldRef x_o, long h0,
+                   long h1) {
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
   const int mode = c->clover_on ? MODE_HOP_AINV : MODE_HOP;
-  return run_dslash(c, prec, recon, mode, 0, nrhs, y_e, x_o, kNone, kNone, 0.0, 1.0, 0.0, dagger, 0, 0, nullptr, 0);
+  return run_dslash(c, prec, recon, mode, 0, nrhs, y_e, x_o, kNone, kNone, 0.0, 1.0, 0.0, dagger, 0, 0, nullptr, 0,
+                    nullptr, nullptr, h0, h1);
 }
 
 lqcd_status op_k2b(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
-                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride) {
+                   FieldRef y_e, FieldRef zf, double gz, double *norm_result, int norm_stride, long h0, long h1) {
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
   const int mode = c->clover_on ? MODE_LOCAL_A : MODE_LOCAL_IDENT;
   return run_dslash(c, prec, recon, mode, 1, nrhs, out_o, y_e, x_o, zf, 1.0, -c->kappa * c->kappa, gz, 0, dagger, 0,
-                    norm_result, norm_stride);
+                    norm_result, norm_stride, nullptr, nullptr, h0, h1);
 }
 
 lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,

@@ -66,6 +66,12 @@ void overlap_free(lqcd_ctx *c) {
 namespace {
 
 constexpr int kT = 256;
+#ifndef LQCD_OV_BLOCK_MULT
+#define LQCD_OV_BLOCK_MULT 2
+#endif
+#ifndef LQCD_OV_FP32_RULE
+#define LQCD_OV_FP32_RULE 0
+#endif
 // LQCD_OVERLAP_TRACE=1 prints one line per low-mode sweep to stderr
 const bool kOvTrace = std::getenv("LQCD_OVERLAP_TRACE") != nullptr;
 
@@ -916,7 +922,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   // the block holds the wanted modes plus a margin wide enough to contain a
   // near-degenerate cluster at the edge (smooth fields keep the free field's
   // 12-fold momentum multiplets almost degenerate)
-  int m = std::min<long>(want + std::max(16, want), 96);
+  int m = std::min<long>(std::max(want + 16, LQCD_OV_BLOCK_MULT * want), 96);
   if (m > N) m = (int)N;
   if (want >= m) return set_error(LQCD_ERR_ARG, "lattice too small for %d low modes", want);
   FieldGuard g;
@@ -946,6 +952,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   double2 *d;
   int sweep = 0, kneed = want;
   bool fp32_phase = true;
+  int fp32_stall = 0;
   double prev_worst = 1e300;
   lqcd_field *Bs[4] = {nullptr, nullptr, nullptr, nullptr};  // FP32 filter block
   lqcd_field *Bd[4] = {nullptr, nullptr, nullptr, nullptr};  // double-float filter block
@@ -1002,7 +1009,15 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     for (int i = 0; i < kneed; i++) worst = std::max(worst, std::sqrt(r2[i]));
     // FP32 filtering injects ~1e-7 relative noise: use it only while the
     // residuals are large and still falling, FP64 from then on
+#if LQCD_OV_FP32_RULE == 0
     if (fp32_phase && (worst < 1e-4 || worst > 0.5 * prev_worst)) fp32_phase = false;
+#else
+    // FP32 filtering injects ~1e-7 relative noise (~1e-5 absolute on H_W^2,
+    // whose norm is ~42): keep it while the residuals are above 1e-4 and still
+    // falling (two sweeps in a row without a 5 % drop end it)
+    fp32_stall = worst > 0.95 * prev_worst ? fp32_stall + 1 : 0;
+    if (fp32_phase && (worst < 1e-4 || fp32_stall >= 2)) fp32_phase = false;
+#endif
     if (kOvTrace)
       std::fprintf(stderr, "lqcd overlap: sweep %d worst %.3e kneed %d mu[kneed-1] %.6f mu[m-1] %.6f %s\n", sweep,
                    worst, kneed, mus[kneed - 1], mus[m - 1], fp32_phase ? "fp32" : (S.df ? "df64" : "fp64"));
