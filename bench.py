@@ -314,12 +314,16 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
     bt = torch.from_numpy(b.view(np.float64).copy()).cuda()
     res = {"lattice": list(DIMS), "kappa": KAPPA, "c_sw": CSW, "tol": 1e-10, "source": "Gaussian, seed 2003"}
     xs = {}
-    for name, inner, outer in (("fp64", L.LQCD_F64, L.LQCD_F64), ("mixed_f32", L.LQCD_F32, L.LQCD_F64),
-                               ("mixed_f16", L.LQCD_F16, L.LQCD_F64), ("mixed_bf16", L.LQCD_BF16, L.LQCD_F64),
-                               ("df64", L.LQCD_DF64, L.LQCD_DF64), ("mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64)):
+    cg, bi = L.LQCD_SOLVER_CGLS, L.LQCD_SOLVER_BICGSTAB
+    for name, inner, outer, solver in (
+            ("fp64", L.LQCD_F64, L.LQCD_F64, cg), ("mixed_f32", L.LQCD_F32, L.LQCD_F64, cg),
+            ("mixed_f16", L.LQCD_F16, L.LQCD_F64, cg), ("mixed_bf16", L.LQCD_BF16, L.LQCD_F64, cg),
+            ("df64", L.LQCD_DF64, L.LQCD_DF64, cg), ("mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, cg),
+            ("bicgstab_fp64", L.LQCD_F64, L.LQCD_F64, bi), ("bicgstab_mixed_f16", L.LQCD_F16, L.LQCD_F64, bi),
+            ("bicgstab_mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, bi)):
         xt = torch.zeros_like(bt)
-        prm = L.solve_params(tol=1e-10, max_iter=40000, inner=inner, delta=0.1, recon=18, inner_recon=12,
-                             check_every=0, outer=outer)
+        prm = L.solve_params(tol=1e-10, max_iter=40000 if solver == cg else 4000, inner=inner, delta=0.1, recon=18,
+                             inner_recon=12, check_every=0, outer=outer, solver=solver)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
@@ -337,6 +341,11 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
         res["speedup_vs_fp64"] = res["fp64"]["seconds"] / res[best]["seconds"]
     if res["df64"]["status"] == "ok" and res["fp64"]["status"] == "ok":
         res["df64_cg_speedup_vs_fp64_cg"] = res["fp64"]["seconds"] / res["df64"]["seconds"]
+    ok = [k for k in res if isinstance(res[k], dict) and res[k].get("status") == "ok" and k != "fp64"]
+    if ok and res["fp64"]["status"] == "ok":
+        fastest = min(ok, key=lambda k: res[k]["seconds"])
+        res["fastest"] = fastest
+        res["fastest_speedup_vs_fp64_cg"] = res["fp64"]["seconds"] / res[fastest]["seconds"]
     if want_oracle and oracle_AAi is not None:
         import oracle
         A, _ = oracle_AAi

@@ -182,6 +182,13 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *ctx, const lqcd_field *field, double *res
 
 /* ---- solvers ----------------------------------------------------------- */
 
+/* Krylov recursion of lqcd_solve.  CGLS (CG on the normal equations Mhat^dag
+ * Mhat) is the paper's; BiCGStab (van der Vorst 1992) works on Mhat itself,
+ * with the same plain / mixed-precision-with-reliable-updates structure (no
+ * counterpart in the paper's text; QUDA's inverter family, which the paper
+ * ports, includes it).  lqcd_solve_batch runs CGLS only. */
+typedef enum { LQCD_SOLVER_CGLS = 0, LQCD_SOLVER_BICGSTAB = 1 } lqcd_solver;
+
 typedef struct {
   double tol;          /* target ||b - M x|| / ||b|| on the full lattice, > 0     */
   int max_iter;        /* cap on CG iterations (inner iterations when mixed)       */
@@ -197,6 +204,8 @@ typedef struct {
   lqcd_prec outer;     /* mixed solver: precision of the reliable updates and of  */
                        /* the accumulated solution, LQCD_F64 (0, the default) or  */
                        /* LQCD_DF64; the final residual check is FP64 either way  */
+  int solver;          /* lqcd_solver: LQCD_SOLVER_CGLS (0, the default: CG on    */
+                       /* the normal equations) or LQCD_SOLVER_BICGSTAB           */
 } lqcd_solve_params;
 
 typedef struct {

@@ -47,7 +47,7 @@ class lqcd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("use_x0", ctypes.c_int),
                 ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("outer", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class lqcd_overlap_params(ctypes.Structure):
@@ -295,9 +295,16 @@ def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):
     return st, info
 
 
+LQCD_SOLVER_CGLS, LQCD_SOLVER_BICGSTAB = 0, 1
+SOLVERS = {"cgls": LQCD_SOLVER_CGLS, "bicgstab": LQCD_SOLVER_BICGSTAB}
+
+
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,
-                 inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64):
-    return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every, outer)
+                 inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64, solver=LQCD_SOLVER_CGLS):
+    if isinstance(solver, str):
+        solver = SOLVERS[solver]
+    return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every, outer,
+                             solver)
 
 
 # ---- convenience ------------------------------------------------------------

@@ -409,6 +409,10 @@ __device__ __forceinline__ void link_mul(const cx<df> (&U)[3][3], bool dag, cons
 #ifndef LQCD_PIPE
 #define LQCD_PIPE 1
 #endif
+#ifndef LQCD_PIPE_UNROLL
+#define LQCD_PIPE_UNROLL 8
+#endif
+constexpr int kPipeUnroll = LQCD_PIPE_UNROLL;  // pragma arguments are not macro-expanded
 
 // global -> shared copy of B bytes; `dep` is an unused operand that makes the
 // copy wait for a value combined from every word of the slot's previous
@@ -461,7 +465,7 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
   };
   issue(0, 0u);
   issue(1, 0u);
-#pragma unroll
+#pragma unroll kPipeUnroll
   for (int k = 0; k < 8; k++) {
     const int mu = k >> 1, dir = (k & 1) ? -1 : +1, b = k & 1;
     if (k < 7)
@@ -527,6 +531,45 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
     project<T>(mu, s, psi, hh);
     link_mul(U, dir < 0, hh, uh);
     reconstruct(mu, s, f, uh, acc);
+  }
+}
+
+// The hop sum with the eight directions in a rolled loop: the double-float
+// kernel is ~15 k instructions per site when unrolled, and ncu shows it
+// stalled on instruction fetch ("no_instruction") more than on anything else;
+// one direction's code stays resident in the instruction cache.
+template <typename S, int R, int NR>
+__device__ __forceinline__ void hop_rolled(const DslashParams &P, long h, int p, int rg, const Coords &xc,
+                                           cx<typename Math<S>::T> (&acc)[NR][4][3]) {
+  using T = typename Math<S>::T;
+#pragma unroll 1
+  for (int k = 0; k < 8; k++) {
+    const int mu = k >> 1, dir = (k & 1) ? -1 : +1;
+    const long n = neighbour(P.g, xc, h, mu, dir);
+    const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
+    const T s = dir > 0 ? (T)-1 : (T)1;
+    cx<T> U[3][3];
+    if (dir > 0)
+      load_link<S, R>(P.links[mu][p], P.g.Vh, h, U);
+    else
+      load_link<S, R>(P.links[mu][1 - p], P.g.Vh, n, U);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      cx<T> psi[4][3];
+      T f = load_spinor_raw<S>(P.in, P.g.Vh, rg * NR + r, n, psi);
+      if (wrap) f = -f;
+      if (P.g5_in) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          psi[2][c] = (T)-1 * psi[2][c];
+          psi[3][c] = (T)-1 * psi[3][c];
+        }
+      }
+      cx<T> hh[2][3], uh[2][3];
+      project<T>(mu, s, psi, hh);
+      link_mul(U, dir < 0, hh, uh);
+      reconstruct(mu, s, f, uh, acc[r]);
+    }
   }
 }
 
@@ -608,6 +651,9 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, 
     if (hop && kPipe) {
       const Coords xc = site_coords(P.g, h, p);
       hop_pipelined<S, R, LaunchCfg<S, NR, MODE>::threads>(P, h, p, rg, xc, acc[0]);
+    } else if (hop && std::is_same<S, df>::value) {
+      const Coords xc = site_coords(P.g, h, p);
+      hop_rolled<S, R, NR>(P, h, p, rg, xc, acc);
     } else if (hop) {
       const Coords xc = site_coords(P.g, h, p);
 #pragma unroll

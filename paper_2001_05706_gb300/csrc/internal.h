@@ -50,6 +50,31 @@ cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y,
 cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
                        cudaStream_t st);
 
+// ---- bicgstab.cu: building blocks of BiCGStab (complex per-RHS scalars)
+struct BiScalars {
+  double2 rho, rho_old, alpha, omega, beta;
+  double rr;      // ||r||^2 of the last iteration
+  double active;  // 1.0 while this right-hand side iterates
+  double pad[3];
+};
+// reduction buffer: three regions of 3 doubles per right-hand side, written by
+// bi_dot3 / bi_xr as (complex dot re, im, squared norm): (rhat, v), (t, s) with
+// |t|^2, and (rhat, r) with |r|^2
+constexpr int kBiRed = 9;
+enum { BI_BETA = 0, BI_ALPHA = 1, BI_OMEGA = 2 };
+cudaError_t bi_scalar(int which, BiScalars *s, const double *red, int nrhs, cudaStream_t st);
+cudaError_t bi_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef r, FieldRef v, const BiScalars *s,
+                 cudaStream_t st);
+cudaError_t bi_s(lqcd_prec pv, long Vh, int nrhs, MutField sv, FieldRef r, FieldRef v, const BiScalars *s,
+                 cudaStream_t st);
+// red[3k..3k+2] = (a_k^H b_k) re, im, |a_k|^2  (red may be any of the slots)
+cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, unsigned *counter,
+                    double *red, cudaStream_t st);
+// x += alpha p + omega s; r = s - omega t; red = (rhat, r), |r|^2
+cudaError_t bi_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, FieldRef sv, FieldRef t,
+                  MutField r, FieldRef rhat, const BiScalars *s, double *partials, unsigned *counter, double *red,
+                  cudaStream_t st);
+
 // ---- dslash_<type>.cu
 cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);
 

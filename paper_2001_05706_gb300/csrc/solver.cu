@@ -539,6 +539,187 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
   return m.done ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "mixed CG did not converge in %d iterations", W.max_iter);
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab on Mhat x = bhat (building blocks in bicgstab.cu), one recursion per
+// right-hand side with its complex scalars in device memory.  Plain: vectors
+// in FP64 or DF64, and when an iterated residual reaches its target the true
+// residual bhat - Mhat x replaces r (converged right-hand sides stop).  Mixed:
+// vectors in FP32/FP16/BF16 (FP32 arithmetic) on the residual normalised to 1,
+// x_lo in FP32; when every active inner residual fell by delta (or reached its
+// target, or grew past 1e4) the high-precision solution absorbs sigma x_lo and
+// the residual is recomputed in FP64/DF64 (a reliable update).  The shadow
+// residual rhat is kept across updates; r takes the new residual, p and v are
+// rescaled with it, rho_old too, and rho = (rhat, r) is recomputed, so the
+// recursion continues where it was.  The host looks at the residuals every
+// check_every iterations.
+// ---------------------------------------------------------------------------
+lqcd_status bicgstab(Work &W, bool mixed) {
+  lqcd_ctx *c = W.c;
+  const int n = W.nrhs;
+  const lqcd_prec L = mixed ? W.lo : W.hp;
+  const int rec = mixed ? W.recon_lo : W.recon64;
+  lqcd_field *rhat, *r, *p, *v, *sv, *t, *ye, *ye64, *xlo = nullptr;
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 50, &rhat));
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 51, &r));
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 52, &p));
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 53, &v));
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 54, &sv));
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 55, &t));
+  LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 56, &ye));
+  LQ_TRY(temp_field(c, W.hp, LQCD_EVEN, n, 58, &ye64));
+  if (mixed) LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 57, &xlo));
+  LQ_TRY(ensure_partials(c, 3 * n));
+  struct Bufs {
+    BiScalars *ds = nullptr, *hs = nullptr;
+    double *red = nullptr, *hred = nullptr, *fac = nullptr, *hfac = nullptr;
+    ~Bufs() {
+      if (ds) cudaFree(ds);
+      if (red) cudaFree(red);
+      if (fac) cudaFree(fac);
+      if (hs) cudaFreeHost(hs);
+      if (hred) cudaFreeHost(hred);
+      if (hfac) cudaFreeHost(hfac);
+    }
+  } b;
+  if (dev_malloc((void **)&b.ds, sizeof(BiScalars) * n) != cudaSuccess ||
+      dev_malloc((void **)&b.red, sizeof(double) * kBiRed * n) != cudaSuccess ||
+      dev_malloc((void **)&b.fac, sizeof(double) * 2 * n) != cudaSuccess ||
+      cudaMallocHost(&b.hs, sizeof(BiScalars) * n) != cudaSuccess ||
+      cudaMallocHost(&b.hred, sizeof(double) * kBiRed * n) != cudaSuccess ||
+      cudaMallocHost(&b.hfac, sizeof(double) * 2 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ERR_OOM, "cannot allocate BiCGStab state");
+  }
+  double *red_rv = b.red, *red_ts = b.red + 3 * n, *red_xr = b.red + 6 * n;
+  const size_t vbytes = (size_t)r->rhs_words() * 16 * n;
+  const size_t sbytes = r->scale[1] ? sizeof(float) * c->Vh * n : 0;
+  std::vector<double> target(n), sigma(n, 1.0), nrm(n);
+  std::vector<char> active(n, 1);
+  for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
+  // high-precision residual r64 = bhat - Mhat x64 and its norms
+  auto true_residual = [&]() -> lqcd_status {
+    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
+                   c->results, 1));
+    LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n; k++) nrm[k] = std::sqrt(c->h_results[k]);
+    W.info->mhat_applies += 1;
+    return LQCD_OK;
+  };
+  auto copy_vec = [&](lqcd_field *dst, const lqcd_field *src) -> lqcd_status {
+    LQ_CU(cudaMemcpyAsync(dst->data[1], src->data[1], vbytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (sbytes) LQ_CU(cudaMemcpyAsync(dst->scale[1], src->scale[1], sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LQCD_OK;
+  };
+  // r from r64 (normalised when mixed), then rho = (rhat, r)
+  auto load_r = [&]() -> lqcd_status {
+    if (mixed) {
+      for (int k = 0; k < n; k++) b.hfac[k] = active[k] ? 1.0 / sigma[k] : 0.0;
+      LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), b.fac, c->stream));
+    } else {
+      LQ_TRY(copy_vec(r, W.r64));
+    }
+    return LQCD_OK;
+  };
+  LQ_TRY(true_residual());
+  int nact = 0;
+  for (int k = 0; k < n; k++) {
+    active[k] = nrm[k] > target[k];
+    nact += active[k];
+    if (mixed) sigma[k] = nrm[k] > 0 ? nrm[k] : 1.0;
+  }
+  if (nact == 0) return LQCD_OK;
+  LQ_TRY(load_r());
+  LQ_TRY(copy_vec(rhat, r));
+  for (lqcd_field *f : {p, v}) {
+    LQ_CU(cudaMemsetAsync(f->data[1], 0, vbytes, c->stream));
+    if (sbytes) LQ_CU(cudaMemsetAsync(f->scale[1], 0, sbytes, c->stream));
+  }
+  if (mixed) LQ_CU(cudaMemsetAsync(xlo->data[1], 0, (size_t)xlo->rhs_words() * 16 * n, c->stream));
+  for (int k = 0; k < n; k++) {
+    std::memset(&b.hs[k], 0, sizeof(BiScalars));
+    b.hs[k].rho_old = b.hs[k].alpha = b.hs[k].omega = make_double2(1.0, 0.0);
+    b.hs[k].active = active[k] ? 1.0 : 0.0;
+  }
+  LQ_CU(cudaMemcpyAsync(b.ds, b.hs, sizeof(BiScalars) * n, cudaMemcpyHostToDevice, c->stream));
+  LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, c->counter, red_xr, c->stream));
+  lqcd_field *x = mixed ? xlo : W.x64;
+  const lqcd_prec px = mixed ? LQCD_F32 : W.hp;
+  const double delta2 = W.delta * W.delta;
+  int it = 0;
+  while (true) {
+    for (int j = 0; j < W.check_every && it < W.max_iter; j++, it++) {
+      LQ_CU(bi_scalar(BI_BETA, b.ds, red_xr, n, c->stream));
+      LQ_CU(bi_p(L, c->Vh, n, p->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
+      LQ_TRY(op_mhat(c, L, rec, 0, n, v->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
+      LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), v->ref(1), c->partials, c->counter, red_rv, c->stream));
+      LQ_CU(bi_scalar(BI_ALPHA, b.ds, red_rv, n, c->stream));
+      LQ_CU(bi_s(L, c->Vh, n, sv->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
+      LQ_TRY(op_mhat(c, L, rec, 0, n, t->mut(1), sv->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
+      LQ_CU(bi_dot3(L, c->Vh, n, t->ref(1), sv->ref(1), c->partials, c->counter, red_ts, c->stream));
+      LQ_CU(bi_scalar(BI_OMEGA, b.ds, red_ts, n, c->stream));
+      LQ_CU(bi_xr(px, L, c->Vh, n, x->mut(1), p->ref(1), sv->ref(1), t->ref(1), r->mut(1), rhat->ref(1), b.ds,
+                  c->partials, c->counter, red_xr, c->stream));
+      W.info->mhat_applies += 2;
+    }
+    LQ_CU(cudaMemcpyAsync(b.hred, b.red, sizeof(double) * kBiRed * n, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    bool all_dropped = true, any_target = false, grown = false;
+    for (int k = 0; k < n; k++) {
+      if (!active[k]) continue;
+      const double rr = b.hred[6 * n + 3 * k + 2];
+      if (!std::isfinite(rr)) return set_error(LQCD_ERR_NOCONV, "BiCGStab breakdown on RHS %d at iteration %d", k, it);
+      if (sigma[k] * std::sqrt(rr) <= target[k]) any_target = true;
+      else if (!(rr <= delta2)) all_dropped = false;
+      if (rr > 1e8) grown = true;
+    }
+    const bool at_cap = it >= W.max_iter;
+    if (!(any_target || (mixed && (all_dropped || grown)) || at_cap)) continue;
+    // reliable update (mixed) / true-residual replacement (plain)
+    if (mixed) {
+      for (int k = 0; k < n; k++) b.hfac[k] = active[k] ? sigma[k] : 0.0;
+      LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      LQ_CU(blas_axpy(W.hp, LQCD_F32, c->Vh, n, W.x64->mut(1), xlo->ref(1), b.fac, c->stream));
+      LQ_CU(cudaMemsetAsync(xlo->data[1], 0, (size_t)xlo->rhs_words() * 16 * n, c->stream));
+      W.info->reliable_updates += 1;
+    }
+    LQ_TRY(true_residual());
+    LQ_CU(cudaMemcpyAsync(b.hs, b.ds, sizeof(BiScalars) * n, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    nact = 0;
+    for (int k = 0; k < n; k++) {
+      b.hfac[k] = 0.0;
+      if (!active[k]) continue;
+      if (!std::isfinite(nrm[k])) return set_error(LQCD_ERR_NOCONV, "residual of RHS %d is not finite", k);
+      if (nrm[k] <= target[k]) {
+        active[k] = 0;
+        b.hs[k].active = 0.0;
+        continue;
+      }
+      nact++;
+      if (mixed) {  // p, v and rho_old follow r into the new normalisation
+        const double f = sigma[k] / nrm[k];
+        b.hfac[k] = f;
+        b.hs[k].rho_old = make_double2(b.hs[k].rho_old.x * f, b.hs[k].rho_old.y * f);
+        sigma[k] = nrm[k];
+      }
+    }
+    if (nact == 0) break;
+    if (at_cap) break;
+    LQ_CU(cudaMemcpyAsync(b.ds, b.hs, sizeof(BiScalars) * n, cudaMemcpyHostToDevice, c->stream));
+    if (mixed) {
+      LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), b.fac, c->stream));
+      LQ_CU(blas_scale(L, L, c->Vh, n, v->mut(1), v->ref(1), b.fac, c->stream));
+    }
+    LQ_TRY(load_r());
+    LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, c->counter, red_xr, c->stream));
+  }
+  W.info->iters = it;
+  return nact == 0 ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "BiCGStab did not converge in %d iterations", W.max_iter);
+}
+
 // One solve: staging, even-odd source, the recursion, reconstruction and the
 // FP64 true residual.  Split so that a batch of lattices can share the loop.
 struct SolveJob {
@@ -567,6 +748,8 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
   if (prm->max_iter < 1) return set_error(LQCD_ERR_ARG, "max_iter must be >= 1");
   if (prm->nrhs < 1 || prm->nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
   if ((int)prm->inner < 0 || (int)prm->inner > 4) return set_error(LQCD_ERR_ARG, "bad inner precision");
+  if (prm->solver != LQCD_SOLVER_CGLS && prm->solver != LQCD_SOLVER_BICGSTAB)
+    return set_error(LQCD_ERR_ARG, "bad solver %d", prm->solver);
   if (prm->outer != LQCD_F64 && prm->outer != LQCD_DF64)
     return set_error(LQCD_ERR_ARG, "outer precision must be LQCD_F64 or LQCD_DF64");
   if (!plain_cg(prm) && !(prm->delta > 0.0 && prm->delta < 1.0))
@@ -742,7 +925,9 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
   J.prm = *prm;
   J.inf = info;
   LQ_TRY(job_prepare(J));
-  const lqcd_status st = plain_cg(prm) ? cgls_plain(J.W, J.B) : cgls_mixed(J.W, J.B);
+  const lqcd_status st = prm->solver == LQCD_SOLVER_BICGSTAB ? bicgstab(J.W, !plain_cg(prm))
+                         : plain_cg(prm)                      ? cgls_plain(J.W, J.B)
+                                                              : cgls_mixed(J.W, J.B);
   return job_finish(J, st);
 }
 
@@ -756,6 +941,7 @@ extern "C" lqcd_status lqcd_solve_batch(lqcd_ctx *const *ctxs, int nctx, double 
   if (!ctxs || !x || !b || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (nctx < 1 || nctx > 256) return set_error(LQCD_ERR_ARG, "nctx must be in 1..256");
   if (plain_cg(prm)) return set_error(LQCD_ERR_ARG, "batched solves run the mixed-precision recursion");
+  if (prm->solver != LQCD_SOLVER_CGLS) return set_error(LQCD_ERR_ARG, "batched solves run CGLS");
   for (int i = 0; i < nctx; i++) {
     LQ_TRY(check_params(ctxs[i], prm));
     if (!x[i] || !b[i]) return set_error(LQCD_ERR_ARG, "NULL buffer for lattice %d", i);

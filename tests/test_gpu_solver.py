@@ -185,3 +185,53 @@ def test_batch_of_uneven_lattices(lib):
         assert np.array_equal(x1, xs[j]) and info1.iters == infos[j].iters
     for lat in lats:
         lat.close()
+
+
+@pytest.mark.parametrize("inner,outer,nrhs", [("f64", "f64", 1), ("df64", "df64", 1), ("f32", "f64", 2),
+                                              ("f16", "f64", 2), ("bf16", "f64", 1), ("f16", "df64", 1)])
+def test_bicgstab(lib, inner, outer, nrhs):
+    """BiCGStab on Mhat, plain and mixed with reliable updates: every right-hand
+    side to a true residual of 1e-10 (recomputed by the oracle), and the same
+    solution as the FP64 CGLS."""
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003, nrhs=nrhs)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner=inner, outer=outer, delta=0.1, recon=18, inner_recon=12,
+                            solver="bicgstab")
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(nrhs):
+        assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+        assert info.true_resid[k] <= 1e-10
+    xc, stc, _ = lat.solve(b, tol=1e-10, inner="f64", recon=18)
+    assert stc == lib.LQCD_OK
+    assert rel(x, xc) < 1e-8
+    if inner not in ("f64", "df64"):
+        assert info.reliable_updates >= 1
+    lat.close()
+
+
+def test_bicgstab_point_sources_and_batch_rejects(lib):
+    """Point sources (a very uneven residual) converge with the mixed BiCGStab;
+    the batched entry point runs CGLS only and says so."""
+    dims = (8, 8, 8, 8)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1004)
+    b = gen.point_sources(dims)[:3]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner="f16", nrhs=3, solver="bicgstab")
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(3):
+        assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+    prm = lib.solve_params(tol=1e-10, inner=lib.LQCD_F16, solver="bicgstab")
+    with pytest.raises(lib.LqcdError) as e:
+        lib.lqcd_solve_batch([lat.ctx], [np.zeros_like(b[0])], [np.ascontiguousarray(b[0])], prm)
+    assert e.value.status == lib.LQCD_ERR_ARG
+    lat.close()
