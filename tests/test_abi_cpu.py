@@ -49,17 +49,23 @@ def test_binding_reports_errors_without_gpu():
 
 
 def test_struct_layouts_match_header(tmp_path):
-    """The ctypes mirrors of the parameter structs match the C compiler's layout."""
+    """The ctypes mirrors of the parameter and info structs match the C
+    compiler's layout (sizes and the offset of every field)."""
     import paper_2001_05706_gb300 as L
+    structs = {"lqcd_solve_params": L.lqcd_solve_params, "lqcd_solve_info": L.lqcd_solve_info,
+               "lqcd_overlap_params": L.lqcd_overlap_params, "lqcd_overlap_info": L.lqcd_overlap_info}
+    lines, expect = [], []
+    for cname, py in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            cfield = "lambda" if fname == "lambda_" else fname
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {cfield}));')
+            expect.append(getattr(py, fname).offset)
     src = tmp_path / "sz.c"
-    src.write_text(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lqcd_solve_params), sizeof(lqcd_solve_info),'
-        ' offsetof(lqcd_solve_params, check_every), offsetof(lqcd_solve_info, true_resid),'
-        ' offsetof(lqcd_solve_info, mhat_applies)); return 0;}\n')
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lqcd.h"\nint main(void){' + "".join(lines) +
+                   ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
-    P, I = L.lqcd_solve_params, L.lqcd_solve_info
-    assert got == [ctypes.sizeof(P), ctypes.sizeof(I), P.check_every.offset, I.true_resid.offset,
-                   I.mhat_applies.offset]
+    assert got == expect
