@@ -356,27 +356,36 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
 
 def run_multi_rhs(L, torch, lat, U, want_oracle, oracle_AAi):
     """Config 4 (i): the 12 spin-colour point sources on the benchmark lattice,
-    mixed precision (FP16 inner), one multi-RHS solve."""
+    mixed precision (FP16 inner), one multi-RHS solve: CGLS with FP64 updates
+    (the headline configuration), CGLS with DF64 updates, BiCGStab with DF64
+    updates."""
     import gen
     b = gen.point_sources(DIMS)
     bt = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda()
-    xt = torch.zeros_like(bt)
-    prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=12, recon=18, inner_recon=12,
-                         check_every=0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    res = {"rhs": "12 point sources at the origin", "inner": "f16", "seconds": wall, "iters": info.iters,
-           "reliable_updates": info.reliable_updates, "mhat_applies": info.mhat_applies,
-           "max_true_resid_gpu_fp64": max(info.true_resid[:12]),
-           "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
-    if want_oracle and oracle_AAi is not None:
-        import oracle
-        x = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
-        res["true_resid_oracle_rhs0_rhs11"] = [oracle.true_residual(DIMS, U, oracle_AAi[0], KAPPA, x[k], b[k])
-                                               for k in (0, 11)]
+    res = {"rhs": "12 point sources at the origin", "inner": "f16"}
+    for name, outer, solver in (("cgls", L.LQCD_F64, L.LQCD_SOLVER_CGLS),
+                                ("cgls_df64_updates", L.LQCD_DF64, L.LQCD_SOLVER_CGLS),
+                                ("bicgstab_df64_updates", L.LQCD_DF64, L.LQCD_SOLVER_BICGSTAB)):
+        xt = torch.zeros_like(bt)
+        prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=12, recon=18,
+                             inner_recon=12, check_every=0, outer=outer, solver=solver)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        r = {"seconds": wall, "iters": info.iters, "reliable_updates": info.reliable_updates,
+             "mhat_applies": info.mhat_applies, "max_true_resid_gpu_fp64": max(info.true_resid[:12]),
+             "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+        if want_oracle and oracle_AAi is not None:
+            import oracle
+            x = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
+            r["true_resid_oracle_rhs0_rhs11"] = [oracle.true_residual(DIMS, U, oracle_AAi[0], KAPPA, x[k], b[k])
+                                                 for k in (0, 11)]
+        if name == "cgls":
+            res.update(r)
+        else:
+            res[name] = r
     return res
 
 
@@ -396,18 +405,26 @@ def run_batch(L, torch, stream):
         b = torch.from_numpy(gen.gaussian_spinor(d, 4000 + j, nrhs=4).view(np.float64).reshape(-1).copy()).cuda()
         bs.append(b)
         xs.append(torch.zeros_like(b))
-    prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=4, recon=18, inner_recon=12,
-                         check_every=0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm, raise_on_noconv=False)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
     sites = sum(int(np.prod(d)) for d in shapes)
     res = {"lattices": "8 x 16^3x32 + 8 x 20^3x40 + 8 x 24^3x48", "sites": sites, "rhs_per_lattice": 4,
-           "inner": "f16", "seconds": wall, "max_iters": max(i.iters for i in infos),
-           "max_true_resid_gpu_fp64": max(max(i.true_resid[:4]) for i in infos),
-           "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+           "inner": "f16"}
+    for name, outer in (("fp64_updates", L.LQCD_F64), ("df64_updates", L.LQCD_DF64)):
+        for x in xs:
+            x.zero_()
+        prm = L.solve_params(tol=1e-10, max_iter=40000, inner=L.LQCD_F16, delta=0.1, nrhs=4, recon=18,
+                             inner_recon=12, check_every=0, outer=outer)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        r = {"seconds": wall, "max_iters": max(i.iters for i in infos),
+             "max_true_resid_gpu_fp64": max(max(i.true_resid[:4]) for i in infos),
+             "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+        if name == "fp64_updates":
+            res.update(r)
+        else:
+            res[name] = r
     for lat in lats:
         lat.close()
     return res
@@ -454,7 +471,8 @@ def run_overlap(args):
         t0 = time.perf_counter()
         st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
         out["setup"] = {"seconds": time.perf_counter() - t0, "status": "ok" if st == 0 else L.lqcd_last_error(),
-                        "sweeps": info.sweeps, "degree": info.degree, "a": info.a, "b": info.b,
+                        "sweeps": info.sweeps, "degree": info.degree, "degree_inner_fp32": info.degree_inner,
+                        "a": info.a, "b": info.b,
                         "sign_error": info.sign_error, "max_eig_resid": max(info.resid[:20]),
                         "lambda_min_max": [min(abs(v) for v in info.lambda_[:20]),
                                            max(abs(v) for v in info.lambda_[:20])]}

@@ -285,6 +285,9 @@ typedef struct {
   double sign_error;      /* its sup error on [sqrt a, sqrt b]                         */
   int sweeps;             /* subspace-iteration sweeps used                            */
   double seconds;         /* wall time of the set-up                                   */
+  int degree_inner;       /* degree of the FP32 sign function inside the mixed CG: the */
+                          /* smallest reaching max(sign_tol, 1e-6), the FP32 rounding */
+                          /* level (reliable updates use the full degree)             */
 } lqcd_overlap_info;
 
 typedef enum {

@@ -59,7 +59,8 @@ class lqcd_overlap_params(ctypes.Structure):
 class lqcd_overlap_info(ctypes.Structure):
     _fields_ = [("n_low", ctypes.c_int), ("lambda_", ctypes.c_double * 64), ("resid", ctypes.c_double * 64),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("degree", ctypes.c_int),
-                ("sign_error", ctypes.c_double), ("sweeps", ctypes.c_int), ("seconds", ctypes.c_double)]
+                ("sign_error", ctypes.c_double), ("sweeps", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("degree_inner", ctypes.c_int)]
 
 
 LQCD_OV_APPLY, LQCD_OV_APPLY_DAG, LQCD_OV_SIGN, LQCD_OV_SOLVE = 0, 1, 2, 3

@@ -43,9 +43,10 @@ struct OverlapState {
   std::vector<double> lam;
   lqcd_field *vecs = nullptr;    // FULL FP64, nrhs = nlow
   lqcd_field *vecs32 = nullptr;  // the same in FP32 (inner solves)
-  std::vector<double> coef;
+  std::vector<double> coef;    // sign function to sign_tol (FP64 / DF64)
+  std::vector<double> coef32;  // the FP32 one inside the mixed CG: to max(sign_tol, 1e-6)
   double a = 0, b = 0;
-  int degree = 0;
+  int degree = 0, degree32 = 0;
   cublasHandle_t blas = nullptr;
   bool df = false;            // FP64 parts computed in double-float (prm.high == LQCD_DF64)
   double2 *dsmall = nullptr;  // device scratch for small matrices
@@ -66,6 +67,8 @@ void overlap_free(lqcd_ctx *c) {
 namespace {
 
 constexpr int kT = 256;
+// accuracy of the FP32 sign function of the mixed overlap CG (its rounding level)
+constexpr double kInnerSignTol = 1e-6;
 // Low-mode block size m = max(want + 16, LQCD_OV_BLOCK_MULT * want), capped at
 // 96.  Measured on 16^3x32 (20 modes, |lambda| 0.509-0.510 clustered, DF64
 // sweeps): m = 40: 214 sweeps, 84 s; m = 60: 191 sweeps, 114 s; m = 96: 143
@@ -568,16 +571,19 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
   }
   const double a = S.a, b = S.b;
   const double s2 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
-  const int n = S.degree;
+  // an FP32 sign function carries ~1e-6 rounding anyway: its polynomial stops there
+  const bool lowdeg = in->prec == LQCD_F32;
+  const int n = lowdeg ? S.degree32 : S.degree;
+  const std::vector<double> &coef = lowdeg ? S.coef32 : S.coef;
   // b_n = c_n w  (and w in the recurrence's precision)
   if (rp != in->prec) {
     LQ_TRY(new_prec(c, rp, nrhs, &wr));
     g.f.push_back(wr);
     LQ_TRY(convert_full(c, wr, w, nrhs));
-    LQ_TRY(convert_full(c, b1, w, nrhs, S.coef[n]));
+    LQ_TRY(convert_full(c, b1, w, nrhs, coef[n]));
   } else {
     wr = w;
-    LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, S.coef[n], 0.0, 0.0, 0.0));
+    LQ_TRY(clenshaw(c, nrhs, b1, w, w, w, nullptr, coef[n], 0.0, 0.0, 0.0));
   }
   // b_k = c_k w + 2 T b_{k+1} - b_{k+2} (k = n-1 .. 1), then P w = c_0 w + T b_1 - b_2
   // (n = 0: P w = c_0 w = b_0),
@@ -587,7 +593,7 @@ lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *
   for (int k = n - 1; k >= 0; k--) {
     const double t = k > 0 ? 2.0 : 1.0;
     LQ_TRY(hw(c, nrhs, h, b1));
-    LQ_TRY(hw_cheb(c, nrhs, hh, h, t * s2, wr, S.coef[k], b1, t * s0, b2_zero ? nullptr : b2, -1.0));
+    LQ_TRY(hw_cheb(c, nrhs, hh, h, t * s2, wr, coef[k], b1, t * s0, b2_zero ? nullptr : b2, -1.0));
     b2_zero = false;
     lqcd_field *o = hh;
     hh = b2;
@@ -1132,6 +1138,12 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   inf->a = S.a;
   inf->b = S.b;
   inf->degree = S.degree;
+  S.degree32 = cheb_degree(S.a, S.b, std::max(prm->sign_tol, kInnerSignTol), prm->max_degree, S.coef32);
+  if (S.degree32 < 0) {
+    S.degree32 = S.degree;
+    S.coef32 = S.coef;
+  }
+  inf->degree_inner = S.degree32;
   inf->sign_error = sign_error(S.a, S.b, S.coef);
   LQ_CU(cudaStreamSynchronize(c->stream));
   inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -60,6 +60,8 @@ def test_low_modes_against_dense(rough):
     res, ortho = oracle.eigen_residuals(dims, U, RHO, lam, vecs)
     assert res.max() < 1e-10 and ortho < 1e-10
     assert info.degree > 0 and info.sign_error <= 1e-12
+    # the FP32 sign function of the mixed CG stops at its rounding level
+    assert 0 < info.degree_inner < info.degree
 
 
 def test_sign_and_overlap_against_oracle(rough, lib):
@@ -140,4 +142,16 @@ def test_overlap_solve(lib, inner, high):
     for k in range(2):
         r = b[k] - oracle.apply_overlap(dims, U, RHO, m, x[k], info.a, info.b, c, lam=lam, vecs=vecs)
         assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10
+    lat.close()
+
+
+def test_overlap_rejects_bad_high_precision(lib):
+    L = lib
+    dims = (4, 4, 4, 4)
+    lat = L.Lattice(dims)
+    lat.load_gauge(gen.gauge_field(dims, 0.3, 23).view(np.float64))
+    prm = L.overlap_params(rho=RHO, n_low=2, high=L.LQCD_F32)
+    with pytest.raises(L.LqcdError) as e:
+        L.lqcd_overlap_setup(lat.ctx, prm)
+    assert e.value.status == L.LQCD_ERR_ARG
     lat.close()

@@ -157,9 +157,11 @@ def test_noconv_reports(lib):
     lat.close()
 
 
-def test_batch_of_uneven_lattices(lib):
+@pytest.mark.parametrize("outer", ["f64", "df64"])
+def test_batch_of_uneven_lattices(lib, outer):
     """Three lattices of different volumes in one graph-captured batch: each
-    reaches 1e-10 (oracle) and equals the single-lattice solve bitwise."""
+    reaches 1e-10 (oracle) and equals the single-lattice solve bitwise, with
+    FP64 or DF64 reliable updates."""
     L = lib
     dims_list = [(4, 4, 4, 8), (6, 4, 4, 8), (8, 4, 6, 4)]
     kappa, csw = 0.125, 1.0
@@ -173,7 +175,7 @@ def test_batch_of_uneven_lattices(lib):
         Us.append(U)
         bs.append(np.ascontiguousarray(gen.gaussian_spinor(dims, 4000 + j, nrhs=2)))
     xs = [np.zeros_like(b) for b in bs]
-    prm = L.solve_params(tol=1e-10, inner=L.LQCD_F16, nrhs=2, check_every=8)
+    prm = L.solve_params(tol=1e-10, inner=L.LQCD_F16, nrhs=2, check_every=8, outer=L.PREC[outer])
     st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm)
     assert st == L.LQCD_OK
     for j, dims in enumerate(dims_list):
@@ -234,4 +236,27 @@ def test_bicgstab_point_sources_and_batch_rejects(lib):
     with pytest.raises(lib.LqcdError) as e:
         lib.lqcd_solve_batch([lat.ctx], [np.zeros_like(b[0])], [np.ascontiguousarray(b[0])], prm)
     assert e.value.status == lib.LQCD_ERR_ARG
+    lat.close()
+
+
+def test_bicgstab_initial_guess(lib):
+    """BiCGStab started from the solution of a looser solve: it converges in
+    fewer iterations than from zero and to the same 1e-10 true residual."""
+    dims = (8, 8, 8, 8)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1006)
+    b = gen.gaussian_spinor(dims, 2006)[0]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x0, st0, i0 = lat.solve(b, tol=1e-4, inner="f64", solver="bicgstab")
+    assert st0 == lib.LQCD_OK
+    prm = lib.solve_params(tol=1e-10, inner=lib.LQCD_F16, use_x0=1, solver="bicgstab")
+    x = np.ascontiguousarray(x0.copy())
+    st, info = lib.lqcd_solve(lat.ctx, x, np.ascontiguousarray(b), prm)
+    assert st == lib.LQCD_OK
+    _, _, cold = lat.solve(b, tol=1e-10, inner="f16", solver="bicgstab")
+    assert info.iters < cold.iters
+    A = oracle.clover(dims, U, kappa, csw)
+    assert oracle.true_residual(dims, U, A, kappa, x, b) <= 1e-10
     lat.close()
