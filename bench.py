@@ -462,8 +462,8 @@ def run_overlap(args):
     b = gen.gaussian_spinor(dims, 2005, nrhs=12)
     out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "high": args.high, "config": {
         "workload": "overlap D_ov(m) = rho[1 + g5 sign(H_W)] + ..., 16^3x32, eps 0.1, rho 1.5, m 0.05, 20 low modes, "
-                    "sign to 1e-10, 12 Gaussian RHS, CG on the normal equations with FP32 sign inside and FP64 "
-                    "reliable updates"}}
+                    "sign to 1e-10 (FP32 sign inside the CG to 1e-6), 12 Gaussian RHS, CG on the normal "
+                    "equations with FP64 (or DF64) reliable updates every two decades (delta 0.01)"}}
     with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
         lat.load_gauge(U.view(np.float64))
         prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400,
@@ -482,7 +482,9 @@ def run_overlap(args):
         t_apply = time.perf_counter() - t0
         out["apply_fp64_12rhs"] = {"seconds": t_apply, "hw_applications": 2 * info.degree + 1,
                                    "wilson_rhs_applications_per_s": 12 * (2 * info.degree + 1) / t_apply}
-        cg = L.solve_params(tol=1e-10, max_iter=4000, nrhs=12, inner=L.LQCD_F32, delta=0.1)
+        # delta 0.01: the inner FP32 sign function is good to ~1e-6, so an update per
+        # two decades costs fewer FP64/DF64 sign functions than one per decade
+        cg = L.solve_params(tol=1e-10, max_iter=4000, nrhs=12, inner=L.LQCD_F32, delta=0.01)
         t0 = time.perf_counter()
         st, si = L.lqcd_overlap(lat.ctx, x, b, 12, L.LQCD_OV_SOLVE, cg, raise_on_noconv=False)
         out["solve_mixed_12rhs"] = {"seconds": time.perf_counter() - t0, "iters": si.iters,

@@ -484,6 +484,16 @@ lqcd_status mhat_host_pipelined(lqcd_ctx *c, double *out, const double *in, int 
       if (!c->chunk_event[k][j]) LQ_CU(cudaEventCreateWithFlags(&c->chunk_event[k][j], cudaEventDisableTiming));
   }
   cudaStream_t sin = c->copy_stream[0], sout = c->copy_stream[1];
+  // whatever happens below, the call returns only once no copy touches the
+  // caller's host buffers any more
+  struct Drain {
+    cudaStream_t a, b, d;
+    ~Drain() {
+      cudaStreamSynchronize(a);
+      cudaStreamSynchronize(b);
+      cudaStreamSynchronize(d);
+    }
+  } drain{sin, sout, c->stream};
   const long slab = c->V / nch;  // sites per chunk
   const long hs = slab / 2;      // sites per parity per chunk
   const size_t bytes = (size_t)slab * 24 * sizeof(double);
