@@ -625,9 +625,14 @@ def run_gpu(args, rank, world, local_rank):
                    "kappa": KAPPA, "c_sw": CSW, "eps": EPS, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each step streams ~1.2 GB (links 403 MB, clover 604 MB, spinors)"},
         "pct_of_peak": 100.0 * gbs / world / peak,
+        # the literature's "no-reuse" convention (8 neighbour spinors read per site; K2a 1536 B,
+        # K2b 1632 B for FP32 12-real) and the flop rate, for comparison with published tables
+        "effective_no_reuse_GBps": Vh * (1536 + 1632) / (ms * 1e-3) / 1e9,
+        "TFLOPs": Vh * (FLOPS["k2a"] + FLOPS["k2b"]) / (ms * 1e-3) / 1e12,
         "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peak, "unit": "GB/s", "frac": dom_gbs / peak,
                      "traffic": traffic, "kernel": f"dslash_kernel {dom} (FP32, 12-real)",
                      "bytes_per_launch": Vh * site_bytes("f32", 12, dom), "ms_per_launch": dom_ms,
+                     "traffic_over_compulsory": (traffic / (Vh * site_bytes("f32", 12, dom))) if traffic else None,
                      "peak_source": peak_src},
         "kernels": {"k2a_ms": k2a_ms, "k2a_GBps": k2a_gbs, "k2b_ms": k2b_ms, "k2b_GBps": k2b_gbs},
         "variants": variants,
