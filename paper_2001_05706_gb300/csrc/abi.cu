@@ -470,6 +470,7 @@ namespace {
 // host link carries both directions at once.
 lqcd_status mhat_host_pipelined(lqcd_ctx *c, double *out, const double *in, int nrhs, lqcd_prec prec, int recon,
                                 int nch) {
+  NvtxRange nv("lqcd Mhat on host buffers (pipelined)");
   const size_t n = (size_t)nrhs * c->V * 24;
   double *din, *dout;
   LQ_TRY(staging(c, 0, n, &din));

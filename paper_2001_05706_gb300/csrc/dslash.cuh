@@ -61,7 +61,28 @@ struct DslashParams {
   unsigned int *norm_counter;
   double *norm_result;    // result of RHS r at norm_result[r * norm_stride]
   int norm_stride;
+  unsigned int *dbg;      // builds with LQCD_DEBUG_BOUNDS: set to 1 on an out-of-range index
 };
+
+// Debug builds (-DLQCD_DEBUG_BOUNDS=1) check every gathered index against the
+// parity's site range; a bad one is recorded in *P.dbg (the host turns it into
+// an error after the launch) and replaced by 0 so no access leaves the field.
+#ifndef LQCD_DEBUG_BOUNDS
+#define LQCD_DEBUG_BOUNDS 0
+#endif
+#if LQCD_DEBUG_BOUNDS
+#define LQCD_CHECK_INDEX(P, i)            \
+  do {                                    \
+    if ((i) < 0 || (i) >= (P).g.Vh) {     \
+      atomicOr((P).dbg, 1u);              \
+      (i) = 0;                            \
+    }                                     \
+  } while (0)
+#else
+#define LQCD_CHECK_INDEX(P, i) \
+  do {                         \
+  } while (0)
+#endif
 
 // ---------------------------------------------------------------------------
 // field access
@@ -453,7 +474,8 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
   const float *scb = IsHalf<S>::value ? P.in.scale + (long)rg * Vh : nullptr;
   auto issue = [&](int k, unsigned dep) {
     const int mu = k >> 1, b = k & 1;
-    const long n = neighbour(P.g, xc, h, mu, (k & 1) ? -1 : +1);
+    long n = neighbour(P.g, xc, h, mu, (k & 1) ? -1 : +1);
+    LQCD_CHECK_INDEX(P, n);
 #pragma unroll
     for (int w = 0; w < WS::NW; w++) cp_async_after<WS::W>(&st.sp[b][w][tid], spb + ((long)w * Vh + n) * WS::W, dep);
     if constexpr (IsHalf<S>::value) cp_async_after<4>(&st.sc[b][tid], scb + n, dep);
@@ -545,7 +567,8 @@ __device__ __forceinline__ void hop_rolled(const DslashParams &P, long h, int p,
 #pragma unroll 1
   for (int k = 0; k < 8; k++) {
     const int mu = k >> 1, dir = (k & 1) ? -1 : +1;
-    const long n = neighbour(P.g, xc, h, mu, dir);
+    long n = neighbour(P.g, xc, h, mu, dir);
+    LQCD_CHECK_INDEX(P, n);
     const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
     const T s = dir > 0 ? (T)-1 : (T)1;
     cx<T> U[3][3];
@@ -661,7 +684,8 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, 
 #pragma unroll
         for (int d = 0; d < 2; d++) {
           const int dir = d == 0 ? +1 : -1;
-          const long n = neighbour(P.g, xc, h, mu, dir);
+          long n = neighbour(P.g, xc, h, mu, dir);
+          LQCD_CHECK_INDEX(P, n);
           const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
           const T s = dir > 0 ? (T)-1 : (T)1;  // forward (1 - g_mu), backward (1 + g_mu)
           cx<T> U[3][3];

@@ -5,10 +5,21 @@
 #include <map>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "dslash.cuh"
 
 namespace lqcd {
+
+// NVTX range over a scope: the solver phases show up by name in Nsight
+// Systems and can filter ncu captures (no cost without an attached tool)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct MutField {
   void *data;

@@ -225,8 +225,25 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
     P.norm_result = norm_result;
     P.norm_stride = norm_stride;
   }
+#if LQCD_DEBUG_BOUNDS
+  P.dbg = c->counter + 63;  // spare reduction counter, zero between launches
+#endif
   const int nr = pick_nr(c, P, prec, recon, mode, nrhs);
   LQ_CU(launch_dslash_prec(prec, P, recon, mode, nr, c->stream));
+#if LQCD_DEBUG_BOUNDS
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  LQ_CU(cudaStreamIsCapturing(c->stream, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
+    unsigned flag = 0;
+    LQ_CU(cudaMemcpyAsync(&flag, P.dbg, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    if (flag) {
+      LQ_CU(cudaMemsetAsync(P.dbg, 0, sizeof(flag), c->stream));
+      return set_error(LQCD_ERR_CUDA, "dslash gathered an out-of-range site index (mode %d, parity %d)", mode,
+                       out_p);
+    }
+  }
+#endif
   return LQCD_OK;
 }
 

@@ -546,6 +546,7 @@ int cheb_degree(double a, double b, double tol, int nmax, std::vector<double> &c
 
 // eps(H_W) in -> out (nrhs RHS), FULL fields of one precision (FP64 or FP32)
 lqcd_status sign_apply(lqcd_ctx *c, int nrhs, const lqcd_field *in, lqcd_field *out) {
+  NvtxRange nv("lqcd sign function");
   OverlapState &S = *c->ov;
   const bool f64 = in->prec == LQCD_F64;
   // the recurrence of an FP64 sign function runs in double-float on request
@@ -911,6 +912,7 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
 using namespace lqcd;
 
 extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params *prm, lqcd_overlap_info *info) {
+  NvtxRange nv("lqcd overlap set-up");
   if (!c || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!(prm->rho > 0 && prm->rho < 2)) return set_error(LQCD_ERR_ARG, "rho must be in (0, 2)");

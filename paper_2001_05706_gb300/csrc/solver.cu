@@ -96,6 +96,7 @@ struct Work {
 // Plain CGLS in FP64 or DF64: iterate until every RHS has ||r|| <= target,
 // where r is recomputed as bhat - Mhat x before a right-hand side is accepted.
 lqcd_status cgls_plain(Work &W, SolveBufs &B) {
+  NvtxRange nv("lqcd CGLS (plain)");
   lqcd_ctx *c = W.c;
   const int n = W.nrhs;
   const lqcd_prec P = W.hp;
@@ -388,6 +389,7 @@ struct MixedCG {
   // reliable update, accepted only if it lowers the FP64 residual:
   // x_try = x64 + sigma x_lo, r_try = bhat - Mhat64 x_try
   lqcd_status update() {
+    NvtxRange nv("lqcd reliable update");
     for (int k = 0; k < n; k++) {
       if (B.h_sc[k].active != 0.0 && !(B.h_sc[k].rr == B.h_sc[k].rr))
         return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
@@ -532,6 +534,7 @@ lqcd_status run_mixed(const std::vector<MixedCG *> &all, cudaStream_t launch, in
 }
 
 lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
+  NvtxRange nv("lqcd CGLS (mixed)");
   MixedCG m(W, B);
   LQ_TRY(m.init());
   if (!m.done) LQ_TRY(run_mixed({&m}, W.c->stream, W.max_iter));
@@ -554,6 +557,7 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
 // check_every iterations.
 // ---------------------------------------------------------------------------
 lqcd_status bicgstab(Work &W, bool mixed) {
+  NvtxRange nv(mixed ? "lqcd BiCGStab (mixed)" : "lqcd BiCGStab (plain)");
   lqcd_ctx *c = W.c;
   const int n = W.nrhs;
   const lqcd_prec L = mixed ? W.lo : W.hp;
@@ -762,6 +766,7 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
 }
 
 lqcd_status job_prepare(SolveJob &J) {
+  NvtxRange nv("lqcd solve: stage and even-odd source");
   lqcd_ctx *c = J.c;
   const lqcd_solve_params *prm = &J.prm;
   J.t0 = std::chrono::steady_clock::now();
@@ -853,6 +858,7 @@ lqcd_status job_prepare(SolveJob &J) {
 }
 
 lqcd_status job_finish(SolveJob &J, lqcd_status solve_status) {
+  NvtxRange nv("lqcd solve: reconstruct and FP64 residual");
   lqcd_ctx *c = J.c;
   const int n = J.prm.nrhs;
   lqcd_solve_info *inf = J.inf;
