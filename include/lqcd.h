@@ -146,10 +146,11 @@ lqcd_status lqcd_set_rho(lqcd_ctx *ctx, double rho);
  * the op's output subset are set to zero.  Needs the gauge field, and
  * kappa for every op but HOP_EO/HOP_OE/HW (rho for HW).  Host buffers are
  * read and written inside the call, which then blocks; for LQCD_OP_MHAT on
- * host buffers with L3 divisible by 4, 8 or 16 the call is pipelined over
- * chunks of whole time slices (copies in and out on two streams of the
- * context while the context's stream computes; the result is bit-identical
- * to the device-buffer path).  Environment LQCD_NO_PIPELINE=1 disables that. */
+ * host buffers the call is pipelined over chunks of whole time slices (the
+ * largest divisor of L3 between 4 and LQCD_HOST_CHUNKS, default 32; copies in
+ * and out on two streams of the context while the context's stream computes;
+ * the result is bit-identical to the device-buffer path).  Environment
+ * LQCD_NO_PIPELINE=1 disables that. */
 lqcd_status lqcd_dslash(lqcd_ctx *ctx, double *out, const double *in, int nrhs, lqcd_op op, lqcd_prec prec,
                         lqcd_recon recon, int on_device);
 
