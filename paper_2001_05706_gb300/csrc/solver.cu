@@ -171,17 +171,18 @@ lqcd_status cgls_plain(Work &W, SolveBufs &B) {
 // body is one CG iteration followed by cg_control_kernel, which reads the new
 // iterated residuals, updates per-RHS trigger state (best and reference
 // residual, stagnation count, growth) and sets the loop condition.  The loop
-// stops when a reliable update is due -- every active RHS dropped by delta, or
-// one reached its target, stagnated for kStallIters iterations, or grew 20 %
-// past its best -- or when the iteration cap of this launch is reached, so it
-// always terminates.  The control kernel also moves the new gamma into the
+// stops when a reliable update is due -- every active RHS dropped by delta or
+// reached its target (a right-hand side that reached it is parked: it stops
+// updating until the FP64 check), or one stagnated for kStallIters iterations
+// or grew 20 % past its best -- or when the iteration cap of this launch is
+// reached, so it always terminates.  The control kernel also moves the new gamma into the
 // slot the next iteration reads, which makes the body the same every time.
 // ---------------------------------------------------------------------------
 constexpr int kStallIters = 48;
 
 struct CtrlRhs {
   double best, ref, sigma, target;
-  int stall, grown, pad0, pad1;
+  int stall, grown, parked, pad;
 };
 struct CtrlGlobal {
   int it, cap, stop, pad;
@@ -219,9 +220,15 @@ __global__ void cg_control_kernel(SolverScalars *sc, CtrlRhs *cr, CtrlGlobal *cg
           c.grown = 1;
           any_trigger = 1;
         }
-        if (c.sigma * sqrt(c.best) <= c.target) any_trigger = 1;
+        // a right-hand side at its target is parked (it stops updating) until
+        // the FP64 check of the next reliable update confirms it; the others
+        // iterate on
+        if (c.sigma * sqrt(rr) <= c.target) {
+          c.parked = 1;
+          sc[k].active = 0.0;
+        }
       }
-      if (!(c.best <= cg->delta2)) all_dropped = 0;
+      if (!c.parked && !(c.best <= cg->delta2)) all_dropped = 0;
       cr[k] = c;
     }
   }
@@ -276,6 +283,7 @@ struct MixedCG {
   }
 
   void reset_rhs(int k) {
+    hcr[k].parked = 0;
     hcr[k].best = 1.0;
     hcr[k].ref = 1.0;
     hcr[k].stall = 0;
@@ -388,12 +396,15 @@ struct MixedCG {
 
   // reliable update, accepted only if it lowers the FP64 residual:
   // x_try = x64 + sigma x_lo, r_try = bhat - Mhat64 x_try
+  // a right-hand side takes part in an update while it iterates or is parked
+  bool takes_part(int k) const { return B.h_sc[k].active != 0.0 || hcr[k].parked; }
+
   lqcd_status update() {
     NvtxRange nv("lqcd reliable update");
     for (int k = 0; k < n; k++) {
       if (B.h_sc[k].active != 0.0 && !(B.h_sc[k].rr == B.h_sc[k].rr))
         return set_error(LQCD_ERR_NOCONV, "inner residual of RHS %d is NaN at iteration %d", k, it);
-      B.h_fac[k] = B.h_sc[k].active != 0.0 ? sigma[k] : 0.0;
+      B.h_fac[k] = takes_part(k) ? sigma[k] : 0.0;
     }
     LQ_TRY(write_fac(c, B, n));
     LQ_CU(cudaMemcpyAsync(xtry->data[1], W.x64->data[1], rhs_bytes64 * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -406,7 +417,7 @@ struct MixedCG {
     done = true;
     for (int k = 0; k < n; k++) {
       B.h_fac[k] = B.h_fac[n + k] = B.h_fac[2 * n + k] = 0.0;
-      if (B.h_sc[k].active == 0.0) continue;
+      if (!takes_part(k)) continue;
       const double snew = std::sqrt(B.h_sc[k].aux);
       if (kTrace)
         std::fprintf(stderr,
@@ -423,6 +434,7 @@ struct MixedCG {
                               cudaMemcpyDeviceToDevice, c->stream));
         if (snew <= target[k]) {
           B.h_sc[k].active = 0.0;
+          hcr[k].parked = 0;
           continue;
         }
       }
@@ -431,7 +443,8 @@ struct MixedCG {
       // normalisation r_lo = r64 / snew, unless the update was rejected or the
       // inner iteration was turning round (grown, stagnating): then CG
       // restarts from p = s
-      const bool restart = !accept || hcr[k].grown || hcr[k].stall >= kStallIters;
+      const bool restart = !accept || hcr[k].grown || hcr[k].parked || hcr[k].stall >= kStallIters;
+      B.h_sc[k].active = 1.0;  // a parked right-hand side that was not converged iterates again
       const double snext = accept ? snew : sigma[k];
       B.h_fac[k] = restart ? 0.0 : sigma[k] / snext;
       B.h_fac[n + k] = 1.0 / snext;
@@ -548,8 +561,9 @@ lqcd_status cgls_mixed(Work &W, SolveBufs &B) {
 // in FP64 or DF64, and when an iterated residual reaches its target the true
 // residual bhat - Mhat x replaces r (converged right-hand sides stop).  Mixed:
 // vectors in FP32/FP16/BF16 (FP32 arithmetic) on the residual normalised to 1,
-// x_lo in FP32; when every active inner residual fell by delta (or reached its
-// target, or grew past 1e4) the high-precision solution absorbs sigma x_lo and
+// x_lo in FP32; when every active inner residual fell by delta or reached its
+// target (a right-hand side that reached it is parked: it stops until the
+// check), or one grew past 1e4, the high-precision solution absorbs sigma x_lo and
 // the residual is recomputed in FP64/DF64 (a reliable update).  The shadow
 // residual rhat is kept across updates; r takes the new residual, p and v are
 // rescaled with it, rho_old too, and rho = (rhat, r) is recomputed, so the
@@ -598,7 +612,7 @@ lqcd_status bicgstab(Work &W, bool mixed) {
   const size_t vbytes = (size_t)r->rhs_words() * 16 * n;
   const size_t sbytes = r->scale[1] ? sizeof(float) * c->Vh * n : 0;
   std::vector<double> target(n), sigma(n, 1.0), nrm(n);
-  std::vector<char> active(n, 1);
+  std::vector<char> active(n, 1), parked(n, 0);
   for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
   // high-precision residual r64 = bhat - Mhat x64 and its norms
   auto true_residual = [&]() -> lqcd_status {
@@ -669,17 +683,33 @@ lqcd_status bicgstab(Work &W, bool mixed) {
     }
     LQ_CU(cudaMemcpyAsync(b.hred, b.red, sizeof(double) * kBiRed * n, cudaMemcpyDeviceToHost, c->stream));
     LQ_CU(cudaStreamSynchronize(c->stream));
-    bool all_dropped = true, any_target = false, grown = false;
+    // a right-hand side whose iterated residual reached its target is parked
+    // (the kernels skip it) until the next true-residual check confirms it
+    bool all_dropped = true, grown = false, newly_parked = false, any_left = false;
     for (int k = 0; k < n; k++) {
-      if (!active[k]) continue;
+      if (!active[k] || parked[k]) continue;
       const double rr = b.hred[6 * n + 3 * k + 2];
       if (!std::isfinite(rr)) return set_error(LQCD_ERR_NOCONV, "BiCGStab breakdown on RHS %d at iteration %d", k, it);
-      if (sigma[k] * std::sqrt(rr) <= target[k]) any_target = true;
-      else if (!(rr <= delta2)) all_dropped = false;
+      if (sigma[k] * std::sqrt(rr) <= target[k]) {
+        parked[k] = 1;
+        newly_parked = true;
+        continue;
+      }
+      any_left = true;
+      if (!(rr <= delta2)) all_dropped = false;
       if (rr > 1e8) grown = true;
     }
     const bool at_cap = it >= W.max_iter;
-    if (!(any_target || (mixed && (all_dropped || grown)) || at_cap)) continue;
+    if (!(!any_left || (mixed && (all_dropped || grown)) || at_cap)) {
+      if (newly_parked) {
+        LQ_CU(cudaMemcpyAsync(b.hs, b.ds, sizeof(BiScalars) * n, cudaMemcpyDeviceToHost, c->stream));
+        LQ_CU(cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < n; k++)
+          if (parked[k]) b.hs[k].active = 0.0;
+        LQ_CU(cudaMemcpyAsync(b.ds, b.hs, sizeof(BiScalars) * n, cudaMemcpyHostToDevice, c->stream));
+      }
+      continue;
+    }
     // reliable update (mixed) / true-residual replacement (plain)
     if (mixed) {
       for (int k = 0; k < n; k++) b.hfac[k] = active[k] ? sigma[k] : 0.0;
@@ -698,10 +728,13 @@ lqcd_status bicgstab(Work &W, bool mixed) {
       if (!std::isfinite(nrm[k])) return set_error(LQCD_ERR_NOCONV, "residual of RHS %d is not finite", k);
       if (nrm[k] <= target[k]) {
         active[k] = 0;
+        parked[k] = 0;
         b.hs[k].active = 0.0;
         continue;
       }
       nact++;
+      parked[k] = 0;
+      b.hs[k].active = 1.0;  // a parked right-hand side that was not converged iterates again
       if (mixed) {  // p, v and rho_old follow r into the new normalisation
         const double f = sigma[k] / nrm[k];
         b.hfac[k] = f;
