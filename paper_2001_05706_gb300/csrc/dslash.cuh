@@ -641,12 +641,26 @@ template <int NR, int MODE> struct LaunchCfg<double, NR, MODE> {
 // (three 128-thread blocks): 1.31 / 1.40; 128 registers (four 128-thread
 // blocks): 1.20 / 1.61, the hop-only kernel tolerating its ~400 B of spills
 // while the clover-and-local kernel's 650 B cost more than the extra warps
-// gain; 204 registers (five 64-thread blocks): 1.30 / 1.39.  Hop-only modes
-// take 128 registers, modes with a local term 204.
+// gain; 204 registers (five 64-thread blocks): 1.30 / 1.39.  With the
+// compensated accumulators and the rolled direction loop (far fewer live
+// values) the balance moved: 128 registers 0.86 / 0.93, 204 registers 0.72 /
+// 0.74, 170 registers (six 64-thread blocks) 0.71 / 0.74, the choice for both.
+#ifndef LQCD_TDF_HOP
+#define LQCD_TDF_HOP 64
+#endif
+#ifndef LQCD_MDF_HOP
+#define LQCD_MDF_HOP 6
+#endif
+#ifndef LQCD_TDF_LOC
+#define LQCD_TDF_LOC 64
+#endif
+#ifndef LQCD_MDF_LOC
+#define LQCD_MDF_LOC 6
+#endif
 template <int NR, int MODE> struct LaunchCfg<df, NR, MODE> {
   static constexpr bool hop_only = MODE == MODE_HOP || MODE == MODE_HOP_AINV;
-  static constexpr int threads = NR > 1 ? 128 : (hop_only ? 128 : 64);
-  static constexpr int min_blocks = NR > 1 ? 1 : (hop_only ? 4 : 5);
+  static constexpr int threads = NR > 1 ? 128 : (hop_only ? LQCD_TDF_HOP : LQCD_TDF_LOC);
+  static constexpr int min_blocks = NR > 1 ? 1 : (hop_only ? LQCD_MDF_HOP : LQCD_MDF_LOC);
 };
 
 template <typename S, int R, int MODE, int NR>
