@@ -448,7 +448,7 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *c, const lqcd_field *f, double *result) {
   for (int p = 0; p < 2; p++) {
     if (!f->has(p)) continue;
     if (f->nrhs > 256) return set_error(LQCD_ERR_ARG, "norm2 supports up to 256 right-hand sides");
-    LQ_CU(blas_norm2(f->prec, c->Vh, f->nrhs, f->ref(p), c->partials, c->counter, c->results, 1, c->stream));
+    LQ_CU(blas_norm2(f->prec, c->Vh, f->nrhs, f->ref(p), c->partials, c->results, 1, c->stream));
     LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * f->nrhs, cudaMemcpyDeviceToHost, c->stream));
     LQ_CU(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < f->nrhs; k++) total += c->h_results[k];

@@ -105,8 +105,7 @@ __global__ void __launch_bounds__(kBiThreads) bi_s_kernel(long Vh, MutField sv, 
 
 // red[3k..] = (a, b), |a|^2 over the sites of RHS k
 template <typename S>
-__global__ void __launch_bounds__(kBiThreads) bi_dot3_kernel(long Vh, FieldRef a, FieldRef b, double *partials,
-                                                             unsigned *counter, double *red, int nrhs) {
+__global__ void __launch_bounds__(kBiThreads) bi_dot3_kernel(long Vh, FieldRef a, FieldRef b, double *partials) {
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
@@ -117,15 +116,14 @@ __global__ void __launch_bounds__(kBiThreads) bi_dot3_kernel(long Vh, FieldRef a
     load_spinor<S>(b, Vh, k, h, bv);
     site_dot3<T>(av, bv, o);
   }
-  grid_reduce<3>(o, partials, counter, red, 3 * k, 3 * nrhs);
+  block_partials<3>(o, partials, 3 * k);
 }
 
 // x += alpha p + omega s; r = s - omega t; red = (rhat, r) and |r|^2
 template <typename SX, typename S>
 __global__ void __launch_bounds__(kBiThreads) bi_xr_kernel(long Vh, MutField x, FieldRef p, FieldRef sv, FieldRef t,
                                                            MutField r, FieldRef rhat, const BiScalars *s,
-                                                           double *partials, unsigned *counter, double *red,
-                                                           int nrhs) {
+                                                           double *partials) {
   using T = typename Math<S>::T;
   using TX = typename Math<SX>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,7 +163,7 @@ __global__ void __launch_bounds__(kBiThreads) bi_xr_kernel(long Vh, MutField x, 
     o[1] = d[1];
     o[2] = n2[2];
   }
-  grid_reduce<3>(o, partials, counter, red, 3 * k, 3 * nrhs);
+  block_partials<3>(o, partials, 3 * k);
 }
 
 dim3 bgrid(long Vh, int nrhs) { return dim3((unsigned)((Vh + kBiThreads - 1) / kBiThreads), (unsigned)nrhs); }
@@ -198,40 +196,41 @@ cudaError_t bi_s(lqcd_prec pv, long Vh, int nrhs, MutField sv, FieldRef r, Field
   return cudaGetLastError();
 }
 
-cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, unsigned *counter,
-                    double *red, cudaStream_t st) {
-  LQ_BI_DISPATCH(pv, (bi_dot3_kernel<SV><<<bgrid(Vh, nrhs), kBiThreads, 0, st>>>(Vh, a, b, partials, counter, red,
-                                                                                  nrhs)));
-  return cudaGetLastError();
+cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, double *red,
+                    cudaStream_t st) {
+  const dim3 g = bgrid(Vh, nrhs);
+  LQ_BI_DISPATCH(pv, (bi_dot3_kernel<SV><<<g, kBiThreads, 0, st>>>(Vh, a, b, partials)));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish_reduce(partials, (int)g.x, 3 * nrhs, red, 1, st);
 }
 
 cudaError_t bi_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, FieldRef sv, FieldRef t,
-                  MutField r, FieldRef rhat, const BiScalars *s, double *partials, unsigned *counter, double *red,
-                  cudaStream_t st) {
+                  MutField r, FieldRef rhat, const BiScalars *s, double *partials, double *red, cudaStream_t st) {
   const dim3 g = bgrid(Vh, nrhs);
   if (px == pv && (pv == LQCD_F64 || pv == LQCD_DF64)) {
     if (pv == LQCD_F64)
-      bi_xr_kernel<double, double><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials, counter, red, nrhs);
+      bi_xr_kernel<double, double><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials);
     else
-      bi_xr_kernel<df, df><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials, counter, red, nrhs);
+      bi_xr_kernel<df, df><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials);
   } else if (px == LQCD_F32 && pv != LQCD_F64 && pv != LQCD_DF64) {
     switch (pv) {
       case LQCD_F32:
-        bi_xr_kernel<float, float><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials, counter, red, nrhs);
+        bi_xr_kernel<float, float><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials);
         break;
       case LQCD_F16:
-        bi_xr_kernel<float, __half><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials, counter, red,
-                                                              nrhs);
+        bi_xr_kernel<float, __half><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials);
         break;
       default:
-        bi_xr_kernel<float, __nv_bfloat16><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials, counter,
-                                                                     red, nrhs);
+        bi_xr_kernel<float, __nv_bfloat16><<<g, kBiThreads, 0, st>>>(Vh, x, p, sv, t, r, rhat, s, partials);
         break;
     }
   } else {
     return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish_reduce(partials, (int)g.x, 3 * nrhs, red, 1, st);
 }
 
 }  // namespace lqcd

@@ -17,7 +17,7 @@ constexpr int kBlasThreads = 256;
 template <typename SX, typename SV>
 __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x, FieldRef p, MutField r,
                                                              FieldRef q, SolverScalars *sc, int cur, double *partials,
-                                                             unsigned *counter, int nrhs) {
+                                                             int nrhs) {
   using TV = typename Math<SV>::T;
   using TX = typename Math<SX>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x
     nrm[0] = site_norm2<TV>(rv);
   }
   // an inactive right-hand side reduces zeros: its rr reads 0 from then on
-  grid_reduce<1>(nrm, partials, counter, &sc[0].rr, k, nrhs, (int)(sizeof(SolverScalars) / 8));
+  block_partials<1>(nrm, partials, k);
 }
 
 // p = s + beta p with beta = gamma[1-cur] / gamma[cur]
@@ -72,8 +72,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_p_kernel(long Vh, MutField p,
 
 // ||v||^2 per right-hand side into result[k * stride]
 template <typename S>
-__global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v, double *partials, unsigned *counter,
-                                                             double *result, int stride, int nrhs) {
+__global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v, double *partials, int nrhs) {
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
@@ -83,7 +82,7 @@ __global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v
     load_spinor<S>(v, Vh, k, h, a);
     nrm[0] = site_norm2<T>(a);
   }
-  grid_reduce<1>(nrm, partials, counter, result, k, nrhs, stride);
+  block_partials<1>(nrm, partials, k);
 }
 
 // y += f_k x  (per right-hand side factor f[k]; arithmetic in the wider of
@@ -134,6 +133,40 @@ __global__ void __launch_bounds__(kBlasThreads) scale_kernel(long Vh, MutField y
 
 static dim3 bgrid(long Vh, int nrhs) { return dim3((unsigned)((Vh + kBlasThreads - 1) / kBlasThreads), (unsigned)nrhs); }
 
+// one block per quantity: thread t adds partials t, t + 256, ... into eight
+// accumulators (independent loads in flight), then the fixed tree
+constexpr int kFinishThreads = 256;
+__global__ void __launch_bounds__(kFinishThreads) finish_reduce_kernel(const double *partials, int nblk,
+                                                                        double *result, int rstride) {
+  const int k = blockIdx.x, t = threadIdx.x;
+  const double *p = partials + (long)k * nblk;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = t;
+  for (; b + 7 * kFinishThreads < nblk; b += 8 * kFinishThreads) {
+#pragma unroll
+    for (int u = 0; u < 8; u++) a[u] += __ldcg(p + b + u * kFinishThreads);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; u++)
+    if (b + u * kFinishThreads < nblk) a[u] += __ldcg(p + b + u * kFinishThreads);
+  double v[1] = {((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]))};
+  __shared__ double sh[kFinishThreads / 32];
+  v[0] = warp_sum(v[0]);
+  if ((t & 31) == 0) sh[t >> 5] = v[0];
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kFinishThreads / 32; w++) s += sh[w];
+    result[(long)k * rstride] = s;
+  }
+}
+
+cudaError_t finish_reduce(const double *partials, int nblk, int nk, double *result, int rstride, cudaStream_t st) {
+  finish_reduce_kernel<<<nk, kFinishThreads, 0, st>>>(partials, nblk, result, rstride);
+  return cudaGetLastError();
+}
+
 long blas_blocks(long Vh) { return (Vh + kBlasThreads - 1) / kBlasThreads; }
 
 #define LQ_DISPATCH_V(prec, CALL)                                  \
@@ -146,18 +179,20 @@ long blas_blocks(long Vh) { return (Vh + kBlasThreads - 1) / kBlasThreads; }
   }
 
 cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, MutField r, FieldRef q,
-                       SolverScalars *sc, int cur, double *partials, unsigned *counter, cudaStream_t st) {
+                       SolverScalars *sc, int cur, double *partials, cudaStream_t st) {
   dim3 g = bgrid(Vh, nrhs);
   if (px == LQCD_F64 && pv == LQCD_F64) {
-    cg_xr_kernel<double, double><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs);
+    cg_xr_kernel<double, double><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, nrhs);
   } else if (px == LQCD_DF64 && pv == LQCD_DF64) {
-    cg_xr_kernel<df, df><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs);
+    cg_xr_kernel<df, df><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, nrhs);
   } else if (px == LQCD_F32) {
-    LQ_DISPATCH_V(pv, (cg_xr_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, counter, nrhs)));
+    LQ_DISPATCH_V(pv, (cg_xr_kernel<float, SV><<<g, kBlasThreads, 0, st>>>(Vh, x, p, r, q, sc, cur, partials, nrhs)));
   } else {
     return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish_reduce(partials, (int)g.x, nrhs, &sc[0].rr, (int)(sizeof(SolverScalars) / 8), st);
 }
 
 cudaError_t blas_cg_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef s, SolverScalars *sc, int cur,
@@ -167,11 +202,13 @@ cudaError_t blas_cg_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef s, S
   return cudaGetLastError();
 }
 
-cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, unsigned *counter,
-                       double *result, int stride, cudaStream_t st) {
+cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, double *result, int stride,
+                       cudaStream_t st) {
   dim3 g = bgrid(Vh, nrhs);
-  LQ_DISPATCH_V(pv, (norm2_kernel<SV><<<g, kBlasThreads, 0, st>>>(Vh, v, partials, counter, result, stride, nrhs)));
-  return cudaGetLastError();
+  LQ_DISPATCH_V(pv, (norm2_kernel<SV><<<g, kBlasThreads, 0, st>>>(Vh, v, partials, nrhs)));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish_reduce(partials, (int)g.x, nrhs, result, stride, st);
 }
 
 cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,

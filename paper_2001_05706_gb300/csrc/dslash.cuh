@@ -57,8 +57,7 @@ struct DslashParams {
   const float *lmat_scale;
   double alpha, beta, gz;
   int g5_in, g5_hop, g5_total;
-  double *norm_partials;  // nullptr: no norm
-  unsigned int *norm_counter;
+  double *norm_partials;  // nullptr: no norm (else per-block partials, summed by finish_reduce)
   double *norm_result;    // result of RHS r at norm_result[r * norm_stride]
   int norm_stride;
   unsigned int *dbg;      // builds with LQCD_DEBUG_BOUNDS: set to 1 on an out-of-range index
@@ -799,7 +798,7 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, 
       if (P.norm_partials) nrm[r] = site_norm2<T>(acc[r]);
     }
   }
-  if (P.norm_partials) grid_reduce<NR>(nrm, P.norm_partials, P.norm_counter, P.norm_result, rg * NR, P.nrhs, P.norm_stride);
+  if (P.norm_partials) block_partials<NR>(nrm, P.norm_partials, rg * NR);
 }
 
 // Host-side launcher, instantiated per storage type in dslash_<type>.cu.

@@ -13,7 +13,9 @@ static cudaError_t launch_one(const DslashParams &P, cudaStream_t st) {
   constexpr int T = LaunchCfg<S, NR, MODE>::threads;
   dim3 grid((unsigned)((P.h1 - P.h0 + T - 1) / T), (unsigned)(P.nrhs / NR));
   dslash_kernel<S, R, MODE, NR><<<grid, T, 0, st>>>(P);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !P.norm_partials) return e;
+  return finish_reduce(P.norm_partials, (int)grid.x, P.nrhs, P.norm_result, P.norm_stride, st);
 }
 
 template <typename S, int R, int MODE>

@@ -51,11 +51,11 @@ cudaError_t clover_build(const Geom &g, const double *U, double kappa, double cs
 // ---- blas.cu
 long blas_blocks(long Vh);
 cudaError_t blas_cg_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, MutField r, FieldRef q,
-                       SolverScalars *sc, int cur, double *partials, unsigned *counter, cudaStream_t st);
+                       SolverScalars *sc, int cur, double *partials, cudaStream_t st);
 cudaError_t blas_cg_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef s, SolverScalars *sc, int cur,
                       cudaStream_t st);
-cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, unsigned *counter,
-                       double *result, int stride, cudaStream_t st);
+cudaError_t blas_norm2(lqcd_prec pv, long Vh, int nrhs, FieldRef v, double *partials, double *result, int stride,
+                       cudaStream_t st);
 cudaError_t blas_axpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
                       cudaStream_t st);
 cudaError_t blas_scale(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double *f,
@@ -79,12 +79,11 @@ cudaError_t bi_p(lqcd_prec pv, long Vh, int nrhs, MutField p, FieldRef r, FieldR
 cudaError_t bi_s(lqcd_prec pv, long Vh, int nrhs, MutField sv, FieldRef r, FieldRef v, const BiScalars *s,
                  cudaStream_t st);
 // red[3k..3k+2] = (a_k^H b_k) re, im, |a_k|^2  (red may be any of the slots)
-cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, unsigned *counter,
-                    double *red, cudaStream_t st);
+cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, double *red,
+                    cudaStream_t st);
 // x += alpha p + omega s; r = s - omega t; red = (rhat, r), |r|^2
 cudaError_t bi_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, FieldRef sv, FieldRef t,
-                  MutField r, FieldRef rhat, const BiScalars *s, double *partials, unsigned *counter, double *red,
-                  cudaStream_t st);
+                  MutField r, FieldRef rhat, const BiScalars *s, double *partials, double *red, cudaStream_t st);
 
 // ---- dslash_<type>.cu
 cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);

@@ -221,7 +221,6 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
   if (norm_result) {
     LQ_TRY(ensure_partials(c, nrhs));
     P.norm_partials = c->partials;
-    P.norm_counter = c->counter;
     P.norm_result = norm_result;
     P.norm_stride = norm_stride;
   }

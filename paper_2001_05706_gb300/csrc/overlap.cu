@@ -669,7 +669,7 @@ lqcd_status field_norms(lqcd_ctx *c, const lqcd_field *v, int nrhs, std::vector<
   if (nrhs > 128) return set_error(LQCD_ERR_ARG, "at most 128 vectors per norm batch");
   LQ_TRY(ensure_partials(c, nrhs));
   for (int p = 0; p < 2; p++)
-    LQ_CU(blas_norm2(v->prec, c->Vh, nrhs, v->ref(p), c->partials, c->counter, c->results + 128 * p, 1, c->stream));
+    LQ_CU(blas_norm2(v->prec, c->Vh, nrhs, v->ref(p), c->partials, c->results + 128 * p, 1, c->stream));
   LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * 256, cudaMemcpyDeviceToHost, c->stream));
   LQ_CU(cudaStreamSynchronize(c->stream));
   out.resize(nrhs);

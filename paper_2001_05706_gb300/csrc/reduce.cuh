@@ -64,4 +64,35 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[NV], double *parti
   }
 }
 
+// The block-level half of a reduction for kernels whose grid has thousands of
+// blocks: each block adds its threads' NV values with the fixed shuffle tree
+// and writes one partial per quantity (same layout as grid_reduce); the sums
+// over blocks are left to finish_reduce, a separate launch that spreads them
+// over a whole block per quantity.  The last-block scheme of grid_reduce sums
+// thousands of partials with one warp, a latency-bound tail of tens of
+// microseconds per reduction.  All threads must call this.
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&v)[NV], double *partials, int kbase) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double s = lane < nwarp ? sh[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) partials[(long)(kbase + k) * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// result[k * rstride] = sum over b < nblk of partials[k * nblk + b], k < nk, in
+// a fixed order (blas.cu); stream-ordered after the kernel that wrote them
+cudaError_t finish_reduce(const double *partials, int nblk, int nk, double *result, int rstride, cudaStream_t st);
+
 }  // namespace lqcd

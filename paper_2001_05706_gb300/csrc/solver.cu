@@ -73,7 +73,7 @@ lqcd_status write_fac(lqcd_ctx *c, SolveBufs &B, int nrhs) {
 // norms of nrhs parity fields into host array out (FP64 reduction on GPU)
 lqcd_status norms(lqcd_ctx *c, lqcd_prec prec, int nrhs, FieldRef f, double *out) {
   LQ_TRY(ensure_partials(c, nrhs));
-  LQ_CU(blas_norm2(prec, c->Vh, nrhs, f, c->partials, c->counter, c->results, 1, c->stream));
+  LQ_CU(blas_norm2(prec, c->Vh, nrhs, f, c->partials, c->results, 1, c->stream));
   LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
   LQ_CU(cudaStreamSynchronize(c->stream));
   std::memcpy(out, c->h_results, sizeof(double) * nrhs);
@@ -139,7 +139,7 @@ lqcd_status cgls_plain(Work &W, SolveBufs &B) {
     for (int j = 0; j < W.check_every && it < W.max_iter; j++, it++) {
       LQ_TRY(op_mhat(c, P, W.recon64, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
       LQ_CU(blas_cg_xr(P, P, c->Vh, n, W.x64->mut(1), p->ref(1), W.r64->mut(1), q->ref(1), B.sc, cur, c->partials,
-                       c->counter, c->stream));
+                       c->stream));
       LQ_TRY(op_mhat(c, P, W.recon64, 1, n, s->mut(1), W.r64->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cur],
                      kScStride));
       LQ_CU(blas_cg_p(P, c->Vh, n, p->mut(1), s->ref(1), B.sc, cur, c->stream));
@@ -365,7 +365,7 @@ struct MixedCG {
   lqcd_status enqueue_iteration(cudaGraphConditionalHandle h, bool use_handle) const {
     LQ_TRY(op_mhat(c, L, W.recon_lo, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
     LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, 0, c->partials,
-                     c->counter, c->stream));
+                     c->stream));
     LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1],
                    kScStride));
     LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, 0, c->stream));
@@ -661,7 +661,7 @@ lqcd_status bicgstab(Work &W, bool mixed) {
     b.hs[k].active = active[k] ? 1.0 : 0.0;
   }
   LQ_CU(cudaMemcpyAsync(b.ds, b.hs, sizeof(BiScalars) * n, cudaMemcpyHostToDevice, c->stream));
-  LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, c->counter, red_xr, c->stream));
+  LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, red_xr, c->stream));
   lqcd_field *x = mixed ? xlo : W.x64;
   const lqcd_prec px = mixed ? LQCD_F32 : W.hp;
   const double delta2 = W.delta * W.delta;
@@ -671,14 +671,14 @@ lqcd_status bicgstab(Work &W, bool mixed) {
       LQ_CU(bi_scalar(BI_BETA, b.ds, red_xr, n, c->stream));
       LQ_CU(bi_p(L, c->Vh, n, p->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
       LQ_TRY(op_mhat(c, L, rec, 0, n, v->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
-      LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), v->ref(1), c->partials, c->counter, red_rv, c->stream));
+      LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), v->ref(1), c->partials, red_rv, c->stream));
       LQ_CU(bi_scalar(BI_ALPHA, b.ds, red_rv, n, c->stream));
       LQ_CU(bi_s(L, c->Vh, n, sv->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
       LQ_TRY(op_mhat(c, L, rec, 0, n, t->mut(1), sv->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
-      LQ_CU(bi_dot3(L, c->Vh, n, t->ref(1), sv->ref(1), c->partials, c->counter, red_ts, c->stream));
+      LQ_CU(bi_dot3(L, c->Vh, n, t->ref(1), sv->ref(1), c->partials, red_ts, c->stream));
       LQ_CU(bi_scalar(BI_OMEGA, b.ds, red_ts, n, c->stream));
       LQ_CU(bi_xr(px, L, c->Vh, n, x->mut(1), p->ref(1), sv->ref(1), t->ref(1), r->mut(1), rhat->ref(1), b.ds,
-                  c->partials, c->counter, red_xr, c->stream));
+                  c->partials, red_xr, c->stream));
       W.info->mhat_applies += 2;
     }
     LQ_CU(cudaMemcpyAsync(b.hred, b.red, sizeof(double) * kBiRed * n, cudaMemcpyDeviceToHost, c->stream));
@@ -751,7 +751,7 @@ lqcd_status bicgstab(Work &W, bool mixed) {
       LQ_CU(blas_scale(L, L, c->Vh, n, v->mut(1), v->ref(1), b.fac, c->stream));
     }
     LQ_TRY(load_r());
-    LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, c->counter, red_xr, c->stream));
+    LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), r->ref(1), c->partials, red_xr, c->stream));
   }
   W.info->iters = it;
   return nact == 0 ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "BiCGStab did not converge in %d iterations", W.max_iter);
