@@ -69,6 +69,8 @@ def _load():
                 "or_keep_parity": ([_ip, ctypes.c_int, _dp], None),
                 "or_apply_M": ([_ip, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int], None),
                 "or_apply_Mhat": ([_ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int], None),
+                "or_apply_Mhat_sym": ([_ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int],
+                                      None),
                 "or_mhat_slab": ([_ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int,
                                   _dp], None),
                 "or_prepare_source": ([_ip, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp], None),
@@ -266,6 +268,18 @@ def apply_Mhat(dims, U, A, Ainv, kappa, psi, tbc=1, dagger=False):
     psi = keep_parity(dims, _field(psi, V), 1)
     out = np.empty(spinor_shape(dims), dtype=_c)
     _load().or_apply_Mhat(Ld, int(tbc), _p(U), _opt(A), _opt(Ainv), float(kappa), _p(psi), _p(out), int(dagger))
+    return out
+
+
+def apply_Mhat_sym(dims, U, A, Ainv, kappa, psi, tbc=1, dagger=False):
+    """Symmetric even-odd Schur complement A_oo^-1 Mhat psi_o (or its adjoint
+    Mhat^dag A_oo^-1 psi_o); the standard alternative to the asymmetric form of
+    the even-odd preconditioned clover operator in the QUDA inverters (Sec. 3)."""
+    Ld, V = _dims(dims)
+    U = _links(U, V)
+    psi = keep_parity(dims, _field(psi, V), 1)
+    out = np.empty(spinor_shape(dims), dtype=_c)
+    _load().or_apply_Mhat_sym(Ld, int(tbc), _p(U), _opt(A), _opt(Ainv), float(kappa), _p(psi), _p(out), int(dagger))
     return out
 
 

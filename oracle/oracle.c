@@ -400,6 +400,26 @@ void or_apply_Mhat(const int L[4], int tbc, const cplx *U, const cplx *A, const 
   free(u);
 }
 
+/* The symmetric even-odd Schur complement, defined as A_oo^-1 Mhat:
+ * out_o = A_oo^-1 Mhat in_o (= in_o - kappa^2 A_oo^-1 D_oe A_ee^-1 D_eo in_o),
+ * or its adjoint Mhat^dag A_oo^-1 in_o (A^-1 is Hermitian).  Same field
+ * conventions as or_apply_Mhat. */
+void or_apply_Mhat_sym(const int L[4], int tbc, const cplx *U, const cplx *A, const cplx *Ainv, double kappa,
+                       const cplx *in, cplx *out, int dagger) {
+  long V = volume_of(L);
+  cplx *t = malloc(sizeof(cplx) * 12 * V);
+  if (!dagger) {
+    or_apply_Mhat(L, tbc, U, A, Ainv, kappa, in, t, 0);
+    or_site_mul(V, Ainv, t, out);
+  } else {
+    or_site_mul(V, Ainv, in, t);
+    or_keep_parity(L, 1, t);
+    or_apply_Mhat(L, tbc, U, A, Ainv, kappa, t, out, 1);
+  }
+  or_keep_parity(L, 1, out);
+  free(t);
+}
+
 /* Even-odd source: bhat_o = b_o + kappa D_oe A_ee^-1 b_e (odd sites of out). */
 void or_prepare_source(const int L[4], int tbc, const cplx *U, const cplx *Ainv, double kappa, const cplx *b,
                        cplx *bhat) {

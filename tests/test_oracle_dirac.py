@@ -247,6 +247,48 @@ def test_dense_schur_complement(dense24):
     assert np.abs(M[np.ix_(e, e)] - blk).max() < 1e-15
 
 
+def test_dense_symmetric_schur_complement(dense24):
+    """The symmetric form is M_oo^-1 times the Schur complement of M's even
+    block (M_oo = A_oo: the hop couples opposite parities only), its adjoint
+    is the conjugate transpose, and it solves for the same x_o as M x = b."""
+    dims, U, A, Ai, M = dense24
+    shape = oracle.spinor_shape(dims)
+    e = parity_flat_indices(dims, 0)
+    o = parity_flat_indices(dims, 1)
+    Moo, Moe, Meo, Mee = M[np.ix_(o, o)], M[np.ix_(o, e)], M[np.ix_(e, o)], M[np.ix_(e, e)]
+    schur = Moo - Moe @ np.linalg.solve(Mee, Meo)
+    sym = np.linalg.solve(Moo, schur)
+    assert np.abs(sym - (np.eye(len(o)) - np.linalg.solve(Moo, Moe) @ np.linalg.solve(Mee, Meo))).max() < 1e-13
+    Ms = dense_matrix(lambda v: oracle.apply_Mhat_sym(dims, U, A, Ai, 0.13, v), shape, o)
+    assert np.abs(Ms - sym).max() < 1e-13
+    Msd = dense_matrix(lambda v: oracle.apply_Mhat_sym(dims, U, A, Ai, 0.13, v, dagger=True), shape, o)
+    assert np.abs(Msd - sym.conj().T).max() < 1e-13
+    # same solution: x_o of M x = b solves sym x_o = M_oo^-1 (b_o - M_oe M_ee^-1 b_e)
+    b = gen.gaussian_spinor(dims, 9)[0].reshape(-1)
+    x = np.linalg.solve(M, b)
+    rhs = np.linalg.solve(Moo, b[o] - Moe @ np.linalg.solve(Mee, b[e]))
+    assert rel(np.linalg.solve(Ms, rhs), x[o]) < 1e-12
+    # the symmetric form is not gamma5-hermitian (unlike Mhat): g5 Ms g5 != Ms^dag
+    g5 = np.diag(np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), len(o) // 12))
+    assert np.abs(g5 @ Ms @ g5 - Msd).max() > 1e-3
+
+
+def test_symmetric_schur_adjoint_and_wilson_limit(rough):
+    dims, U, A, Ai = rough
+    u = oracle.keep_parity(dims, gen.gaussian_spinor(dims, 31)[0], 1)
+    v = oracle.keep_parity(dims, gen.gaussian_spinor(dims, 32)[0], 1)
+    Msv = oracle.apply_Mhat_sym(dims, U, A, Ai, KAPPA, v)
+    Msdu = oracle.apply_Mhat_sym(dims, U, A, Ai, KAPPA, u, dagger=True)
+    assert abs(_inner(u, Msv) - _inner(Msdu, v)) < 1e-12 * abs(_inner(u, Msv))
+    # Ms = 1 - kappa^2 A_oo^-1 D_oe A_ee^-1 D_eo, composed from the hop and the site matrices
+    t = oracle.keep_parity(dims, oracle.hop(dims, U, v), 0)
+    t = oracle.keep_parity(dims, oracle.hop(dims, U, oracle.site_mul(Ai, t)), 1)
+    assert rel(Msv, v - KAPPA ** 2 * oracle.site_mul(Ai, t)) < 1e-13
+    # c_sw = 0: A = 1 and the two forms coincide
+    assert rel(oracle.apply_Mhat_sym(dims, U, None, None, KAPPA, v), oracle.apply_Mhat(dims, U, None, None, KAPPA, v)) \
+        < 1e-15
+
+
 def test_dense_solve(dense24):
     dims, U, A, Ai, M = dense24
     b = gen.gaussian_spinor(dims, 8)[0]
