@@ -389,6 +389,51 @@ def run_multi_rhs(L, torch, lat, U, want_oracle, oracle_AAi):
     return res
 
 
+def run_schur_rough(L, torch, stream, want_oracle):
+    """Asymmetric (Mhat) against symmetric (A_oo^-1 Mhat) Schur complement on a
+    rough 32^3x64 field: eps 0.45 (mean plaquette ~0.59, as a quenched beta = 6
+    ensemble), c_sw 1.77, kappa 0.13, one Gaussian RHS to 1e-10."""
+    import gen
+    eps, kappa, csw = 0.45, 0.13, 1.77
+    U = gen.gauge_field(DIMS, eps, GAUGE_SEED)
+    b = gen.gaussian_spinor(DIMS, 2003)[0]
+    bt = torch.from_numpy(b.view(np.float64).copy()).cuda()
+    res = {"lattice": list(DIMS), "eps": eps, "kappa": kappa, "c_sw": csw, "tol": 1e-10}
+    cg, bi = L.LQCD_SOLVER_CGLS, L.LQCD_SOLVER_BICGSTAB
+    xs = {}
+    with L.Lattice(DIMS, stream=stream) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(kappa, csw)
+        for name, inner, outer, solver, schur in (
+                ("fp64_asym", L.LQCD_F64, L.LQCD_F64, cg, "asym"), ("fp64_sym", L.LQCD_F64, L.LQCD_F64, cg, "sym"),
+                ("mixed_f16_asym", L.LQCD_F16, L.LQCD_F64, cg, "asym"),
+                ("mixed_f16_sym", L.LQCD_F16, L.LQCD_F64, cg, "sym"),
+                ("bicgstab_mixed_f16_df64_asym", L.LQCD_F16, L.LQCD_DF64, bi, "asym"),
+                ("bicgstab_mixed_f16_df64_sym", L.LQCD_F16, L.LQCD_DF64, bi, "sym")):
+            xt = torch.zeros_like(bt)
+            prm = L.solve_params(tol=1e-10, max_iter=40000 if solver == cg else 8000, inner=inner, delta=0.1,
+                                 recon=18, inner_recon=12, check_every=0, outer=outer, solver=solver, schur=schur)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            res[name] = {"seconds": time.perf_counter() - t0, "iters": info.iters,
+                         "reliable_updates": info.reliable_updates, "mhat_applies": info.mhat_applies,
+                         "true_resid_gpu_fp64": info.true_resid[0],
+                         "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+            xs[name] = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
+    for pre in ("fp64", "mixed_f16", "bicgstab_mixed_f16_df64"):
+        a, y = res[pre + "_asym"], res[pre + "_sym"]
+        if a["status"] == "ok" and y["status"] == "ok":
+            res[pre + "_sym_speedup"] = a["seconds"] / y["seconds"]
+    if want_oracle:
+        import oracle
+        A = oracle.clover(DIMS, U, kappa, csw)
+        for name, x in xs.items():
+            res[name]["true_resid_oracle"] = oracle.true_residual(DIMS, U, A, kappa, x, b)
+    return res
+
+
 def run_batch(L, torch, stream):
     """Config 4 (ii): 24 lattices of uneven volume (8 each of 16^3x32, 20^3x40,
     24^3x48; eps 0.2, kappa 0.125, c_sw 1.0), 4 Gaussian RHS each, mixed
@@ -601,6 +646,7 @@ def run_gpu(args, rank, world, local_rank):
     solve = None
     if not args.no_solve and world == 1:
         solve = run_solves(L, torch, lat, U, rank, need_oracle, oracle_AAi)
+        solve["schur_forms_rough_field"] = run_schur_rough(L, torch, stream, need_oracle)
     multi = None
     if not args.no_batch and world == 1:
         multi = {"point_sources_32x32x32x64": run_multi_rhs(L, torch, lat, U, need_oracle, oracle_AAi),

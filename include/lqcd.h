@@ -90,7 +90,12 @@ typedef enum {
   LQCD_OP_HOP_OE = 5,       /* odd sites:    out_o = D_oe in_e                          */
   LQCD_OP_HW = 6,           /* full lattice: out = g5 [(4 - rho) in - D in / 2]         */
   LQCD_OP_K2A = 7,          /* even sites:   out_e = A_ee^-1 D_eo in_o (c_sw = 0: D_eo) */
-  LQCD_OP_M_DAG = 8         /* full lattice: out = M^dag in = g5 M g5 in                */
+  LQCD_OP_M_DAG = 8,        /* full lattice: out = M^dag in = g5 M g5 in                */
+  LQCD_OP_MHAT_SYM = 9,     /* odd sites:    out_o = A_oo^-1 Mhat in_o                  */
+                            /*   = in_o - kappa^2 A_oo^-1 D_oe A_ee^-1 D_eo in_o         */
+                            /*   (the symmetric Schur complement; c_sw = 0: Mhat)        */
+  LQCD_OP_MHAT_SYM_DAG = 10 /* odd sites:    out_o = (A_oo^-1 Mhat)^dag in_o            */
+                            /*   = in_o - kappa^2 g5 D_oe A_ee^-1 D_eo g5 A_oo^-1 in_o   */
 } lqcd_op;
 
 typedef struct lqcd_ctx lqcd_ctx;     /* one lattice geometry, gauge field and clover term */
@@ -194,6 +199,19 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *ctx, const lqcd_field *field, double *res
  * ports, includes it).  lqcd_solve_batch runs CGLS only. */
 typedef enum { LQCD_SOLVER_CGLS = 0, LQCD_SOLVER_BICGSTAB = 1 } lqcd_solver;
 
+/* Even-odd reduced operator the recursion works on.  Both solve the same
+ * system M x = b (same x_o):
+ *   LQCD_SCHUR_ASYM: Mhat x_o = bhat_o with Mhat = A_oo - kappa^2 D_oe A_ee^-1 D_eo
+ *   LQCD_SCHUR_SYM:  A_oo^-1 Mhat x_o = A_oo^-1 bhat_o, i.e.
+ *                    (1 - kappa^2 A_oo^-1 D_oe A_ee^-1 D_eo) x_o = A_oo^-1 bhat_o
+ * The symmetric form has the better-conditioned operator on rough gauge fields
+ * (fewer iterations); its application costs the same bytes as Mhat, its
+ * adjoint one more site-local clover pass.  Its iterated residual is
+ * A_oo^-1 (bhat - Mhat x), so the solver's targets are divided by a
+ * Gershgorin bound of ||A_oo|| taken when the clover term is built: the
+ * true residual still meets tol.  With c_sw = 0 the two forms coincide. */
+typedef enum { LQCD_SCHUR_ASYM = 0, LQCD_SCHUR_SYM = 1 } lqcd_schur;
+
 typedef struct {
   double tol;          /* target ||b - M x|| / ||b|| on the full lattice, > 0     */
   int max_iter;        /* cap on CG iterations (inner iterations when mixed)       */
@@ -211,6 +229,8 @@ typedef struct {
                        /* LQCD_DF64; the final residual check is FP64 either way  */
   int solver;          /* lqcd_solver: LQCD_SOLVER_CGLS (0, the default: CG on    */
                        /* the normal equations) or LQCD_SOLVER_BICGSTAB           */
+  int schur;           /* lqcd_schur: LQCD_SCHUR_ASYM (0, the default) or         */
+                       /* LQCD_SCHUR_SYM; any solver, plain, mixed and batched    */
 } lqcd_solve_params;
 
 typedef struct {

@@ -35,19 +35,19 @@ LQCD_F64, LQCD_F32, LQCD_F16, LQCD_BF16, LQCD_DF64 = 0, 1, 2, 3, 4
 LQCD_RECON_18, LQCD_RECON_12 = 18, 12
 LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
 (LQCD_OP_M, LQCD_OP_MHAT, LQCD_OP_MHAT_DAG, LQCD_OP_MHAT_NORMAL, LQCD_OP_HOP_EO, LQCD_OP_HOP_OE, LQCD_OP_HW,
- LQCD_OP_K2A, LQCD_OP_M_DAG) = range(9)
+ LQCD_OP_K2A, LQCD_OP_M_DAG, LQCD_OP_MHAT_SYM, LQCD_OP_MHAT_SYM_DAG) = range(11)
 
 PREC = {"f64": LQCD_F64, "f32": LQCD_F32, "f16": LQCD_F16, "bf16": LQCD_BF16, "df64": LQCD_DF64}
 OPS = {"M": LQCD_OP_M, "MHAT": LQCD_OP_MHAT, "MHAT_DAG": LQCD_OP_MHAT_DAG, "MHAT_NORMAL": LQCD_OP_MHAT_NORMAL,
        "HOP_EO": LQCD_OP_HOP_EO, "HOP_OE": LQCD_OP_HOP_OE, "HW": LQCD_OP_HW, "K2A": LQCD_OP_K2A,
-       "M_DAG": LQCD_OP_M_DAG}
+       "M_DAG": LQCD_OP_M_DAG, "MHAT_SYM": LQCD_OP_MHAT_SYM, "MHAT_SYM_DAG": LQCD_OP_MHAT_SYM_DAG}
 
 
 class lqcd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("use_x0", ctypes.c_int),
                 ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("outer", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("solver", ctypes.c_int), ("schur", ctypes.c_int)]
 
 
 class lqcd_overlap_params(ctypes.Structure):
@@ -298,14 +298,19 @@ def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):
 
 LQCD_SOLVER_CGLS, LQCD_SOLVER_BICGSTAB = 0, 1
 SOLVERS = {"cgls": LQCD_SOLVER_CGLS, "bicgstab": LQCD_SOLVER_BICGSTAB}
+LQCD_SCHUR_ASYM, LQCD_SCHUR_SYM = 0, 1
+SCHUR = {"asym": LQCD_SCHUR_ASYM, "sym": LQCD_SCHUR_SYM}
 
 
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,
-                 inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64, solver=LQCD_SOLVER_CGLS):
+                 inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64, solver=LQCD_SOLVER_CGLS,
+                 schur=LQCD_SCHUR_ASYM):
     if isinstance(solver, str):
         solver = SOLVERS[solver]
+    if isinstance(schur, str):
+        schur = SCHUR[schur]
     return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every, outer,
-                             solver)
+                             solver, schur)
 
 
 # ---- convenience ------------------------------------------------------------

@@ -219,6 +219,7 @@ lqcd_status lqcd_clover(lqcd_ctx *c, double kappa, double c_sw) {
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!(kappa == kappa) || !(c_sw == c_sw)) return set_error(LQCD_ERR_ARG, "kappa or c_sw is NaN");
   free_clover(c);
+  c->a_bound[0] = c->a_bound[1] = 1.0;
   c->kappa = kappa;
   c->csw = c_sw;
   c->have_kappa = true;
@@ -235,13 +236,20 @@ lqcd_status lqcd_clover(lqcd_ctx *c, double kappa, double c_sw) {
     A[q] = (double *)m.A[q];
     Ai[q] = (double *)m.Ainv[q];
   }
+  // results[0]: the singular flag; results[1], results[2]: the per-parity norm bounds
   int *sing = reinterpret_cast<int *>(c->results);
-  LQ_CU(cudaMemsetAsync(sing, 0, sizeof(int), c->stream));
-  LQ_CU(clover_build(c->geom, c->U64, kappa, c_sw, A, Ai, sing, c->stream));
-  LQ_CU(cudaMemcpyAsync(c->h_results, sing, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long *bound = reinterpret_cast<unsigned long long *>(c->results + 1);
+  LQ_CU(cudaMemsetAsync(c->results, 0, 3 * sizeof(double), c->stream));
+  LQ_CU(clover_build(c->geom, c->U64, kappa, c_sw, A, Ai, sing, bound, c->stream));
+  LQ_CU(cudaMemcpyAsync(c->h_results, c->results, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LQ_CU(cudaStreamSynchronize(c->stream));
   int hs = 0;
   std::memcpy(&hs, c->h_results, sizeof(int));
+  for (int q = 0; q < 2; q++) {
+    unsigned long long bits;
+    std::memcpy(&bits, c->h_results + 1 + q, sizeof(bits));
+    std::memcpy(&c->a_bound[q], &bits, sizeof(double));
+  }
   c->clover_on = true;
   if (hs) {
     free_clover(c);
@@ -385,6 +393,15 @@ static lqcd_status apply_fields(lqcd_ctx *c, lqcd_op op, int recon, lqcd_field *
       }
       return op_mhat(c, prec, recon, op == LQCD_OP_MHAT_DAG, nrhs, out->mut(1), in->ref(1), y->mut(0), kNoField, 0.0,
                      nullptr, 0);
+    }
+    case LQCD_OP_MHAT_SYM:
+    case LQCD_OP_MHAT_SYM_DAG: {
+      LQ_TRY(need(in->has(1) && out->has(1), "needs odd-parity input and output"));
+      lqcd_field *y, *t;
+      LQ_TRY(temp_field(c, prec, LQCD_EVEN, nrhs, 0, &y));
+      LQ_TRY(temp_field(c, prec, LQCD_ODD, nrhs, 1, &t));
+      return op_mhat_sym(c, prec, recon, op == LQCD_OP_MHAT_SYM_DAG, nrhs, out->mut(1), in->ref(1), y->mut(0),
+                         t->mut(1), nullptr, 0);
     }
     case LQCD_OP_K2A:
       LQ_TRY(need(in->has(1) && out->has(0), "needs odd input and even output"));
@@ -559,7 +576,7 @@ lqcd_status lqcd_dslash(lqcd_ctx *c, double *out, const double *in, int nrhs, lq
   if (out == in) return set_error(LQCD_ERR_ARG, "out and in must not alias");
   if (nrhs < 1 || nrhs > 4096) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..4096");
   if ((int)prec < 0 || (int)prec > 4) return set_error(LQCD_ERR_ARG, "bad precision");
-  if ((int)op < 0 || (int)op > 8) return set_error(LQCD_ERR_ARG, "bad op");
+  if ((int)op < 0 || (int)op > 10) return set_error(LQCD_ERR_ARG, "bad op");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!on_device && op == LQCD_OP_MHAT && c->have_kappa && !std::getenv("LQCD_NO_PIPELINE")) {
     // chunks of whole time slices, at least 4 of them, at most LQCD_HOST_CHUNKS (default 32,
@@ -589,7 +606,8 @@ lqcd_status lqcd_dslash(lqcd_ctx *c, double *out, const double *in, int nrhs, lq
   for (int p = 0; p < 2; p++) {
     const bool written = full || (p == 0 ? (op == LQCD_OP_HOP_EO || op == LQCD_OP_K2A)
                                          : (op == LQCD_OP_MHAT || op == LQCD_OP_MHAT_DAG ||
-                                            op == LQCD_OP_MHAT_NORMAL || op == LQCD_OP_HOP_OE));
+                                            op == LQCD_OP_MHAT_NORMAL || op == LQCD_OP_HOP_OE ||
+                                            op == LQCD_OP_MHAT_SYM || op == LQCD_OP_MHAT_SYM_DAG));
     if (written)
       LQ_CU(unpack_spinor(prec, c->geom, p, fout->data[p], fout->scale[p], fout->rhs_words(), nrhs, dout, c->stream));
     else

@@ -146,7 +146,8 @@ __device__ __forceinline__ void store_block(double *base, long Vh, long h, int b
 
 __global__ void __launch_bounds__(64) clover_build_kernel(Geom g, const double *__restrict__ U, double kappa,
                                                            double csw, double *A0, double *A1, double *Ai0,
-                                                           double *Ai1, int *singular) {
+                                                           double *Ai1, int *singular,
+                                                           unsigned long long *bound) {
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long V = 2 * g.Vh;
   if (s >= V) return;
@@ -177,6 +178,17 @@ __global__ void __launch_bounds__(64) clover_build_kernel(Geom g, const double *
     }
   double *A = p ? A1 : A0;
   double *Ai = p ? Ai1 : Ai0;
+  // Gershgorin: every eigenvalue of a Hermitian block lies within
+  // |a_ii| + sum_{j != i} |a_ij| of 0, so the largest row sum bounds ||A||
+  double gb = 0.0;
+  for (int b = 0; b < 2; b++)
+    for (int i = 0; i < 6; i++) {
+      double row = 0.0;
+      for (int j = 0; j < 6; j++) row += hypot(Ab[b][i][j].r, Ab[b][i][j].i);
+      gb = fmax(gb, row);
+    }
+  // non-negative doubles order like their bit patterns
+  atomicMax(bound + p, (unsigned long long)__double_as_longlong(gb));
   for (int b = 0; b < 2; b++) {
     store_block(A, g.Vh, h, b, Ab[b]);
     cx<double> inv[6][6];
@@ -190,10 +202,10 @@ __global__ void __launch_bounds__(64) clover_build_kernel(Geom g, const double *
 }
 
 cudaError_t clover_build(const Geom &g, const double *U, double kappa, double csw, double *A[2], double *Ainv[2],
-                         int *singular, cudaStream_t st) {
+                         int *singular, unsigned long long *bound, cudaStream_t st) {
   const long V = 2 * g.Vh;
   clover_build_kernel<<<(unsigned)((V + 63) / 64), 64, 0, st>>>(g, U, kappa, csw, A[0], A[1], Ainv[0], Ainv[1],
-                                                                 singular);
+                                                                 singular, bound);
   return cudaGetLastError();
 }
 

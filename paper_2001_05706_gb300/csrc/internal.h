@@ -45,8 +45,10 @@ size_t clover_bytes(lqcd_prec prec, long Vh);
 cudaError_t pack_clover(lqcd_prec prec, long Vh, const double *in, void *out, float *scale, cudaStream_t st);
 
 // ---- clover.cu
+// bound[p] (as the bits of a non-negative double, max-combined): a Gershgorin
+// bound of ||A|| over the sites of parity p
 cudaError_t clover_build(const Geom &g, const double *U, double kappa, double csw, double *A[2], double *Ainv[2],
-                         int *singular, cudaStream_t st);
+                         int *singular, unsigned long long *bound, cudaStream_t st);
 
 // ---- blas.cu
 long blas_blocks(long Vh);
@@ -137,6 +139,7 @@ struct lqcd_ctx {
   double kappa = 0, csw = 0;
   bool have_kappa = false;
   bool clover_on = false;  // csw != 0 and built
+  double a_bound[2] = {1.0, 1.0};  // per parity: Gershgorin bound of ||A|| (1 without clover)
   CloverStore clov[5];  // indexed by lqcd_prec
   double rho = 0;
   bool have_rho = false;
@@ -152,7 +155,7 @@ struct lqcd_ctx {
   // copy streams and per-chunk events of the pipelined host-buffer dslash
   cudaStream_t copy_stream[2] = {nullptr, nullptr};
   cudaEvent_t chunk_event[2][64] = {};
-  // cached intermediate fields (key: 10*prec + nrhs*1000 + slot)
+  // cached intermediate fields (key: slot, subset, prec, nrhs; see temp_field)
   std::map<long, lqcd_field *> temps;
   // overlap operator state (low modes, Chebyshev coefficients), overlap.cu
   lqcd::OverlapState *ov = nullptr;
@@ -200,6 +203,13 @@ lqcd_status op_k2b(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs,
 // out_o = Mhat x_o or Mhat^dag x_o, y_e scratch
 lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
                     MutField y_e, FieldRef zf, double gz, double *norm_result, int norm_stride);
+// out_o = A_oo^-1 Mhat x_o (the symmetric Schur complement) or its adjoint;
+// y_e and t_o scratch (t_o used by the adjoint only)
+lqcd_status op_mhat_sym(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                        MutField y_e, MutField t_o, double *norm_result, int norm_stride);
+// out_o = A_oo^-1 x_o (site-local), optional norm
+lqcd_status op_ainv_odd(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out_o, FieldRef x_o,
+                        double *norm_result, int norm_stride);
 // full-lattice out = [zf + gz*] M x (dagger: M^dag), per parity
 lqcd_status op_M(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out[2], FieldRef x[2],
                  FieldRef zf[2], double gz, double *norm_result, int norm_stride);

@@ -270,6 +270,37 @@ lqcd_status op_mhat(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs
   return op_k2b(c, prec, recon, dagger, nrhs, out_o, x_o, y_e.ref(), zf, gz, norm_result, norm_stride);
 }
 
+lqcd_status op_ainv_odd(lqcd_ctx *c, lqcd_prec prec, int recon, int nrhs, MutField out_o, FieldRef x_o,
+                        double *norm_result, int norm_stride) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  if (!c->clover_on) return set_error(LQCD_ERR_STATE, "no clover term");
+  return run_dslash(c, prec, recon, MODE_FOLDED_AINV, 1, nrhs, out_o, kNone, x_o, kNone, 1.0, 0.0, 0.0, 0, 0, 0,
+                    norm_result, norm_stride);
+}
+
+// Symmetric Schur complement Mhat_s = A_oo^-1 Mhat = 1 - kappa^2 A_oo^-1 D_oe A_ee^-1 D_eo.
+// Forward: K2a, then the second hop with A_oo^-1 applied to the hop sum and x_o
+// added in the epilogue (same bytes as K2b: A_oo^-1 replaces A_oo).  Adjoint,
+// with A Hermitian, commuting with g5, and D_eo^dag = g5 D_oe g5:
+//   Mhat_s^dag = 1 - kappa^2 g5 D_oe A_ee^-1 D_eo g5 A_oo^-1,
+// i.e. a site-local A_oo^-1 pass, K2a with g5 on its input, and the second
+// hop with g5 on the hop sum plus x_o.  c_sw = 0: A = 1 and Mhat_s = Mhat.
+lqcd_status op_mhat_sym(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out_o, FieldRef x_o,
+                        MutField y_e, MutField t_o, double *norm_result, int norm_stride) {
+  if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
+  if (!c->clover_on) return op_mhat(c, prec, recon, dagger, nrhs, out_o, x_o, y_e, kNone, 0.0, norm_result, norm_stride);
+  const double k2 = c->kappa * c->kappa;
+  if (!dagger) {
+    LQ_TRY(op_k2a(c, prec, recon, 0, nrhs, y_e, x_o));
+    return run_dslash(c, prec, recon, MODE_HOP_AINV, 1, nrhs, out_o, y_e.ref(), kNone, x_o, 0.0, -k2, 1.0, 0, 0, 0,
+                      norm_result, norm_stride);
+  }
+  LQ_TRY(op_ainv_odd(c, prec, recon, nrhs, t_o, x_o, nullptr, 0));
+  LQ_TRY(op_k2a(c, prec, recon, 1, nrhs, y_e, t_o.ref()));
+  return run_dslash(c, prec, recon, MODE_LOCAL_IDENT, 1, nrhs, out_o, y_e.ref(), x_o, kNone, 1.0, -k2, 0.0, 0, 1, 0,
+                    norm_result, norm_stride);
+}
+
 lqcd_status op_M(lqcd_ctx *c, lqcd_prec prec, int recon, int dagger, int nrhs, MutField out[2], FieldRef x[2],
                  FieldRef zf[2], double gz, double *norm_result, int norm_stride) {
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");

@@ -91,7 +91,34 @@ struct Work {
   std::vector<double> bnorm;  // ||b|| full lattice per RHS
   lqcd_field *bhat, *x64, *r64;  // precision hp: bhat_o, x (odd part used), r_o
   lqcd_solve_info *info;
+  int schur = LQCD_SCHUR_ASYM;
+  // targets on the recursion's residual are 0.5 tol ||b|| / rscale: 1 for Mhat; a
+  // bound of ||A_oo|| for A_oo^-1 Mhat, whose residual is A_oo^-1 times the true one
+  double rscale = 1.0;
+  lqcd_field *t_hp = nullptr, *t_lo = nullptr;  // odd scratch of the symmetric form (precision hp, lo)
 };
+
+// The recursion's operator: Mhat x_o, or A_oo^-1 Mhat x_o with the symmetric
+// Schur form (or the adjoint), optional fused norm.
+lqcd_status op_eo(const Work &W, lqcd_prec prec, int recon, int dagger, MutField out, FieldRef x, lqcd_field *ye,
+                  double *norm, int stride) {
+  if (W.schur == LQCD_SCHUR_SYM) {
+    lqcd_field *t = prec == W.hp ? W.t_hp : W.t_lo;
+    return op_mhat_sym(W.c, prec, recon, dagger, W.nrhs, out, x, ye->mut(0), t->mut(1), norm, stride);
+  }
+  return op_mhat(W.c, prec, recon, dagger, W.nrhs, out, x, ye->mut(0), kNone, 0.0, norm, stride);
+}
+
+// The recursion's residual in precision hp: bhat - Mhat x, or A_oo^-1 (bhat -
+// Mhat x) = A_oo^-1 bhat - A_oo^-1 Mhat x for the symmetric form, with its norm.
+lqcd_status residual_eo(const Work &W, MutField r, FieldRef x, lqcd_field *ye, double *norm, int stride) {
+  if (W.schur == LQCD_SCHUR_SYM) {
+    LQ_TRY(op_mhat(W.c, W.hp, W.recon64, 0, W.nrhs, W.t_hp->mut(1), x, ye->mut(0), W.bhat->ref(1), -1.0, nullptr,
+                   0));
+    return op_ainv_odd(W.c, W.hp, W.recon64, W.nrhs, r, W.t_hp->ref(1), norm, stride);
+  }
+  return op_mhat(W.c, W.hp, W.recon64, 0, W.nrhs, r, x, ye->mut(0), W.bhat->ref(1), -1.0, norm, stride);
+}
 
 // Plain CGLS in FP64 or DF64: iterate until every RHS has ||r|| <= target,
 // where r is recomputed as bhat - Mhat x before a right-hand side is accepted.
@@ -107,13 +134,11 @@ lqcd_status cgls_plain(Work &W, SolveBufs &B) {
   LQ_TRY(temp_field(c, P, LQCD_EVEN, n, 23, &ye));
   LQ_TRY(ensure_partials(c, n));
   std::vector<double> target2(n);
-  for (int k = 0; k < n; k++) target2[k] = std::pow(0.5 * W.tol * W.bnorm[k], 2);
+  for (int k = 0; k < n; k++) target2[k] = std::pow(0.5 * W.tol * W.bnorm[k] / W.rscale, 2);
   // r = bhat - Mhat x ; s = Mhat^dag r ; p = s
-  LQ_TRY(op_mhat(c, P, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye->mut(0), W.bhat->ref(1), -1.0, &B.sc[0].rr,
-                 kScStride));
+  LQ_TRY(residual_eo(W, W.r64->mut(1), W.x64->ref(1), ye, &B.sc[0].rr, kScStride));
   int cur = 0;
-  LQ_TRY(op_mhat(c, P, W.recon64, 1, n, s->mut(1), W.r64->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[cur],
-                 kScStride));
+  LQ_TRY(op_eo(W, P, W.recon64, 1, s->mut(1), W.r64->ref(1), ye, &B.sc[0].gamma[cur], kScStride));
   LQ_CU(cudaMemcpyAsync(p->data[1], s->data[1], (size_t)p->rhs_words() * 16 * n, cudaMemcpyDeviceToDevice, c->stream));
   W.info->mhat_applies += 2;
   int it = 0;
@@ -137,11 +162,10 @@ lqcd_status cgls_plain(Work &W, SolveBufs &B) {
     if (changed) LQ_TRY(write_scalars(c, B, n));
     if (all_done || it >= W.max_iter) break;
     for (int j = 0; j < W.check_every && it < W.max_iter; j++, it++) {
-      LQ_TRY(op_mhat(c, P, W.recon64, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
+      LQ_TRY(op_eo(W, P, W.recon64, 0, q->mut(1), p->ref(1), ye, &B.sc[0].qq, kScStride));
       LQ_CU(blas_cg_xr(P, P, c->Vh, n, W.x64->mut(1), p->ref(1), W.r64->mut(1), q->ref(1), B.sc, cur, c->partials,
                        c->stream));
-      LQ_TRY(op_mhat(c, P, W.recon64, 1, n, s->mut(1), W.r64->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1 - cur],
-                     kScStride));
+      LQ_TRY(op_eo(W, P, W.recon64, 1, s->mut(1), W.r64->ref(1), ye, &B.sc[0].gamma[1 - cur], kScStride));
       LQ_CU(blas_cg_p(P, c->Vh, n, p->mut(1), s->ref(1), B.sc, cur, c->stream));
       cur ^= 1;
       W.info->mhat_applies += 2;
@@ -151,8 +175,7 @@ lqcd_status cgls_plain(Work &W, SolveBufs &B) {
     bool any = false;
     for (int k = 0; k < n; k++) any |= (B.h_sc[k].active != 0.0 && B.h_sc[k].rr <= target2[k]);
     if (any) {
-      LQ_TRY(op_mhat(c, P, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye->mut(0), W.bhat->ref(1), -1.0,
-                     &B.sc[0].aux, kScStride));
+      LQ_TRY(residual_eo(W, W.r64->mut(1), W.x64->ref(1), ye, &B.sc[0].aux, kScStride));
       W.info->mhat_applies += 1;
       W.info->reliable_updates += 1;
       LQ_TRY(read_scalars(c, B, n));
@@ -312,13 +335,12 @@ struct MixedCG {
     }
     target.assign(n, 0.0);
     sigma.assign(n, 0.0);
-    for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
+    for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k] / W.rscale;
     delta2 = W.delta * W.delta;
     rhs_bytes64 = (size_t)xtry->rhs_words() * 16;
     xlo_bytes = (size_t)xlo->rhs_words() * 16 * n;
     // r64 = bhat - Mhat64 x64 -> sigma
-    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
-                   &B.sc[0].aux, kScStride));
+    LQ_TRY(residual_eo(W, W.r64->mut(1), W.x64->ref(1), ye64, &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
     LQ_TRY(read_scalars(c, B, n));
     int nactive = 0;
@@ -342,8 +364,7 @@ struct MixedCG {
     // r_lo = r64 / sigma ; x_lo = 0 ; s = Mhat^dag r -> gamma[0] ; p = s
     LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac, c->stream));
     LQ_CU(cudaMemsetAsync(xlo->data[1], 0, xlo_bytes, c->stream));
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
-                   kScStride));
+    LQ_TRY(op_eo(W, L, W.recon_lo, 1, s->mut(1), r->ref(1), ye, &B.sc[0].gamma[0], kScStride));
     LQ_CU(cudaMemcpyAsync(p->data[1], s->data[1], (size_t)p->rhs_words() * 16 * n, cudaMemcpyDeviceToDevice,
                           c->stream));
     if (p->scale[1])
@@ -363,11 +384,10 @@ struct MixedCG {
   // one CG iteration and the control kernel; the new gamma goes to slot 1 and
   // the control kernel moves it to slot 0
   lqcd_status enqueue_iteration(cudaGraphConditionalHandle h, bool use_handle) const {
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 0, n, q->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].qq, kScStride));
+    LQ_TRY(op_eo(W, L, W.recon_lo, 0, q->mut(1), p->ref(1), ye, &B.sc[0].qq, kScStride));
     LQ_CU(blas_cg_xr(LQCD_F32, L, c->Vh, n, xlo->mut(1), p->ref(1), r->mut(1), q->ref(1), B.sc, 0, c->partials,
                      c->stream));
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[1],
-                   kScStride));
+    LQ_TRY(op_eo(W, L, W.recon_lo, 1, s->mut(1), r->ref(1), ye, &B.sc[0].gamma[1], kScStride));
     LQ_CU(blas_cg_p(L, c->Vh, n, p->mut(1), s->ref(1), B.sc, 0, c->stream));
     cg_control_kernel<<<1, 64, 0, c->stream>>>(B.sc, dcr, dcg, n, h, use_handle ? 1 : 0);
     LQ_CU(cudaGetLastError());
@@ -409,8 +429,7 @@ struct MixedCG {
     LQ_TRY(write_fac(c, B, n));
     LQ_CU(cudaMemcpyAsync(xtry->data[1], W.x64->data[1], rhs_bytes64 * n, cudaMemcpyDeviceToDevice, c->stream));
     LQ_CU(blas_axpy(W.hp, LQCD_F32, c->Vh, n, xtry->mut(1), xlo->ref(1), B.fac, c->stream));
-    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, rtry->mut(1), xtry->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
-                   &B.sc[0].aux, kScStride));
+    LQ_TRY(residual_eo(W, rtry->mut(1), xtry->ref(1), ye64, &B.sc[0].aux, kScStride));
     W.info->mhat_applies += 1;
     W.info->reliable_updates += 1;
     LQ_TRY(read_scalars(c, B, n));
@@ -461,8 +480,7 @@ struct MixedCG {
     LQ_TRY(upload_ctrl());
     LQ_CU(blas_scale(L, L, c->Vh, n, p->mut(1), p->ref(1), B.fac, c->stream));
     LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), B.fac + n, c->stream));
-    LQ_TRY(op_mhat(c, L, W.recon_lo, 1, n, s->mut(1), r->ref(1), ye->mut(0), kNone, 0.0, &B.sc[0].gamma[0],
-                   kScStride));
+    LQ_TRY(op_eo(W, L, W.recon_lo, 1, s->mut(1), r->ref(1), ye, &B.sc[0].gamma[0], kScStride));
     LQ_CU(blas_axpy(L, L, c->Vh, n, p->mut(1), s->ref(1), B.fac + 2 * n, c->stream));
     W.info->mhat_applies += 1;
     LQ_CU(cudaStreamSynchronize(c->stream));
@@ -613,11 +631,10 @@ lqcd_status bicgstab(Work &W, bool mixed) {
   const size_t sbytes = r->scale[1] ? sizeof(float) * c->Vh * n : 0;
   std::vector<double> target(n), sigma(n, 1.0), nrm(n);
   std::vector<char> active(n, 1), parked(n, 0);
-  for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k];
-  // high-precision residual r64 = bhat - Mhat x64 and its norms
+  for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k] / W.rscale;
+  // high-precision residual r64 = bhat - Mhat x64 (symmetric form: A_oo^-1 times it) and its norms
   auto true_residual = [&]() -> lqcd_status {
-    LQ_TRY(op_mhat(c, W.hp, W.recon64, 0, n, W.r64->mut(1), W.x64->ref(1), ye64->mut(0), W.bhat->ref(1), -1.0,
-                   c->results, 1));
+    LQ_TRY(residual_eo(W, W.r64->mut(1), W.x64->ref(1), ye64, c->results, 1));
     LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     LQ_CU(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n; k++) nrm[k] = std::sqrt(c->h_results[k]);
@@ -670,11 +687,11 @@ lqcd_status bicgstab(Work &W, bool mixed) {
     for (int j = 0; j < W.check_every && it < W.max_iter; j++, it++) {
       LQ_CU(bi_scalar(BI_BETA, b.ds, red_xr, n, c->stream));
       LQ_CU(bi_p(L, c->Vh, n, p->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
-      LQ_TRY(op_mhat(c, L, rec, 0, n, v->mut(1), p->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
+      LQ_TRY(op_eo(W, L, rec, 0, v->mut(1), p->ref(1), ye, nullptr, 0));
       LQ_CU(bi_dot3(L, c->Vh, n, rhat->ref(1), v->ref(1), c->partials, red_rv, c->stream));
       LQ_CU(bi_scalar(BI_ALPHA, b.ds, red_rv, n, c->stream));
       LQ_CU(bi_s(L, c->Vh, n, sv->mut(1), r->ref(1), v->ref(1), b.ds, c->stream));
-      LQ_TRY(op_mhat(c, L, rec, 0, n, t->mut(1), sv->ref(1), ye->mut(0), kNone, 0.0, nullptr, 0));
+      LQ_TRY(op_eo(W, L, rec, 0, t->mut(1), sv->ref(1), ye, nullptr, 0));
       LQ_CU(bi_dot3(L, c->Vh, n, t->ref(1), sv->ref(1), c->partials, red_ts, c->stream));
       LQ_CU(bi_scalar(BI_OMEGA, b.ds, red_ts, n, c->stream));
       LQ_CU(bi_xr(px, L, c->Vh, n, x->mut(1), p->ref(1), sv->ref(1), t->ref(1), r->mut(1), rhat->ref(1), b.ds,
@@ -787,6 +804,8 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
   if ((int)prm->inner < 0 || (int)prm->inner > 4) return set_error(LQCD_ERR_ARG, "bad inner precision");
   if (prm->solver != LQCD_SOLVER_CGLS && prm->solver != LQCD_SOLVER_BICGSTAB)
     return set_error(LQCD_ERR_ARG, "bad solver %d", prm->solver);
+  if (prm->schur != LQCD_SCHUR_ASYM && prm->schur != LQCD_SCHUR_SYM)
+    return set_error(LQCD_ERR_ARG, "bad schur %d", prm->schur);
   if (prm->outer != LQCD_F64 && prm->outer != LQCD_DF64)
     return set_error(LQCD_ERR_ARG, "outer precision must be LQCD_F64 or LQCD_DF64");
   if (!plain_cg(prm) && !(prm->delta > 0.0 && prm->delta < 1.0))
@@ -860,6 +879,13 @@ lqcd_status job_prepare(SolveJob &J) {
   // check often with 16-bit storage: its inner solves can turn round quickly
   W.check_every = prm->check_every > 0 ? prm->check_every : (prec_half(prm->inner) ? 4 : 8);
   W.info = inf;
+  // the two Schur forms coincide without a clover term
+  W.schur = c->clover_on ? prm->schur : LQCD_SCHUR_ASYM;
+  W.rscale = W.schur == LQCD_SCHUR_SYM ? std::max(1.0, c->a_bound[1]) : 1.0;
+  if (W.schur == LQCD_SCHUR_SYM) {
+    LQ_TRY(temp_field(c, W.hp, LQCD_ODD, n, 40, &W.t_hp));
+    if (W.lo != W.hp) LQ_TRY(temp_field(c, W.lo, LQCD_ODD, n, 41, &W.t_lo));
+  }
   W.bnorm.assign(n, 0.0);
   {
     std::vector<double> e(n), o(n);

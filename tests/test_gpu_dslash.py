@@ -59,10 +59,14 @@ def _oracle_op(op, dims, U, A, Ai, psi, tbc=1):
         return oracle.apply_Mhat(dims, U, A, Ai, KAPPA, t, tbc, dagger=True)
     if op == "HW":
         return oracle.apply_HW(dims, U, RHO, psi, tbc)
+    if op == "MHAT_SYM":
+        return oracle.apply_Mhat_sym(dims, U, A, Ai, KAPPA, o(psi), tbc)
+    if op == "MHAT_SYM_DAG":
+        return oracle.apply_Mhat_sym(dims, U, A, Ai, KAPPA, o(psi), tbc, dagger=True)
     raise ValueError(op)
 
 
-OPS = ["HOP_EO", "HOP_OE", "K2A", "M", "M_DAG", "MHAT", "MHAT_DAG", "MHAT_NORMAL", "HW"]
+OPS = ["HOP_EO", "HOP_OE", "K2A", "M", "M_DAG", "MHAT", "MHAT_DAG", "MHAT_NORMAL", "HW", "MHAT_SYM", "MHAT_SYM_DAG"]
 # (8,6,4,10): 960 sites per parity = 7.5 blocks of 128 threads (ragged tail)
 DIMS = (8, 6, 4, 10)
 
@@ -85,7 +89,7 @@ def test_ops_clover(clover_lattice, op, prec, recon):
     assert rel(out, expect) < TOL[prec], f"{op} {prec} r{recon}"
 
 
-@pytest.mark.parametrize("op", ["K2A", "MHAT", "MHAT_DAG", "M"])
+@pytest.mark.parametrize("op", ["K2A", "MHAT", "MHAT_DAG", "M", "MHAT_SYM_DAG"])
 @pytest.mark.parametrize("prec", ["f64", "df64", "f32", "bf16"])
 def test_ops_wilson(lib, op, prec):
     dims = (4, 4, 6, 8)
@@ -105,6 +109,16 @@ def test_multi_rhs(clover_lattice, nrhs, prec):
     out = lat.dslash(psi, "MHAT", prec, 18 if prec == "df64" else 12)
     for k in range(nrhs):
         assert rel(out[k], _oracle_op("MHAT", DIMS, U, A, Ai, psi[k])) < TOL[prec]
+
+
+@pytest.mark.parametrize("op", ["MHAT_SYM", "MHAT_SYM_DAG"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_multi_rhs_symmetric_schur(clover_lattice, op, prec):
+    lat, U, A, Ai = clover_lattice
+    psi = gen.gaussian_spinor(DIMS, 3001, nrhs=4)
+    out = lat.dslash(psi, op, prec, 18 if prec == "f64" else 12)
+    for k in range(4):
+        assert rel(out[k], _oracle_op(op, DIMS, U, A, Ai, psi[k])) < TOL[prec]
 
 
 def test_periodic_time_and_2x4(lib):

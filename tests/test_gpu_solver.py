@@ -105,6 +105,9 @@ def test_solver_rejects_bad_outer(lib):
     with pytest.raises(lib.LqcdError) as e:
         lat.solve(b, inner="f32", outer="f32")
     assert e.value.status == lib.LQCD_ERR_ARG
+    with pytest.raises(lib.LqcdError) as e:
+        lat.solve(b, inner="f32", schur=2)
+    assert e.value.status == lib.LQCD_ERR_ARG
     lat.close()
 
 
@@ -157,11 +160,11 @@ def test_noconv_reports(lib):
     lat.close()
 
 
-@pytest.mark.parametrize("outer", ["f64", "df64"])
-def test_batch_of_uneven_lattices(lib, outer):
+@pytest.mark.parametrize("outer,schur", [("f64", "asym"), ("df64", "asym"), ("f64", "sym")])
+def test_batch_of_uneven_lattices(lib, outer, schur):
     """Three lattices of different volumes in one graph-captured batch: each
     reaches 1e-10 (oracle) and equals the single-lattice solve bitwise, with
-    FP64 or DF64 reliable updates."""
+    FP64 or DF64 reliable updates, on either Schur form."""
     L = lib
     dims_list = [(4, 4, 4, 8), (6, 4, 4, 8), (8, 4, 6, 4)]
     kappa, csw = 0.125, 1.0
@@ -175,7 +178,7 @@ def test_batch_of_uneven_lattices(lib, outer):
         Us.append(U)
         bs.append(np.ascontiguousarray(gen.gaussian_spinor(dims, 4000 + j, nrhs=2)))
     xs = [np.zeros_like(b) for b in bs]
-    prm = L.solve_params(tol=1e-10, inner=L.LQCD_F16, nrhs=2, check_every=8, outer=L.PREC[outer])
+    prm = L.solve_params(tol=1e-10, inner=L.LQCD_F16, nrhs=2, check_every=8, outer=L.PREC[outer], schur=schur)
     st, infos = L.lqcd_solve_batch([l.ctx for l in lats], xs, bs, prm)
     assert st == L.LQCD_OK
     for j, dims in enumerate(dims_list):
@@ -259,4 +262,36 @@ def test_bicgstab_initial_guess(lib):
     assert info.iters < cold.iters
     A = oracle.clover(dims, U, kappa, csw)
     assert oracle.true_residual(dims, U, A, kappa, x, b) <= 1e-10
+    lat.close()
+
+
+@pytest.mark.parametrize("solver,inner,outer,nrhs", [("cgls", "f64", "f64", 1), ("cgls", "df64", "df64", 1),
+                                                     ("cgls", "f32", "f64", 2), ("cgls", "f16", "f64", 1),
+                                                     ("cgls", "f16", "df64", 1), ("bicgstab", "f64", "f64", 1),
+                                                     ("bicgstab", "f16", "f64", 2)])
+def test_symmetric_schur_solves(lib, solver, inner, outer, nrhs):
+    """Solves on the symmetric Schur complement A_oo^-1 Mhat reach the 1e-10
+    true residual of M x = b (recomputed by the oracle), although the recursion
+    only sees A_oo^-1 times that residual, and give the asymmetric form's
+    solution; on this rough field (eps = 1, c_sw = 2) the plain CGLS needs
+    fewer iterations on the better-conditioned operator."""
+    dims = (8, 8, 8, 8)
+    kappa, csw = 0.14, 2.0
+    U = gen.gauge_field(dims, 1.0, 1010)
+    b = gen.gaussian_spinor(dims, 2010, nrhs=nrhs)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    kw = dict(tol=1e-10, inner=inner, outer=outer, recon=18, inner_recon=12, solver=solver, max_iter=20000)
+    xs, st, info = lat.solve(b, schur="sym", **kw)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(nrhs):
+        assert oracle.true_residual(dims, U, A, kappa, xs[k], b[k]) <= 1e-10
+        assert info.true_resid[k] <= 1e-10
+    xa, sta, infa = lat.solve(b, schur="asym", **kw)
+    assert sta == lib.LQCD_OK
+    assert rel(xs, xa) < 1e-8
+    if solver == "cgls" and inner == "f64":
+        assert info.iters < infa.iters
     lat.close()
