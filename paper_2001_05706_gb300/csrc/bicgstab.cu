@@ -27,9 +27,12 @@ __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
 }
 template <typename T> __device__ __forceinline__ cx<T> zc(double2 z) { return mk<T>((T)z.x, (T)z.y); }
 
-// conj(a) . b and |a|^2 of one site in the arithmetic type, returned as doubles
+// conj(a) . b and |a|^2 of one site in the arithmetic type, returned as
+// reduction values (double for FP64, double-float otherwise)
 template <typename T>
-__device__ __forceinline__ void site_dot3(const cx<T> (&a)[4][3], const cx<T> (&b)[4][3], double (&o)[3]) {
+__device__ __forceinline__ void site_dot3(const cx<T> (&a)[4][3], const cx<T> (&b)[4][3],
+                                          typename RedVal<T>::type (&o)[3]) {
+  using RT = typename RedVal<T>::type;
   T re = (T)0, im = (T)0, nn = (T)0;
 #pragma unroll
   for (int sp = 0; sp < 4; sp++)
@@ -39,9 +42,9 @@ __device__ __forceinline__ void site_dot3(const cx<T> (&a)[4][3], const cx<T> (&
       im = fma(a[sp][c].r, b[sp][c].i, fma(-a[sp][c].i, b[sp][c].r, im));
       nn = fma(a[sp][c].r, a[sp][c].r, fma(a[sp][c].i, a[sp][c].i, nn));
     }
-  o[0] = (double)re;
-  o[1] = (double)im;
-  o[2] = (double)nn;
+  o[0] = RT(re);
+  o[1] = RT(im);
+  o[2] = RT(nn);
 }
 
 __global__ void bi_scalar_kernel(int which, BiScalars *s, const double *red, int n) {
@@ -109,7 +112,8 @@ __global__ void __launch_bounds__(kBiThreads) bi_dot3_kernel(long Vh, FieldRef a
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  double o[3] = {0.0, 0.0, 0.0};
+  using RT = typename RedVal<T>::type;
+  RT o[3] = {RT(0), RT(0), RT(0)};
   if (h < Vh) {
     cx<T> av[4][3], bv[4][3];
     load_spinor<S>(a, Vh, k, h, av);
@@ -128,7 +132,8 @@ __global__ void __launch_bounds__(kBiThreads) bi_xr_kernel(long Vh, MutField x, 
   using TX = typename Math<SX>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  double o[3] = {0.0, 0.0, 0.0};
+  using RT = typename RedVal<T>::type;
+  RT o[3] = {RT(0), RT(0), RT(0)};
   if (h < Vh && s[k].active != 0.0) {
     const cx<TX> al = zc<TX>(s[k].alpha), om = zc<TX>(s[k].omega);
     const cx<T> omt = zc<T>(s[k].omega);
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(kBiThreads) bi_xr_kernel(long Vh, MutField x, 
     // (rhat, r) and |r|^2 from the values in registers: r must not be read back
     // through the read-only path in the kernel that writes it
     load_spinor<S>(rhat, Vh, k, h, rh);
-    double d[3], n2[3];
+    RT d[3], n2[3];
     site_dot3<T>(rh, ss, d);
     site_dot3<T>(ss, ss, n2);
     o[0] = d[0];

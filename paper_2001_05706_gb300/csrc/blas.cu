@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x
   using TX = typename Math<SX>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  double nrm[1] = {0.0};
+  typename RedVal<TV>::type nrm[1] = {0};
   const SolverScalars s = sc[k];
   const bool on = s.active != 0.0 && s.qq > 0.0;
   const double alpha = on ? s.gamma[cur] / s.qq : 0.0;
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(long Vh, MutField x
       }
     store_spinor<SX>(x.data, x.scale, x.rhs_words, Vh, k, h, xv);
     store_spinor<SV>(r.data, r.scale, r.rhs_words, Vh, k, h, rv);
-    nrm[0] = site_norm2<TV>(rv);
+    nrm[0] = typename RedVal<TV>::type(site_norm2_t<TV>(rv));
   }
   // an inactive right-hand side reduces zeros: its rr reads 0 from then on
   block_partials<1>(nrm, partials, k);
@@ -76,11 +76,11 @@ __global__ void __launch_bounds__(kBlasThreads) norm2_kernel(long Vh, FieldRef v
   using T = typename Math<S>::T;
   const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  double nrm[1] = {0.0};
+  typename RedVal<T>::type nrm[1] = {0};
   if (h < Vh) {
     cx<T> a[4][3];
     load_spinor<S>(v, Vh, k, h, a);
-    nrm[0] = site_norm2<T>(a);
+    nrm[0] = typename RedVal<T>::type(site_norm2_t<T>(a));
   }
   block_partials<1>(nrm, partials, k);
 }

@@ -132,7 +132,7 @@ template <typename T> __device__ __forceinline__ cx<T> times_i(cx<T> a) { return
 // double; sums over sites are FP64.  GB300 executes FP64 at 1/64 of its FP32
 // rate, so a per-site FP64 sum would make the norms fused into the FP32 and
 // half-precision kernels FP64-bound.
-template <typename T> __device__ __forceinline__ double site_norm2(const cx<T> (&a)[4][3]) {
+template <typename T> __device__ __forceinline__ T site_norm2_t(const cx<T> (&a)[4][3]) {
   T s = (T)0;
 #pragma unroll
   for (int sp = 0; sp < 4; sp++)
@@ -141,7 +141,10 @@ template <typename T> __device__ __forceinline__ double site_norm2(const cx<T> (
       s = fma(a[sp][c].r, a[sp][c].r, s);
       s = fma(a[sp][c].i, a[sp][c].i, s);
     }
-  return (double)s;
+  return s;
+}
+template <typename T> __device__ __forceinline__ double site_norm2(const cx<T> (&a)[4][3]) {
+  return (double)site_norm2_t<T>(a);
 }
 
 // arithmetic type of a binary operation between fields of compute types A, B:

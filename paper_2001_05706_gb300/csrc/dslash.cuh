@@ -669,9 +669,10 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, 
   const int rg = blockIdx.y;  // right-hand-side group
   const bool valid = h < P.h1;
   const int p = P.out_parity;
-  double nrm[NR];
+  using RT = typename RedVal<T>::type;
+  RT nrm[NR];
 #pragma unroll
-  for (int r = 0; r < NR; r++) nrm[r] = 0.0;
+  for (int r = 0; r < NR; r++) nrm[r] = RT(0);
 
   if (valid) {
     cx<T> acc[NR][4][3];
@@ -795,7 +796,7 @@ __global__ void __launch_bounds__(LaunchCfg<S, NR, MODE>::threads, LaunchCfg<S, 
 #pragma unroll
     for (int r = 0; r < NR; r++) {
       store_spinor<S>(P.out, P.out_scale, out_words, P.g.Vh, rg * NR + r, h, acc[r]);
-      if (P.norm_partials) nrm[r] = site_norm2<T>(acc[r]);
+      if (P.norm_partials) nrm[r] = RT(site_norm2_t<T>(acc[r]));
     }
   }
   if (P.norm_partials) block_partials<NR>(nrm, P.norm_partials, rg * NR);

@@ -17,6 +17,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// The per-thread value a kernel reduces: FP64 kernels reduce doubles; kernels
+// computing in FP32 (FP32, FP16/BF16 storage) or in double-float reduce
+// double-float pairs.  GB300 adds doubles at 1/64 of its FP32 rate, so the
+// five FP64 shuffle-adds per site and quantity of a double tree cost more than
+// the streaming of an FP16 field (a three-quantity dot product ran at 37 % of
+// HBM bandwidth); a double-float add is ~11 FP32 operations, exact up to
+// 2^-44 of the operands, and the tree order is unchanged (deterministic).
+template <typename T> struct RedVal { using type = df; };
+template <> struct RedVal<double> { using type = double; };
+
+__device__ __forceinline__ df warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df w(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    v = v + w;
+  }
+  return v;
+}
+
 // Reduce NV values per thread over the blocks of one grid row.  Block
 // (x, y) contributes to quantities kbase .. kbase+NV-1 (callers use
 // kbase = y * NV, so the rows of a 2-D grid hold different quantities);
@@ -87,6 +106,28 @@ __device__ __forceinline__ void block_partials(const double (&v)[NV], double *pa
       double s = lane < nwarp ? sh[k][lane] : 0.0;
       s = warp_sum(s);
       if (lane == 0) partials[(long)(kbase + k) * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// The same with double-float values: both tree levels in double-float, one
+// double per block and quantity written
+template <int NV>
+__device__ __forceinline__ void block_partials(const df (&v)[NV], double *partials, int kbase) {
+  __shared__ float2 shf[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const df s = warp_sum(v[k]);
+    if (lane == 0) shf[k][warp] = make_float2(s.hi, s.lo);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      df s = lane < nwarp ? df(shf[k][lane].x, shf[k][lane].y) : df(0.0f, 0.0f);
+      s = warp_sum(s);
+      if (lane == 0) partials[(long)(kbase + k) * gridDim.x + blockIdx.x] = (double)s.hi + (double)s.lo;
     }
   }
 }
