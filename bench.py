@@ -12,6 +12,7 @@ spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
                   [--no-solve] [--no-batch] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
+                  [--solver-iteration]
   python bench.py --overlap [--high df64]   (overlap set-up and 12-RHS solve on 16^3x32)
   python bench.py --solve-lattice 48,48,48,96   (mixed vs FP64 solve only, on that lattice)
 
@@ -304,6 +305,35 @@ def kernel_only(args):
         for f in (fx, fy, fz):
             L.lqcd_field_destroy(f)
     print(json.dumps({"kernel_only": args.kernel_only, "lattice": list(dims), "launches": args.steps + args.warmup}))
+    return 0
+
+
+def solver_iteration(args):
+    """One inner iteration of each solver on the benchmark lattice, run
+    eagerly (max_iter = 1 stops before the graph-captured loop), twice: the
+    first pass fills the autotuner, the second shows one iteration's kernels
+    in a launch list.  CGLS and BiCGStab with the 12 point sources, CGLS on
+    one Gaussian RHS in both Schur forms; FP16 inner, DF64 updates."""
+    import torch
+    import gen
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(0)
+    U = gen.gauge_field(DIMS, EPS, GAUGE_SEED)
+    b12 = torch.from_numpy(gen.point_sources(DIMS).view(np.float64).reshape(-1).copy()).cuda()
+    b1 = torch.from_numpy(gen.gaussian_spinor(DIMS, 2003)[0].view(np.float64).reshape(-1).copy()).cuda()
+    out = []
+    with L.Lattice(DIMS, stream=torch.cuda.current_stream()) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(KAPPA, CSW)
+        for rep in range(2):
+            for tag, b, n, solver, schur in (("cgls_12rhs", b12, 12, "cgls", "asym"),
+                                             ("bicgstab_12rhs", b12, 12, "bicgstab", "asym"),
+                                             ("cgls_1rhs", b1, 1, "cgls", "asym"), ("cgls_1rhs_sym", b1, 1, "cgls", "sym")):
+                prm = L.solve_params(tol=1e-10, max_iter=1, inner=L.LQCD_F16, outer=L.LQCD_DF64, nrhs=n, recon=18,
+                                     inner_recon=12, check_every=1, solver=solver, schur=schur)
+                st, info = L.lqcd_solve(lat.ctx, torch.zeros_like(b), b, prm, raise_on_noconv=False)
+                out.append({"pass": rep, "solve": tag, "iters": info.iters})
+    print(json.dumps({"solver_iteration": out}))
     return 0
 
 
@@ -722,6 +752,8 @@ def main():
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--recon", type=int, default=12)
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--solver-iteration", action="store_true",
+                    help="one eager inner iteration of each solver, twice (for a launch list)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -732,6 +764,8 @@ def main():
         return run_reference(args, rank)
     if args.kernel_only:
         return kernel_only(args)
+    if args.solver_iteration:
+        return solver_iteration(args) if rank == 0 else 0
     if args.overlap:
         return run_overlap(args) if rank == 0 else 0
     if args.solve_lattice:

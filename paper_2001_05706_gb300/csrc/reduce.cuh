@@ -1,11 +1,13 @@
-// Deterministic FP64 grid reductions without floating-point atomics.
+// Deterministic grid reductions without floating-point atomics.
 //
-// Each block reduces its threads' values with a fixed shuffle tree and
-// writes one partial per reduced quantity; the block that finishes last
-// (found with an integer atomic counter) adds the partials in a fixed order
-// and writes the result.  Same grid, same inputs: bitwise-identical result,
-// independent of block scheduling.  The counter is reset by that last block,
-// so a launch sequence can be replayed (or captured in a CUDA graph).
+// Each block reduces its threads' values with a fixed shuffle tree (FP64 for
+// FP64 kernels, double-float for the others) and writes one FP64 partial per
+// reduced quantity.  The partials are summed in a fixed order either by a
+// separate launch (block_partials + finish_reduce, the solver path) or by the
+// block that finishes last, found with an integer atomic counter that it
+// resets (grid_reduce, for small one-off reductions).  Same grid, same
+// inputs: bitwise-identical result, independent of block scheduling, and a
+// launch sequence can be replayed or captured in a CUDA graph.
 #pragma once
 #include "common.cuh"
 
