@@ -13,7 +13,7 @@ spinor for K2b) -- 864 + 960 bytes per site in FP32 with 12-real links.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
                   [--no-solve] [--no-batch] [--kernel-only k2a|k2b|mhat --lattice X,Y,Z,T]
                   [--solver-iteration]
-  python bench.py --overlap [--high df64]   (overlap set-up and 12-RHS solve on 16^3x32)
+  python bench.py --overlap [--high df64] [--eig lanczos]   (overlap set-up and 12-RHS solve on 16^3x32)
   python bench.py --solve-lattice 48,48,48,96   (mixed vs FP64 solve only, on that lattice)
 
 --impl reference times the FP64 CPU oracle on the same workload (bounded
@@ -546,18 +546,20 @@ def run_overlap(args):
     dims = (16, 16, 16, 32)
     U = gen.gauge_field(dims, 0.1, 1005)
     b = gen.gaussian_spinor(dims, 2005, nrhs=12)
-    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "high": args.high, "config": {
+    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "high": args.high,
+           "eig_method": args.eig, "config": {
         "workload": "overlap D_ov(m) = rho[1 + g5 sign(H_W)] + ..., 16^3x32, eps 0.1, rho 1.5, m 0.05, 20 low modes, "
                     "sign to 1e-10 (FP32 sign inside the CG to 1e-6), 12 Gaussian RHS, CG on the normal "
                     "equations with FP64 (or DF64) reliable updates every two decades (delta 0.01)"}}
     with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
         lat.load_gauge(U.view(np.float64))
         prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400,
-                               high=args.high)
+                               high=args.high, eig_method=args.eig)
         t0 = time.perf_counter()
         st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
         out["setup"] = {"seconds": time.perf_counter() - t0, "status": "ok" if st == 0 else L.lqcd_last_error(),
-                        "sweeps": info.sweeps, "degree": info.degree, "degree_inner_fp32": info.degree_inner,
+                        "sweeps_or_restarts": info.sweeps, "hw_applications": info.hw_applies,
+                        "degree": info.degree, "degree_inner_fp32": info.degree_inner,
                         "a": info.a, "b": info.b,
                         "sign_error": info.sign_error, "max_eig_resid": max(info.resid[:20]),
                         "lambda_min_max": [min(abs(v) for v in info.lambda_[:20]),
@@ -747,6 +749,8 @@ def main():
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
                     help="--overlap: arithmetic of the FP64 parts (FP64 or double-float)")
+    ap.add_argument("--eig", default="subspace", choices=["subspace", "lanczos"],
+                    help="--overlap: low-mode solver (block subspace iteration or thick-restart Lanczos)")
     ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="f32")

@@ -295,7 +295,13 @@ typedef struct {
                      /* FP32, the FP64 sign function and so D_ov, its CG and the mixed   */
                      /* CG's reliable updates): LQCD_F64 (0, the default) or LQCD_DF64;  */
                      /* fields, projections and Gram matrices stay FP64 either way       */
+  int eig_method;    /* low-mode solver on H_W^2: LQCD_EIG_SUBSPACE (0, the default:      */
+                     /* block subspace iteration with a Chebyshev filter; max_filter caps */
+                     /* its sweeps) or LQCD_EIG_LANCZOS (thick-restart Lanczos, one      */
+                     /* vector at a time; max_filter caps its restarts)                 */
 } lqcd_overlap_params;
+
+typedef enum { LQCD_EIG_SUBSPACE = 0, LQCD_EIG_LANCZOS = 1 } lqcd_eig_method;
 
 typedef struct {
   int n_low;              /* low modes found                                           */
@@ -304,11 +310,12 @@ typedef struct {
   double a, b;            /* interval of the Chebyshev interpolant (in H_W^2)          */
   int degree;             /* its degree                                                */
   double sign_error;      /* its sup error on [sqrt a, sqrt b]                         */
-  int sweeps;             /* subspace-iteration sweeps used                            */
+  int sweeps;             /* subspace-iteration sweeps (Lanczos: restart cycles) used  */
   double seconds;         /* wall time of the set-up                                   */
   int degree_inner;       /* degree of the FP32 sign function inside the mixed CG: the */
                           /* smallest reaching max(sign_tol, 1e-6), the FP32 rounding */
                           /* level (reliable updates use the full degree)             */
+  double hw_applies;      /* H_W applications (one per vector) of the low-mode solver */
 } lqcd_overlap_info;
 
 typedef enum {

@@ -53,14 +53,15 @@ class lqcd_solve_params(ctypes.Structure):
 class lqcd_overlap_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("mass", ctypes.c_double), ("n_low", ctypes.c_int),
                 ("max_degree", ctypes.c_int), ("sign_tol", ctypes.c_double), ("eig_tol", ctypes.c_double),
-                ("max_filter", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("high", ctypes.c_int)]
+                ("max_filter", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("high", ctypes.c_int),
+                ("eig_method", ctypes.c_int)]
 
 
 class lqcd_overlap_info(ctypes.Structure):
     _fields_ = [("n_low", ctypes.c_int), ("lambda_", ctypes.c_double * 64), ("resid", ctypes.c_double * 64),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("degree", ctypes.c_int),
                 ("sign_error", ctypes.c_double), ("sweeps", ctypes.c_int), ("seconds", ctypes.c_double),
-                ("degree_inner", ctypes.c_int)]
+                ("degree_inner", ctypes.c_int), ("hw_applies", ctypes.c_double)]
 
 
 LQCD_OV_APPLY, LQCD_OV_APPLY_DAG, LQCD_OV_SIGN, LQCD_OV_SOLVE = 0, 1, 2, 3
@@ -263,11 +264,17 @@ def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):
     _check(_lib.lqcd_norm2_noalloc(px, int(n), int(nrhs), pr, _stream_ptr(stream)))
 
 
+LQCD_EIG_SUBSPACE, LQCD_EIG_LANCZOS = 0, 1
+EIG_METHODS = {"subspace": LQCD_EIG_SUBSPACE, "lanczos": LQCD_EIG_LANCZOS}
+
+
 def overlap_params(rho=1.5, mass=0.0, n_low=20, max_degree=4000, sign_tol=1e-10, eig_tol=1e-11, max_filter=200,
-                   seed=7, high=LQCD_F64):
+                   seed=7, high=LQCD_F64, eig_method=LQCD_EIG_SUBSPACE):
     if isinstance(high, str):
         high = PREC[high]
-    return lqcd_overlap_params(rho, mass, n_low, max_degree, sign_tol, eig_tol, max_filter, seed, high)
+    if isinstance(eig_method, str):
+        eig_method = EIG_METHODS[eig_method]
+    return lqcd_overlap_params(rho, mass, n_low, max_degree, sign_tol, eig_tol, max_filter, seed, high, eig_method)
 
 
 def lqcd_overlap_setup(ctx, params, raise_on_noconv=True):

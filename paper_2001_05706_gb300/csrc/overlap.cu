@@ -74,6 +74,10 @@ constexpr double kInnerSignTol = 1e-6;
 // sweeps): m = 40: 214 sweeps, 84 s; m = 60: 191 sweeps, 114 s; m = 96: 143
 // sweeps, 163 s -- a wider block widens the damped gap, but not by enough to
 // pay for its cost per sweep.
+// Lanczos basis size (thick restart keeps the block size m of vectors)
+#ifndef LQCD_OV_LANCZOS_MMAX
+#define LQCD_OV_LANCZOS_MMAX 128
+#endif
 #ifndef LQCD_OV_BLOCK_MULT
 #define LQCD_OV_BLOCK_MULT 2
 #endif
@@ -911,6 +915,168 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
 
 using namespace lqcd;
 
+namespace lqcd {
+namespace {
+
+// ---- thick-restart Lanczos on H_W^2 -------------------------------------------
+// The smallest eigenpairs of H_W^2 by the thick-restart Lanczos method (Wu and
+// Simon, SIAM J. Matrix Anal. Appl. 22 (2000) 602).  A Lanczos basis V of up
+// to mmax vectors is built one vector at a time, each new H_W^2 v_j made
+// orthogonal to all of V by two passes of classical Gram-Schmidt (so the
+// projected matrix is the Gram coefficients, tridiagonal up to rounding).
+// At a restart the kkeep smallest Ritz vectors and the last Lanczos vector
+// v_m are kept: H_W^2 V_k = V_k diag(theta) + beta_m v_m e_m^T Y_k, so the
+// new projected matrix is diag(theta) bordered by beta_m Y_{m-1,i} (an
+// arrowhead) and the recursion continues from v_m.  The residual of Ritz
+// pair i is beta_m |Y_{m-1,i}|.  Against block subspace iteration with a
+// fixed Chebyshev filter this adapts its polynomial to the spectrum and
+// applies H_W^2 to one vector per step instead of a whole block per filter
+// degree.  H_W^2 runs in FP64 or double-float; the basis, the Gram
+// coefficients and the rotations are FP64 (cuBLAS ZGEMM).
+struct LanczosResult {
+  int kneed = 0, cycles = 0;
+  long applies = 0;
+  bool converged = false;
+};
+
+// dst column kd = src column ks (same precision)
+lqcd_status copy_col(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src, int ks) {
+  const size_t bytes = (size_t)cwords(src) * celem(src);
+  for (int p = 0; p < 2; p++)
+    LQ_CU(cudaMemcpyAsync(static_cast<char *>(dst->data[p]) + bytes * kd,
+                          static_cast<const char *>(src->data[p]) + bytes * ks, bytes, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  return LQCD_OK;
+}
+
+// X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors of H_W^2
+lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int want, int kkeep, int mmax,
+                             lqcd_field *X, FieldGuard &g, LanczosResult &out) {
+  OverlapState &S = *c->ov;
+  lqcd_field *V, *V2, *w, *t1, *xd = nullptr, *td = nullptr, *wd = nullptr;
+  LQ_TRY(new_full(c, mmax + 1, &V));
+  g.f.push_back(V);
+  LQ_TRY(new_full(c, mmax + 1, &V2));
+  g.f.push_back(V2);
+  LQ_TRY(new_full(c, 1, &w));
+  g.f.push_back(w);
+  LQ_TRY(new_full(c, 1, &t1));
+  g.f.push_back(t1);
+  if (S.df) {
+    for (lqcd_field **f : {&xd, &td, &wd}) {
+      LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, 1, f));
+      g.f.push_back(*f);
+    }
+  }
+  // random unit start vector
+  {
+    const long nd = 2L * cwords(w);
+    for (int p = 0; p < 2; p++) {
+      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)w->data[p], nd,
+                                                                                   prm->seed * 2 + p + 1);
+      LQ_CU(cudaGetLastError());
+    }
+    std::vector<double> n2;
+    LQ_TRY(field_norms(c, w, 1, n2));
+    LQ_TRY(scale_full(c, w, w, {1.0 / std::sqrt(n2[0])}, 1));
+    LQ_TRY(copy_col(c, V, 0, w, 0));
+  }
+  const int ld = mmax + 1;
+  std::vector<zc> Hm((size_t)ld * mmax, zc(0, 0));
+  double2 *d;
+  LQ_TRY(small_scratch(c, (size_t)(mmax + 1) * mmax, &d));
+  int j0 = 0;
+  std::vector<zc> h, h2;
+  for (;;) {
+    for (int j = j0; j < mmax; j++) {
+      // w = H_W^2 v_j
+      LQ_TRY(copy_col(c, w, 0, V, j));
+      if (S.df) {
+        LQ_TRY(convert_full(c, xd, w, 1));
+        LQ_TRY(hw(c, 1, td, xd));
+        LQ_TRY(hw(c, 1, wd, td));
+        LQ_TRY(convert_full(c, w, wd, 1));
+      } else {
+        LQ_TRY(hw(c, 1, t1, w));
+        LQ_TRY(hw(c, 1, w, t1));
+      }
+      out.applies += 2;
+      // two passes of classical Gram-Schmidt against v_0 .. v_j
+      h.assign(j + 1, zc(0, 0));
+      for (int pass = 0; pass < 2; pass++) {
+        LQ_TRY(gram(c, V, j + 1, w, 1, d));
+        LQ_TRY(rotate(c, V, j + 1, d, 1, w, -1.0, 1.0));
+        LQ_TRY(to_host(c, d, (size_t)(j + 1), h2));
+        for (int i = 0; i <= j; i++) h[i] += h2[i];
+      }
+      std::vector<double> n2;
+      LQ_TRY(field_norms(c, w, 1, n2));
+      const double beta = std::sqrt(n2[0]);
+      if (!(beta > 1e-13)) return set_error(LQCD_ERR_NOCONV, "Lanczos breakdown at step %d (beta %.3e)", j, beta);
+      for (int i = 0; i <= j; i++) Hm[i + (size_t)ld * j] = h[i];
+      Hm[j + 1 + (size_t)ld * j] = beta;
+      LQ_TRY(scale_full(c, w, w, {1.0 / beta}, 1));
+      LQ_TRY(copy_col(c, V, j + 1, w, 0));
+    }
+    out.cycles++;
+    // Ritz pairs of the (Hermitian part of the) mmax x mmax projected matrix
+    const int m = mmax;
+    std::vector<zc> W((size_t)m * m), Q;
+    for (int jj = 0; jj < m; jj++)
+      for (int i = 0; i < m; i++) W[i + (size_t)m * jj] = Hm[i + (size_t)ld * jj];
+    for (int jj = 0; jj < m; jj++)
+      for (int i = 0; i < jj; i++) {
+        const zc avg = 0.5 * (W[i + (size_t)m * jj] + std::conj(W[jj + (size_t)m * i]));
+        W[i + (size_t)m * jj] = avg;
+        W[jj + (size_t)m * i] = std::conj(avg);
+      }
+    std::vector<double> mu;
+    jacobi_eigh(m, W, Q, mu);
+    std::vector<int> order(m);
+    for (int i = 0; i < m; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] < mu[y]; });
+    std::vector<zc> Qs((size_t)m * m);
+    std::vector<double> mus(m);
+    for (int jj = 0; jj < m; jj++) {
+      mus[jj] = mu[order[jj]];
+      for (int i = 0; i < m; i++) Qs[i + (size_t)m * jj] = Q[i + (size_t)m * order[jj]];
+    }
+    const double beta_m = Hm[m + (size_t)ld * (m - 1)].real();
+    int kneed = want;
+    while (kneed < kkeep - 4 && mus[kneed] <= 1.01 * mus[want - 1]) kneed++;
+    bool conv = true;
+    double worst = 0;
+    for (int i = 0; i < kneed; i++) {
+      const double r = beta_m * std::abs(Qs[m - 1 + (size_t)m * i]);
+      worst = std::max(worst, r);
+      conv &= r <= prm->eig_tol;
+    }
+    if (kOvTrace)
+      std::fprintf(stderr, "lqcd overlap: Lanczos cycle %d worst %.3e kneed %d mu[kneed-1] %.6f mu[kkeep-1] %.6f\n",
+                   out.cycles, worst, kneed, mus[kneed - 1], mus[kkeep - 1]);
+    LQ_TRY(to_dev(c, Qs, d));
+    if (conv || out.cycles >= prm->max_filter) {
+      LQ_TRY(rotate(c, V, m, d, kneed, X, 1.0, 0.0));
+      out.kneed = kneed;
+      out.converged = conv;
+      return LQCD_OK;
+    }
+    // thick restart: V2 = [V Q_k, v_m]; projected matrix diag(theta) bordered by beta_m Q_{m-1,i}
+    LQ_TRY(rotate(c, V, m, d, kkeep, V2, 1.0, 0.0));
+    LQ_TRY(copy_col(c, V2, kkeep, V, m));
+    std::swap(V, V2);
+    std::fill(Hm.begin(), Hm.end(), zc(0, 0));
+    for (int i = 0; i < kkeep; i++) {
+      Hm[i + (size_t)ld * i] = mus[i];
+      Hm[kkeep + (size_t)ld * i] = beta_m * Qs[m - 1 + (size_t)m * i];
+    }
+    j0 = kkeep;
+  }
+}
+
+}  // namespace
+}  // namespace lqcd
+
 extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params *prm, lqcd_overlap_info *info) {
   NvtxRange nv("lqcd overlap set-up");
   if (!c || !prm) return set_error(LQCD_ERR_ARG, "NULL argument");
@@ -920,6 +1086,8 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   if (!(prm->sign_tol > 0) || !(prm->eig_tol > 0)) return set_error(LQCD_ERR_ARG, "tolerances must be > 0");
   if (prm->max_degree < 1 || prm->max_filter < 1) return set_error(LQCD_ERR_ARG, "max_degree, max_filter >= 1");
   if (prm->high != LQCD_F64 && prm->high != LQCD_DF64) return set_error(LQCD_ERR_ARG, "high must be LQCD_F64 or LQCD_DF64");
+  if (prm->eig_method != LQCD_EIG_SUBSPACE && prm->eig_method != LQCD_EIG_LANCZOS)
+    return set_error(LQCD_ERR_ARG, "bad eig_method %d", prm->eig_method);
   const auto t0 = std::chrono::steady_clock::now();
   lqcd_overlap_info local{};
   lqcd_overlap_info *inf = info ? info : &local;
@@ -950,6 +1118,23 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   g.f.push_back(Y);
   LQ_TRY(new_full(c, m, &Z));
   g.f.push_back(Z);
+  const double bmax = std::pow(4.0 - prm->rho + 4.0, 2);
+  std::vector<double> theta, resid;
+  std::vector<int> order;
+  double2 *d;
+  int sweep = 0, kneed = want;
+  long applies = 0;  // H_W applications, one per right-hand side
+  bool converged = false;
+  if (prm->eig_method == LQCD_EIG_LANCZOS) {
+    // restart size m (the block of the subspace method), basis of up to 2m
+    const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
+    LanczosResult lr;
+    LQ_TRY(lowmodes_lanczos(c, prm, want, m, mmax, X, g, lr));
+    kneed = lr.kneed;
+    sweep = lr.cycles - 1;
+    applies = lr.applies;
+    converged = lr.converged;
+  } else {
   {
     const long nd = 2L * cwords(X) * m;  // doubles per parity block
     for (int p = 0; p < 2; p++) {
@@ -959,17 +1144,11 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     }
   }
   LQ_TRY(orthonormalise(c, X, T, m));
-  const double bmax = std::pow(4.0 - prm->rho + 4.0, 2);
-  std::vector<double> theta, resid;
-  std::vector<int> order;
-  double2 *d;
-  int sweep = 0, kneed = want;
   bool fp32_phase = true;
   int fp32_stall = 0;
   double prev_worst = 1e300;
   lqcd_field *Bs[4] = {nullptr, nullptr, nullptr, nullptr};  // FP32 filter block
   lqcd_field *Bd[4] = {nullptr, nullptr, nullptr, nullptr};  // double-float filter block
-  bool converged = false;
   for (;; sweep++) {
     // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
     // extremal problem; Rayleigh-Ritz with H_W itself would be an interior one
@@ -1007,6 +1186,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     std::vector<double> neg(m), r2;
     for (int i = 0; i < m; i++) neg[i] = -mus[i];
     LQ_TRY(axpy_norms(c, Z, X, neg, m, r2));
+    applies += 2L * m;
     // converge the wanted vectors and every vector nearly degenerate with the
     // edge of the wanted set (a near-degenerate +-lambda partner left outside
     // would stay mixed into a wanted vector)
@@ -1068,6 +1248,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
       cur = nxt;
       nxt = t;
     }
+    applies += 2L * deg * m;
     if (fp != LQCD_F64) {
       LQ_TRY(convert_full(c, X, cur, m));
     } else if (cur != X) {  // the filtered block becomes X; the other two are scratch
@@ -1082,12 +1263,14 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     }
     LQ_TRY(orthonormalise(c, X, T, m));
   }
+  }
   // Rayleigh-Ritz with H_W in the span of the kneed converged vectors of
   // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors; the
   // `want` of smallest |lambda| are kept
   {
     const int k = kneed;
     LQ_TRY(hw(c, k, HX, X));
+    applies += k;
     LQ_TRY(small_scratch(c, (size_t)k * k, &d));
     LQ_TRY(gram(c, X, k, HX, k, d));
     std::vector<zc> W, Q;
@@ -1114,6 +1297,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     std::sort(order.begin(), order.end(), [&](int x, int y) { return std::fabs(theta[x]) < std::fabs(theta[y]); });
   }
   inf->sweeps = sweep + 1;
+  inf->hw_applies = (double)applies;
   // keep the `want` lowest (by |theta|), sorted
   S.nlow = prm->n_low;
   S.lam.assign(S.nlow, 0.0);

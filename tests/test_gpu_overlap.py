@@ -25,10 +25,11 @@ def lib():
     return L
 
 
-def _setup(L, dims, U, n_low, mass=0.0, sign_tol=1e-12, high="f64"):
+def _setup(L, dims, U, n_low, mass=0.0, sign_tol=1e-12, high="f64", eig_method="subspace", max_filter=200):
     lat = L.Lattice(dims)
     lat.load_gauge(U.view(np.float64))
-    prm = L.overlap_params(rho=RHO, mass=mass, n_low=n_low, sign_tol=sign_tol, eig_tol=1e-11, high=high)
+    prm = L.overlap_params(rho=RHO, mass=mass, n_low=n_low, sign_tol=sign_tol, eig_tol=1e-11, high=high,
+                           eig_method=eig_method, max_filter=max_filter)
     st, info = L.lqcd_overlap_setup(lat.ctx, prm)
     vecs = np.zeros((n_low,) + oracle.spinor_shape(dims), dtype=np.complex128)
     if n_low:
@@ -43,11 +44,12 @@ def _ov(L, lat, psi, op, nrhs=1, cg=None):
     return out
 
 
-@pytest.fixture(scope="module", params=["f64", "df64"])
+@pytest.fixture(scope="module", params=[("f64", "subspace"), ("df64", "subspace"), ("f64", "lanczos"),
+                                        ("df64", "lanczos")])
 def rough(lib, request):
     dims = (4, 4, 4, 4)
     U = gen.gauge_field(dims, 0.3, 23)
-    lat, info, lam, vecs = _setup(lib, dims, U, 8, high=request.param)
+    lat, info, lam, vecs = _setup(lib, dims, U, 8, high=request.param[0], eig_method=request.param[1])
     yield dims, U, lat, info, lam, vecs
     lat.close()
 
@@ -151,6 +153,38 @@ def test_overlap_rejects_bad_high_precision(lib):
     lat = L.Lattice(dims)
     lat.load_gauge(gen.gauge_field(dims, 0.3, 23).view(np.float64))
     prm = L.overlap_params(rho=RHO, n_low=2, high=L.LQCD_F32)
+    with pytest.raises(L.LqcdError) as e:
+        L.lqcd_overlap_setup(lat.ctx, prm)
+    assert e.value.status == L.LQCD_ERR_ARG
+    lat.close()
+
+
+@pytest.mark.parametrize("high", ["f64", "df64"])
+def test_lanczos_matches_subspace_iteration(lib, high):
+    """Thick-restart Lanczos and block subspace iteration find the same 12 low
+    modes of H_W on a smooth 8^4 field (clustered spectrum), each to an
+    eigen-residual below 1e-10 recomputed by the oracle, and Lanczos applies
+    H_W fewer times."""
+    L = lib
+    dims = (8, 8, 8, 8)
+    U = gen.gauge_field(dims, 0.1, 31)
+    res = {}
+    for method in ("subspace", "lanczos"):
+        lat, info, lam, vecs = _setup(L, dims, U, 12, sign_tol=1e-10, high=high, eig_method=method, max_filter=2000)
+        r, ortho = oracle.eigen_residuals(dims, U, RHO, lam, vecs)
+        assert r.max() < 1e-10 and ortho < 1e-10, method
+        res[method] = (np.sort(lam), info.hw_applies, info.sweeps)
+        lat.close()
+    assert np.allclose(res["lanczos"][0], res["subspace"][0], atol=1e-10)
+    assert 0 < res["lanczos"][1] < res["subspace"][1]
+
+
+def test_overlap_rejects_bad_eig_method(lib):
+    L = lib
+    dims = (4, 4, 4, 4)
+    lat = L.Lattice(dims)
+    lat.load_gauge(gen.gauge_field(dims, 0.3, 23).view(np.float64))
+    prm = L.overlap_params(rho=RHO, n_low=2, eig_method=5)
     with pytest.raises(L.LqcdError) as e:
         L.lqcd_overlap_setup(lat.ctx, prm)
     assert e.value.status == L.LQCD_ERR_ARG
