@@ -949,6 +949,33 @@ lqcd_status copy_col(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src
   return LQCD_OK;
 }
 
+// y (device, p complex) = V[:, :p]^H w over both parities (cuBLAS ZGEMV)
+lqcd_status gemv_c(lqcd_ctx *c, const lqcd_field *V, int p, const lqcd_field *w, double2 *y) {
+  OverlapState &s = *c->ov;
+  const int N = (int)cwords(V);
+  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+  for (int par = 0; par < 2; par++)
+    LQ_TRY(blas_ok(cublasZgemv(s.blas, CUBLAS_OP_C, N, p, &one, (const cuDoubleComplex *)col(V, par, 0), N,
+                               (const cuDoubleComplex *)col(w, par, 0), 1, par ? &one : &zero, (cuDoubleComplex *)y, 1),
+                   "ZGEMV (projection)"));
+  return LQCD_OK;
+}
+
+// w -= V[:, :p] y over both parities
+lqcd_status gemv_sub(lqcd_ctx *c, const lqcd_field *V, int p, const double2 *y, lqcd_field *w) {
+  OverlapState &s = *c->ov;
+  const int N = (int)cwords(V);
+  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), mone = make_cuDoubleComplex(-1, 0);
+  for (int par = 0; par < 2; par++)
+    LQ_TRY(blas_ok(cublasZgemv(s.blas, CUBLAS_OP_N, N, p, &mone, (const cuDoubleComplex *)col(V, par, 0), N,
+                               (const cuDoubleComplex *)y, 1, &one, (cuDoubleComplex *)col(w, par, 0), 1),
+                   "ZGEMV (subtraction)"));
+  return LQCD_OK;
+}
+
+// f[0] = 1 / sqrt(n2[0] + n2[1]) (the normalisation of a vector whose parity norms are n2)
+__global__ void inv_norm_kernel(const double *n2, double *f) { f[0] = 1.0 / sqrt(n2[0] + n2[1]); }
+
 // X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors of H_W^2
 lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int want, int kkeep, int mmax,
                              lqcd_field *X, FieldGuard &g, LanczosResult &out) {
@@ -984,9 +1011,23 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
   const int ld = mmax + 1;
   std::vector<zc> Hm((size_t)ld * mmax, zc(0, 0));
   double2 *d;
-  LQ_TRY(small_scratch(c, (size_t)(mmax + 1) * mmax, &d));
+  LQ_TRY(small_scratch(c, (size_t)(mmax + 1) * mmax + 2 * (size_t)(mmax + 1), &d));
+  double2 *dh1 = d + (size_t)(mmax + 1) * mmax, *dh2 = dh1 + (mmax + 1);  // the two Gram-Schmidt passes
+  // pinned host copies of one step's coefficients and norms: one sync per step
+  struct Pinned {
+    double2 *h = nullptr;
+    ~Pinned() {
+      if (h) cudaFreeHost(h);
+    }
+  } hp;
+  if (cudaMallocHost(&hp.h, sizeof(double2) * (2 * (size_t)(mmax + 1) + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ERR_OOM, "cannot allocate Lanczos host scratch");
+  }
+  LQ_TRY(ensure_partials(c, 1));
+  double *dn2 = c->results, *dfac = c->results + 768;
   int j0 = 0;
-  std::vector<zc> h, h2;
+  std::vector<zc> h;
   for (;;) {
     for (int j = j0; j < mmax; j++) {
       // w = H_W^2 v_j
@@ -1001,22 +1042,27 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
         LQ_TRY(hw(c, 1, w, t1));
       }
       out.applies += 2;
-      // two passes of classical Gram-Schmidt against v_0 .. v_j
-      h.assign(j + 1, zc(0, 0));
-      for (int pass = 0; pass < 2; pass++) {
-        LQ_TRY(gram(c, V, j + 1, w, 1, d));
-        LQ_TRY(rotate(c, V, j + 1, d, 1, w, -1.0, 1.0));
-        LQ_TRY(to_host(c, d, (size_t)(j + 1), h2));
-        for (int i = 0; i <= j; i++) h[i] += h2[i];
-      }
-      std::vector<double> n2;
-      LQ_TRY(field_norms(c, w, 1, n2));
-      const double beta = std::sqrt(n2[0]);
-      if (!(beta > 1e-13)) return set_error(LQCD_ERR_NOCONV, "Lanczos breakdown at step %d (beta %.3e)", j, beta);
-      for (int i = 0; i <= j; i++) Hm[i + (size_t)ld * j] = h[i];
-      Hm[j + 1 + (size_t)ld * j] = beta;
-      LQ_TRY(scale_full(c, w, w, {1.0 / beta}, 1));
+      // two passes of classical Gram-Schmidt against v_0 .. v_j, then
+      // v_{j+1} = w / |w|, all on the stream; the host reads the
+      // coefficients and |w|^2 once
+      LQ_TRY(gemv_c(c, V, j + 1, w, dh1));
+      LQ_TRY(gemv_sub(c, V, j + 1, dh1, w));
+      LQ_TRY(gemv_c(c, V, j + 1, w, dh2));
+      LQ_TRY(gemv_sub(c, V, j + 1, dh2, w));
+      for (int p = 0; p < 2; p++) LQ_CU(blas_norm2(LQCD_F64, c->Vh, 1, w->ref(p), c->partials, dn2 + p, 1, c->stream));
+      inv_norm_kernel<<<1, 1, 0, c->stream>>>(dn2, dfac);
+      LQ_CU(cudaGetLastError());
+      for (int p = 0; p < 2; p++) LQ_CU(blas_scale(LQCD_F64, LQCD_F64, c->Vh, 1, w->mut(p), w->ref(p), dfac, c->stream));
       LQ_TRY(copy_col(c, V, j + 1, w, 0));
+      LQ_CU(cudaMemcpyAsync(hp.h, dh1, sizeof(double2) * 2 * (size_t)(mmax + 1), cudaMemcpyDeviceToHost, c->stream));
+      LQ_CU(cudaMemcpyAsync(hp.h + 2 * (size_t)(mmax + 1), dn2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      LQ_CU(cudaStreamSynchronize(c->stream));
+      const double2 nn = hp.h[2 * (size_t)(mmax + 1)];
+      const double beta = std::sqrt(nn.x + nn.y);
+      if (!(beta > 1e-13)) return set_error(LQCD_ERR_NOCONV, "Lanczos breakdown at step %d (beta %.3e)", j, beta);
+      for (int i = 0; i <= j; i++)
+        Hm[i + (size_t)ld * j] = zc(hp.h[i].x + hp.h[mmax + 1 + i].x, hp.h[i].y + hp.h[mmax + 1 + i].y);
+      Hm[j + 1 + (size_t)ld * j] = beta;
     }
     out.cycles++;
     // Ritz pairs of the (Hermitian part of the) mmax x mmax projected matrix
