@@ -298,7 +298,11 @@ typedef struct {
   int eig_method;    /* low-mode solver on H_W^2: LQCD_EIG_SUBSPACE (0, the default:      */
                      /* block subspace iteration with a Chebyshev filter; max_filter caps */
                      /* its sweeps) or LQCD_EIG_LANCZOS (thick-restart Lanczos, one      */
-                     /* vector at a time; max_filter caps its restarts)                 */
+                     /* vector at a time; max_filter caps its restarts).  Lanczos needs */
+                     /* far fewer H_W applications, but a single Krylov vector can reach */
+                     /* a near-degenerate cluster late: on clustered spectra it may stop */
+                     /* with converged pairs above a cluster it has not yet found, which */
+                     /* the block method (40 random start vectors) guards against        */
 } lqcd_overlap_params;
 
 typedef enum { LQCD_EIG_SUBSPACE = 0, LQCD_EIG_LANCZOS = 1 } lqcd_eig_method;
