@@ -949,71 +949,175 @@ lqcd_status copy_col(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src
   return LQCD_OK;
 }
 
-// y (device, p complex) = V[:, :p]^H w over both parities (cuBLAS ZGEMV)
-lqcd_status gemv_c(lqcd_ctx *c, const lqcd_field *V, int p, const lqcd_field *w, double2 *y) {
-  OverlapState &s = *c->ov;
-  const int N = (int)cwords(V);
-  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
-  for (int par = 0; par < 2; par++)
-    LQ_TRY(blas_ok(cublasZgemv(s.blas, CUBLAS_OP_C, N, p, &one, (const cuDoubleComplex *)col(V, par, 0), N,
-                               (const cuDoubleComplex *)col(w, par, 0), 1, par ? &one : &zero, (cuDoubleComplex *)y, 1),
-                   "ZGEMV (projection)"));
-  return LQCD_OK;
+// ---- double-float kernels of the Lanczos Gram-Schmidt ------------------------
+// The basis is a DF64 field: each complex number one float4 {re.hi, re.lo,
+// im.hi, im.lo}, columns of cwords complex numbers per parity.  GB300 runs
+// FP64 multiply-adds at 1/64 of its FP32 rate, which made FP64 projections
+// against the basis (ZGEMV) ~5 ms per Lanczos step; in double-float on the
+// FP32 pipes they are bound by the basis' bytes.  Elements are indexed over
+// both parities: e < n is parity 0, e - n parity 1.
+constexpr int kLzT = 256;
+constexpr int kLzMaxP = 160;  // basis columns a kernel can take (mmax + 1 <= 129)
+
+struct dfc {
+  df re, im;
+};
+__device__ __forceinline__ dfc lz_load(const float4 *p0, const float4 *p1, long n, long cs, int k, long e) {
+  const float4 v = e < n ? p0[(long)k * cs + e] : p1[(long)k * cs + e - n];
+  return dfc{df(v.x, v.y), df(v.z, v.w)};
+}
+__device__ __forceinline__ void lz_store(float4 *p0, float4 *p1, long n, long cs, int k, long e, dfc a) {
+  const float4 v = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+  if (e < n)
+    p0[(long)k * cs + e] = v;
+  else
+    p1[(long)k * cs + e - n] = v;
 }
 
-// w -= V[:, :p] y over both parities
-lqcd_status gemv_sub(lqcd_ctx *c, const lqcd_field *V, int p, const double2 *y, lqcd_field *w) {
-  OverlapState &s = *c->ov;
-  const int N = (int)cwords(V);
-  const cuDoubleComplex one = make_cuDoubleComplex(1, 0), mone = make_cuDoubleComplex(-1, 0);
-  for (int par = 0; par < 2; par++)
-    LQ_TRY(blas_ok(cublasZgemv(s.blas, CUBLAS_OP_N, N, p, &mone, (const cuDoubleComplex *)col(V, par, 0), N,
-                               (const cuDoubleComplex *)y, 1, &one, (cuDoubleComplex *)col(w, par, 0), 1),
-                   "ZGEMV (subtraction)"));
-  return LQCD_OK;
+// partials of <V_k, w> = sum conj(V_k) w: grid (gx, p), quantities 2k (re), 2k+1 (im)
+__global__ void __launch_bounds__(kLzT) lz_dots_kernel(long n, long cs, const float4 *V0, const float4 *V1,
+                                                        const float4 *w0, const float4 *w1, double *partials) {
+  const int k = blockIdx.y;
+  dfacc re{0.0f, 0.0f}, im{0.0f, 0.0f};
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += (long)gridDim.x * blockDim.x) {
+    const dfc v = lz_load(V0, V1, n, cs, k, e), w = lz_load(w0, w1, n, 0, 0, e);
+    dfacc_madd(re, v.re, w.re);
+    dfacc_madd(re, v.im, w.im);
+    dfacc_madd(im, v.re, w.im);
+    dfacc_madd(im, -v.im, w.re);
+  }
+  const df vals[2] = {dfacc_value(re), dfacc_value(im)};
+  block_partials<2>(vals, partials, 2 * k);
 }
 
-// f[0] = 1 / sqrt(n2[0] + n2[1]) (the normalisation of a vector whose parity norms are n2)
-__global__ void inv_norm_kernel(const double *n2, double *f) { f[0] = 1.0 / sqrt(n2[0] + n2[1]); }
+// w -= sum_{k < p} V_k h_k (h: p complex doubles on the device)
+__global__ void __launch_bounds__(kLzT) lz_sub_kernel(long n, long cs, int p, const float4 *V0, const float4 *V1,
+                                                       const double2 *h, float4 *w0, float4 *w1) {
+  __shared__ dfc hs[kLzMaxP];
+  for (int k = threadIdx.x; k < p; k += blockDim.x) hs[k] = dfc{df(h[k].x), df(h[k].y)};
+  __syncthreads();
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += (long)gridDim.x * blockDim.x) {
+    dfc a = lz_load(w0, w1, n, 0, 0, e);
+    for (int k = 0; k < p; k++) {
+      const dfc v = lz_load(V0, V1, n, cs, k, e);
+      a.re = fma(-v.re, hs[k].re, a.re);
+      a.re = fma(v.im, hs[k].im, a.re);
+      a.im = fma(-v.re, hs[k].im, a.im);
+      a.im = fma(-v.im, hs[k].re, a.im);
+    }
+    lz_store(w0, w1, n, 0, 0, e, a);
+  }
+}
+
+// Z_q = sum_{l < p} V_l M_{l q} for q < nq (M: p x nq complex doubles, column-major, on the
+// device); grid (nq, element chunks, grid-stride) so the blocks of one chunk share its basis
+// rows in L2
+__global__ void __launch_bounds__(kLzT) lz_rotate_kernel(long n, long cs, int p, const float4 *V0, const float4 *V1,
+                                                          const double2 *M, float4 *Z0, float4 *Z1) {
+  __shared__ dfc ms[kLzMaxP];
+  const int q = blockIdx.x;
+  for (int l = threadIdx.x; l < p; l += blockDim.x) ms[l] = dfc{df(M[l + (long)p * q].x), df(M[l + (long)p * q].y)};
+  __syncthreads();
+  for (long e = (long)blockIdx.y * blockDim.x + threadIdx.x; e < 2 * n; e += (long)gridDim.y * blockDim.x) {
+    dfacc re{0.0f, 0.0f}, im{0.0f, 0.0f};
+    for (int l = 0; l < p; l++) {
+      const dfc v = lz_load(V0, V1, n, cs, l, e);
+      dfacc_madd(re, v.re, ms[l].re);
+      dfacc_madd(re, -v.im, ms[l].im);
+      dfacc_madd(im, v.re, ms[l].im);
+      dfacc_madd(im, v.im, ms[l].re);
+    }
+    lz_store(Z0, Z1, n, cs, q, e, dfc{dfacc_value(re), dfacc_value(im)});
+  }
+}
+
+// w *= 1 / sqrt(n2[0]) (n2[0] = |w|^2 from the dots kernel)
+__global__ void __launch_bounds__(kLzT) lz_normalise_kernel(long n, const double *n2, float4 *w0, float4 *w1) {
+  const df f(1.0 / sqrt(n2[0]));
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += (long)gridDim.x * blockDim.x) {
+    dfc a = lz_load(w0, w1, n, 0, 0, e);
+    a.re = a.re * f;
+    a.im = a.im * f;
+    lz_store(w0, w1, n, 0, 0, e, a);
+  }
+}
+
+struct LzOps {
+  lqcd_ctx *c;
+  long n;   // complex numbers per column and parity
+  long gx;  // blocks of the grid-stride kernels (the partials of the dots kernel)
+  const float4 *cp(const lqcd_field *f, int par) const { return reinterpret_cast<const float4 *>(f->data[par]); }
+  float4 *mp(lqcd_field *f, int par) const { return reinterpret_cast<float4 *>(f->data[par]); }
+  // out[2k], out[2k+1] = <V_k, w> for k < p (device doubles)
+  lqcd_status dots(const lqcd_field *V, int p, const lqcd_field *w, double *out) const {
+    lz_dots_kernel<<<dim3((unsigned)gx, (unsigned)p), kLzT, 0, c->stream>>>(n, n, cp(V, 0), cp(V, 1), cp(w, 0), cp(w, 1),
+                                                                             c->partials);
+    LQ_CU(cudaGetLastError());
+    LQ_CU(finish_reduce(c->partials, (int)gx, 2 * p, out, 1, c->stream));
+    return LQCD_OK;
+  }
+  lqcd_status sub(const lqcd_field *V, int p, const double *h, lqcd_field *w) const {
+    lz_sub_kernel<<<(unsigned)gx, kLzT, 0, c->stream>>>(n, n, p, cp(V, 0), cp(V, 1), (const double2 *)h, mp(w, 0),
+                                                         mp(w, 1));
+    LQ_CU(cudaGetLastError());
+    return LQCD_OK;
+  }
+  lqcd_status rotate(const lqcd_field *V, int p, const double2 *M, int nq, lqcd_field *Z) const {
+    const long chunks = std::min<long>((2 * n + kLzT - 1) / kLzT, 65535);
+    lz_rotate_kernel<<<dim3((unsigned)nq, (unsigned)chunks), kLzT, 0, c->stream>>>(
+        n, n, p, cp(V, 0), cp(V, 1), M, mp(Z, 0), mp(Z, 1));
+    LQ_CU(cudaGetLastError());
+    return LQCD_OK;
+  }
+  lqcd_status normalise(const double *n2, lqcd_field *w) const {
+    lz_normalise_kernel<<<(unsigned)gx, kLzT, 0, c->stream>>>(n, n2, mp(w, 0), mp(w, 1));
+    LQ_CU(cudaGetLastError());
+    return LQCD_OK;
+  }
+};
 
 // X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors of H_W^2
 lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int want, int kkeep, int mmax,
                              lqcd_field *X, FieldGuard &g, LanczosResult &out) {
   OverlapState &S = *c->ov;
-  lqcd_field *V, *V2, *w, *t1, *xd = nullptr, *td = nullptr, *wd = nullptr;
-  LQ_TRY(new_full(c, mmax + 1, &V));
-  g.f.push_back(V);
-  LQ_TRY(new_full(c, mmax + 1, &V2));
-  g.f.push_back(V2);
-  LQ_TRY(new_full(c, 1, &w));
-  g.f.push_back(w);
-  LQ_TRY(new_full(c, 1, &t1));
-  g.f.push_back(t1);
-  if (S.df) {
-    for (lqcd_field **f : {&xd, &td, &wd}) {
-      LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, 1, f));
-      g.f.push_back(*f);
-    }
+  if (mmax + 1 > kLzMaxP) return set_error(LQCD_ERR_ARG, "Lanczos basis of %d vectors too large", mmax + 1);
+  // the basis and the vector H_W^2 acts on in double-float; FP64 copies for an FP64 H_W
+  lqcd_field *V, *V2, *xd, *td, *wd, *x64 = nullptr, *t64 = nullptr;
+  for (lqcd_field **f : {&V, &V2}) {
+    LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, mmax + 1, f));
+    g.f.push_back(*f);
   }
-  // random unit start vector
+  for (lqcd_field **f : {&xd, &td, &wd}) {
+    LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, 1, f));
+    g.f.push_back(*f);
+  }
+  LQ_TRY(new_full(c, 1, &x64));
+  g.f.push_back(x64);
+  LQ_TRY(new_full(c, 1, &t64));
+  g.f.push_back(t64);
+  const long n = cwords(V);
+  const long gx = std::min<long>((2 * n + kLzT - 1) / kLzT, (c->Vh + 31) / 32);
+  LQ_TRY(ensure_partials(c, 2 * (mmax + 1)));
+  const LzOps ops{c, n, gx};
+  // random unit start vector (FP64 Gaussian, converted)
   {
-    const long nd = 2L * cwords(w);
+    const long nd = 2L * n;
     for (int p = 0; p < 2; p++) {
-      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)w->data[p], nd,
+      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)x64->data[p], nd,
                                                                                    prm->seed * 2 + p + 1);
       LQ_CU(cudaGetLastError());
     }
     std::vector<double> n2;
-    LQ_TRY(field_norms(c, w, 1, n2));
-    LQ_TRY(scale_full(c, w, w, {1.0 / std::sqrt(n2[0])}, 1));
-    LQ_TRY(copy_col(c, V, 0, w, 0));
+    LQ_TRY(field_norms(c, x64, 1, n2));
+    LQ_TRY(convert_full(c, wd, x64, 1, 1.0 / std::sqrt(n2[0])));
+    LQ_TRY(copy_col(c, V, 0, wd, 0));
   }
   const int ld = mmax + 1;
   std::vector<zc> Hm((size_t)ld * mmax, zc(0, 0));
   double2 *d;
-  LQ_TRY(small_scratch(c, (size_t)(mmax + 1) * mmax + 2 * (size_t)(mmax + 1), &d));
-  double2 *dh1 = d + (size_t)(mmax + 1) * mmax, *dh2 = dh1 + (mmax + 1);  // the two Gram-Schmidt passes
-  // pinned host copies of one step's coefficients and norms: one sync per step
+  LQ_TRY(small_scratch(c, (size_t)(mmax + 1) * mmax + 2 * (size_t)(mmax + 1) + 1, &d));
+  double2 *dh1 = d + (size_t)(mmax + 1) * mmax, *dh2 = dh1 + (mmax + 1), *dn = dh2 + (mmax + 1);
+  // pinned host copies of one step's coefficients and norm: one sync per step
   struct Pinned {
     double2 *h = nullptr;
     ~Pinned() {
@@ -1024,41 +1128,35 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
     cudaGetLastError();
     return set_error(LQCD_ERR_OOM, "cannot allocate Lanczos host scratch");
   }
-  LQ_TRY(ensure_partials(c, 1));
-  double *dn2 = c->results, *dfac = c->results + 768;
   int j0 = 0;
-  std::vector<zc> h;
   for (;;) {
     for (int j = j0; j < mmax; j++) {
       // w = H_W^2 v_j
-      LQ_TRY(copy_col(c, w, 0, V, j));
+      LQ_TRY(copy_col(c, xd, 0, V, j));
       if (S.df) {
-        LQ_TRY(convert_full(c, xd, w, 1));
         LQ_TRY(hw(c, 1, td, xd));
         LQ_TRY(hw(c, 1, wd, td));
-        LQ_TRY(convert_full(c, w, wd, 1));
       } else {
-        LQ_TRY(hw(c, 1, t1, w));
-        LQ_TRY(hw(c, 1, w, t1));
+        LQ_TRY(convert_full(c, x64, xd, 1));
+        LQ_TRY(hw(c, 1, t64, x64));
+        LQ_TRY(hw(c, 1, x64, t64));
+        LQ_TRY(convert_full(c, wd, x64, 1));
       }
       out.applies += 2;
       // two passes of classical Gram-Schmidt against v_0 .. v_j, then
       // v_{j+1} = w / |w|, all on the stream; the host reads the
       // coefficients and |w|^2 once
-      LQ_TRY(gemv_c(c, V, j + 1, w, dh1));
-      LQ_TRY(gemv_sub(c, V, j + 1, dh1, w));
-      LQ_TRY(gemv_c(c, V, j + 1, w, dh2));
-      LQ_TRY(gemv_sub(c, V, j + 1, dh2, w));
-      for (int p = 0; p < 2; p++) LQ_CU(blas_norm2(LQCD_F64, c->Vh, 1, w->ref(p), c->partials, dn2 + p, 1, c->stream));
-      inv_norm_kernel<<<1, 1, 0, c->stream>>>(dn2, dfac);
-      LQ_CU(cudaGetLastError());
-      for (int p = 0; p < 2; p++) LQ_CU(blas_scale(LQCD_F64, LQCD_F64, c->Vh, 1, w->mut(p), w->ref(p), dfac, c->stream));
-      LQ_TRY(copy_col(c, V, j + 1, w, 0));
-      LQ_CU(cudaMemcpyAsync(hp.h, dh1, sizeof(double2) * 2 * (size_t)(mmax + 1), cudaMemcpyDeviceToHost, c->stream));
-      LQ_CU(cudaMemcpyAsync(hp.h + 2 * (size_t)(mmax + 1), dn2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      LQ_TRY(ops.dots(V, j + 1, wd, (double *)dh1));
+      LQ_TRY(ops.sub(V, j + 1, (const double *)dh1, wd));
+      LQ_TRY(ops.dots(V, j + 1, wd, (double *)dh2));
+      LQ_TRY(ops.sub(V, j + 1, (const double *)dh2, wd));
+      LQ_TRY(ops.dots(wd, 1, wd, (double *)dn));
+      LQ_TRY(ops.normalise((const double *)dn, wd));
+      LQ_TRY(copy_col(c, V, j + 1, wd, 0));
+      LQ_CU(cudaMemcpyAsync(hp.h, dh1, sizeof(double2) * (2 * (size_t)(mmax + 1) + 1), cudaMemcpyDeviceToHost,
+                            c->stream));
       LQ_CU(cudaStreamSynchronize(c->stream));
-      const double2 nn = hp.h[2 * (size_t)(mmax + 1)];
-      const double beta = std::sqrt(nn.x + nn.y);
+      const double beta = std::sqrt(hp.h[2 * (size_t)(mmax + 1)].x);
       if (!(beta > 1e-13)) return set_error(LQCD_ERR_NOCONV, "Lanczos breakdown at step %d (beta %.3e)", j, beta);
       for (int i = 0; i <= j; i++)
         Hm[i + (size_t)ld * j] = zc(hp.h[i].x + hp.h[mmax + 1 + i].x, hp.h[i].y + hp.h[mmax + 1 + i].y);
@@ -1102,13 +1200,14 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
                    out.cycles, worst, kneed, mus[kneed - 1], mus[kkeep - 1]);
     LQ_TRY(to_dev(c, Qs, d));
     if (conv || out.cycles >= prm->max_filter) {
-      LQ_TRY(rotate(c, V, m, d, kneed, X, 1.0, 0.0));
+      LQ_TRY(ops.rotate(V, m, d, kneed, V2));
+      LQ_TRY(convert_full(c, X, V2, kneed));
       out.kneed = kneed;
       out.converged = conv;
       return LQCD_OK;
     }
     // thick restart: V2 = [V Q_k, v_m]; projected matrix diag(theta) bordered by beta_m Q_{m-1,i}
-    LQ_TRY(rotate(c, V, m, d, kkeep, V2, 1.0, 0.0));
+    LQ_TRY(ops.rotate(V, m, d, kkeep, V2));
     LQ_TRY(copy_col(c, V2, kkeep, V, m));
     std::swap(V, V2);
     std::fill(Hm.begin(), Hm.end(), zc(0, 0));
