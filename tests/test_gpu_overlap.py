@@ -45,7 +45,8 @@ def _ov(L, lat, psi, op, nrhs=1, cg=None):
 
 
 @pytest.fixture(scope="module", params=[("f64", "subspace"), ("df64", "subspace"), ("f64", "lanczos"),
-                                        ("df64", "lanczos")])
+                                        ("df64", "lanczos")],
+                ids=["f64-subspace", "df64-subspace", "f64-lanczos", "df64-lanczos"])
 def rough(lib, request):
     dims = (4, 4, 4, 4)
     U = gen.gauge_field(dims, 0.3, 23)
