@@ -298,7 +298,8 @@ typedef struct {
   int eig_method;    /* low-mode solver on H_W^2: LQCD_EIG_SUBSPACE (0, the default:      */
                      /* block subspace iteration with a Chebyshev filter; max_filter caps */
                      /* its sweeps) or LQCD_EIG_LANCZOS (thick-restart Lanczos, one      */
-                     /* vector at a time; max_filter caps its restarts).  Lanczos needs */
+                     /* vector at a time, double-float basis; max_filter caps its       */
+                     /* restarts; 16^3x32: 16 s against 70 s).  Lanczos needs           */
                      /* far fewer H_W applications, but a single Krylov vector can reach */
                      /* a near-degenerate cluster late: on clustered spectra it may stop */
                      /* with converged pairs above a cluster it has not yet found, which */
