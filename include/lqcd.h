@@ -330,11 +330,13 @@ typedef enum {
   LQCD_OV_SOLVE = 3       /* out = D_ov(m)^-1 in by CG on the normal equations         */
 } lqcd_overlap_op;
 
-/* Compute the low modes of H_W (FP64 block subspace iteration on H_W^2 with
- * Chebyshev filtering and Rayleigh-Ritz in H_W) and the Chebyshev
+/* Compute the low modes of H_W (block subspace iteration on H_W^2 with
+ * Chebyshev filtering, or thick-restart Lanczos on H_W^2, per
+ * params->eig_method; then Rayleigh-Ritz in H_W) and the Chebyshev
  * coefficients for the sign function, and keep them in the context.  Needs
  * the gauge field.  Blocks.  LQCD_ERR_NOCONV if the low modes do not reach
- * eig_tol within max_filter sweeps (info is filled either way). */
+ * eig_tol within max_filter sweeps or restarts (info is filled either way);
+ * LQCD_ERR_ARG for a lattice too small for the requested modes. */
 lqcd_status lqcd_overlap_setup(lqcd_ctx *ctx, const lqcd_overlap_params *params, lqcd_overlap_info *info);
 
 /* Copy the n_low low-mode vectors (canonical, n_low fields back to back,

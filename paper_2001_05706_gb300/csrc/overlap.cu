@@ -1273,6 +1273,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   if (prm->eig_method == LQCD_EIG_LANCZOS) {
     // restart size m (the block of the subspace method), basis of up to 2m
     const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
+    if (mmax < m + 8) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", m + 8);
     LanczosResult lr;
     LQ_TRY(lowmodes_lanczos(c, prm, want, m, mmax, X, g, lr));
     kneed = lr.kneed;
