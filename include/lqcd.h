@@ -346,8 +346,12 @@ lqcd_status lqcd_overlap_lowmodes(lqcd_ctx *ctx, double *vecs, int on_device);
 /* Apply or invert the overlap operator set up by lqcd_overlap_setup on nrhs
  * canonical full-lattice spinors (host or device), in FP64.  For
  * LQCD_OV_SOLVE, cg->tol is the target ||b - D_ov x|| / ||b|| per right-hand
- * side and cg->max_iter caps the iterations; info (may be NULL) receives the
- * iteration count and the final residuals.  Blocks. */
+ * side and cg->max_iter caps the iterations; cg->inner selects the plain
+ * FP64 CG (LQCD_F64) or the mixed one with an FP32 inner sign function
+ * (LQCD_F32, reliable updates every cg->delta); the other fields of cg
+ * (solver, schur, recon, outer, ...) belong to the Wilson-clover solves and
+ * are ignored here.  info (may be NULL) receives the iteration count and the
+ * final residuals.  Blocks. */
 lqcd_status lqcd_overlap(lqcd_ctx *ctx, double *out, const double *in, int nrhs, int on_device, lqcd_overlap_op op,
                          const lqcd_solve_params *cg, lqcd_solve_info *info);
 
