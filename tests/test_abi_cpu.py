@@ -69,3 +69,17 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == expect
+
+
+def test_enum_values_match_header(tmp_path):
+    """Every enum constant the binding defines has the header's value."""
+    import paper_2001_05706_gb300 as L
+    names = [n for n in dir(L) if n.startswith("LQCD_") and isinstance(getattr(L, n), int)]
+    assert len(names) >= 40
+    lines = "".join(f'printf("%d\\n", (int){n});' for n in names)
+    src = tmp_path / "en.c"
+    src.write_text('#include <stdio.h>\n#include "lqcd.h"\nint main(void){' + lines + ' return 0;}\n')
+    exe = tmp_path / "en"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == [getattr(L, n) for n in names], names
