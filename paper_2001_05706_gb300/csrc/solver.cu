@@ -19,7 +19,10 @@
 // operator, the update being kept only if it lowers that residual; the search
 // direction p is kept, rescaled into the new normalisation, and
 // gamma = |Mhat^dag r|^2 recomputed from the new residual, or CG restarts
-// from p = s after a rejected update or a turn-round.
+// from p = s after a rejected update or a turn-round.  With the symmetric
+// Schur form every Mhat above is A_oo^-1 Mhat and every residual
+// A_oo^-1 (bhat - Mhat x) (op_eo, residual_eo), its targets divided by a
+// bound of ||A_oo||; BiCGStab (below) works on the same operators.
 #include <algorithm>
 #include <chrono>
 #include <functional>
