@@ -52,3 +52,15 @@ def test_single_process_helpers():
     assert abs(bench.weak_gbs(2e9, 1.0, 1) - 2000.0) < 1e-9
     assert bench.site_bytes("f32", 12, "k2a") == 864 and bench.site_bytes("f32", 12, "k2b") == 960
     assert bench.site_bytes("f64", 18, "k2a") == 2112 and bench.site_bytes("f16", 12, "k2b") == 496
+
+
+def test_committed_profile_matches_the_kernel_source():
+    """The ncu summary the bench reads its DRAM traffic from was captured on the
+    current dslash source (same hash), so roofline.traffic is reported."""
+    import bench
+    for kernel in ("k2a", "k2b"):
+        t = bench.profiled_traffic("dslash_f32_r12_mhat", kernel)
+        assert t is not None and t > 0, kernel
+        # compulsory bytes of one full-size launch; the measured traffic is within a few percent
+        compulsory = 1048576 * bench.site_bytes("f32", 12, kernel)
+        assert 0.9 < t / compulsory < 1.1
