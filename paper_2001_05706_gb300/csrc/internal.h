@@ -89,6 +89,14 @@ cudaError_t bi_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, Fie
 
 // ---- dslash_<type>.cu
 cudaError_t launch_dslash_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int nr, cudaStream_t st);
+// the tiled many-right-hand-side kernel (dslash_mrhs.cuh), g warps per block
+cudaError_t launch_dslash_mrhs_prec(lqcd_prec prec, const DslashParams &P, int recon, int mode, int g, cudaStream_t st);
+// Kernel variants of one dslash launch: 1, 2, 4 = dslash_kernel with that many
+// right-hand sides per thread; kMrhsVariant + g = dslash_mrhs_kernel with g warps
+// (2g right-hand sides) per block
+constexpr int kMrhsVariant = 100;
+cudaError_t launch_dslash_variant(lqcd_prec prec, const DslashParams &P, int recon, int mode, int variant,
+                                  cudaStream_t st);
 
 inline int prec_bytes(lqcd_prec p) { return (p == LQCD_F64 || p == LQCD_DF64) ? 8 : p == LQCD_F32 ? 4 : 2; }
 inline bool prec_half(lqcd_prec p) { return p == LQCD_F16 || p == LQCD_BF16; }

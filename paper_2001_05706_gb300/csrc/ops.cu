@@ -82,12 +82,17 @@ lqcd_status ensure_partials(lqcd_ctx *c, int nrhs) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner for the number of right-hand sides each thread carries (links
-// and clover loaded once for all of them): on the first launch of a given
-// (precision, link form, mode, nrhs, volume) every admissible choice is timed
+// Autotuner for the kernel variant of a dslash launch: dslash_kernel with 1,
+// 2 or 4 right-hand sides per thread (links and clover loaded once for all of
+// them), or, for FP32/FP16/BF16 with several right-hand sides,
+// dslash_mrhs_kernel with g warps of two right-hand sides sharing one staged
+// tile of links and clover (g = 1, 2, 3, 6).  On the first launch of a given
+// (precision, link form, mode, nrhs, volume) every admissible variant is timed
 // with CUDA events on the context's stream and the fastest is kept, in memory
 // and, if LQCD_TUNE_CACHE names a file, in that file (one line per entry).
 // Re-running a launch is harmless: the kernel never writes its inputs.
+// LQCD_FORCE_VARIANT (read at every launch) forces a variant wherever it is
+// admissible, so tests can compare each kernel with the oracle.
 // ---------------------------------------------------------------------------
 using TuneKey = std::tuple<int, int, int, int, long>;
 static std::map<TuneKey, int> g_tune;
@@ -116,7 +121,36 @@ static void tune_store(const TuneKey &k, int nr) {
   std::fclose(f);
 }
 
-static int default_nr(lqcd_prec prec, int mode, int nrhs) {
+static bool mrhs_ok(lqcd_prec prec, int mode, int nrhs) {
+  if (nrhs < 2) return false;
+  if (prec != LQCD_F32 && prec != LQCD_F16 && prec != LQCD_BF16) return false;
+  if (mode == MODE_FOLDED_AINV) return false;
+  return mode != MODE_CHEB || prec == LQCD_F32;
+}
+
+// every variant that can run this launch
+static std::vector<int> variants(lqcd_prec prec, int mode, int nrhs) {
+  std::vector<int> v;
+  for (int nr : {1, 2, 4}) {
+    if (nrhs % nr != 0) continue;
+    if (nr > 1 && mode == MODE_FOLDED_AINV) continue;
+    if (nr == 4 && prec == LQCD_DF64) continue;
+    v.push_back(nr);
+  }
+  if (mrhs_ok(prec, mode, nrhs)) {
+    const int pairs = (nrhs + 1) / 2;
+    for (int g : {1, 2, 3, 6})
+      if (g <= pairs) v.push_back(kMrhsVariant + g);
+  }
+  return v;
+}
+
+static int default_variant(lqcd_prec prec, int mode, int nrhs) {
+  if (mrhs_ok(prec, mode, nrhs)) {
+    const int pairs = (nrhs + 1) / 2;
+    for (int g : {6, 3, 2, 1})
+      if (pairs % g == 0) return kMrhsVariant + g;
+  }
   if (mode == MODE_FOLDED_AINV) return 1;
   if (prec == LQCD_F64 || prec == LQCD_DF64) return nrhs % 2 == 0 ? 2 : 1;
   if (nrhs % 4 == 0) return 4;
@@ -124,11 +158,13 @@ static int default_nr(lqcd_prec prec, int mode, int nrhs) {
   return 1;
 }
 
-static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon, int mode, int nrhs) {
-  if (mode == MODE_FOLDED_AINV || nrhs == 1) return 1;
-  std::vector<int> cand;
-  for (int nr : {1, 2, 4})
-    if (nrhs % nr == 0) cand.push_back(nr);
+static int pick_variant(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon, int mode, int nrhs) {
+  const std::vector<int> cand = variants(prec, mode, nrhs);
+  if (const char *f = std::getenv("LQCD_FORCE_VARIANT")) {
+    const int v = std::atoi(f);
+    for (int x : cand)
+      if (x == v) return v;
+  }
   if (cand.size() == 1) return cand[0];
   const TuneKey key((int)prec, recon, mode, nrhs, c->Vh);
   {
@@ -140,27 +176,27 @@ static int pick_nr(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
-    return default_nr(prec, mode, nrhs);
+    return default_variant(prec, mode, nrhs);
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
-    return default_nr(prec, mode, nrhs);
+    return default_variant(prec, mode, nrhs);
   }
-  int best = default_nr(prec, mode, nrhs);
+  int best = default_variant(prec, mode, nrhs);
   float best_ms = 1e30f;
-  for (int nr : cand) {
-    if (launch_dslash_prec(prec, P, recon, mode, nr, c->stream) != cudaSuccess) {
+  for (int v : cand) {
+    if (launch_dslash_variant(prec, P, recon, mode, v, c->stream) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < 3; r++) launch_dslash_prec(prec, P, recon, mode, nr, c->stream);
+    for (int r = 0; r < 3; r++) launch_dslash_variant(prec, P, recon, mode, v, c->stream);
     cudaEventRecord(e1, c->stream);
     float ms = 0;
     if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
       best_ms = ms;
-      best = nr;
+      best = v;
     }
   }
   cudaEventDestroy(e0);
@@ -227,8 +263,8 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
 #if LQCD_DEBUG_BOUNDS
   P.dbg = c->counter + 63;  // spare reduction counter, zero between launches
 #endif
-  const int nr = pick_nr(c, P, prec, recon, mode, nrhs);
-  LQ_CU(launch_dslash_prec(prec, P, recon, mode, nr, c->stream));
+  const int variant = pick_variant(c, P, prec, recon, mode, nrhs);
+  LQ_CU(launch_dslash_variant(prec, P, recon, mode, variant, c->stream));
 #if LQCD_DEBUG_BOUNDS
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   LQ_CU(cudaStreamIsCapturing(c->stream, &cap));

@@ -64,3 +64,15 @@ def rel(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def site_max_rel(got, expect):
+    """Largest per-site relative error: ||got_x - expect_x|| / ||expect_x|| over
+    the sites, the denominator floored at a tenth of the rms site norm (a site
+    whose exact value is near zero is held to an absolute bound instead)."""
+    g = np.asarray(got).reshape(-1, 12)
+    e = np.asarray(expect).reshape(-1, 12)
+    ne = np.linalg.norm(e, axis=1)
+    d = np.linalg.norm(g - e, axis=1)
+    floor = 0.1 * np.sqrt(np.mean(ne**2))
+    return float(np.max(d / np.maximum(ne, floor)))
