@@ -341,3 +341,70 @@ def test_mhat_slab_matches_full(rough):
         assert np.abs(out[t0:t1] - full[t0:t1]).max() < 1e-14 * np.abs(full).max()
         rest = np.delete(out, range(t0, t1), axis=0)
         assert rest.size == 0 or np.abs(rest).max() == 0
+
+
+# ---------------------------------------------------------------------------
+# the checker of every solve: true_residual = ||b - M x|| / ||b||
+# ---------------------------------------------------------------------------
+
+def test_true_residual_free_field_closed_form():
+    """Unit links, b a plane wave, x = M(p)^-1 b + eps v with v another plane
+    wave: the residual is eps ||M(q) v|| / ||b|| with M(q) the momentum-space
+    matrix 1 - 2k sum cos q + 2ik sum g sin q, computed here without the
+    oracle's operator.  A missing square root, a wrong denominator or a sign
+    error in b - M x changes the value."""
+    dims = (4, 4, 4, 8)
+    U = gen.unit_gauge(dims)
+    g = _gammas()
+
+    def Mmom(q):
+        return (1 - 2 * KAPPA * np.cos(q).sum()) * np.eye(4) + 2j * KAPPA * sum(g[mu] * np.sin(q[mu]) for mu in range(4))
+
+    p = momenta(dims, (1, 2, 0, 3), 1)
+    q = momenta(dims, (0, 1, 3, 1), 1)
+    u = (np.arange(12).reshape(4, 3) + 1.0) * (1 - 0.5j)
+    w = np.cos(np.arange(12)).reshape(4, 3) + 1j * np.sin(3.0 * np.arange(12)).reshape(4, 3)
+    b = plane_wave(dims, p, u)
+    x0 = plane_wave(dims, p, np.linalg.solve(Mmom(p), u))
+    assert oracle.true_residual(dims, U, None, KAPPA, x0, b) < 1e-14
+    assert oracle.true_residual(dims, U, None, KAPPA, np.zeros_like(b), b) == 1.0
+    for eps in (1e-3, 0.25):
+        x = x0 + eps * plane_wave(dims, q, w)
+        V = int(np.prod(dims))
+        expect = eps * np.linalg.norm(Mmom(q) @ w) * np.sqrt(V) / (np.linalg.norm(u) * np.sqrt(V))
+        assert abs(oracle.true_residual(dims, U, None, KAPPA, x, b) / expect - 1) < 1e-12
+
+
+def test_true_residual_dense_clover(dense24):
+    """With the clover term (2^4, dense M): x = M^-1 b + d gives ||M d|| / ||b||,
+    the residual is invariant under (x, b) -> (c x, c b), and x = 0 gives 1."""
+    dims, U, A, Ai, M = dense24
+    b = gen.gaussian_spinor(dims, 41)[0]
+    d = 1e-4 * gen.gaussian_spinor(dims, 42)[0]
+    x = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape) + d
+    expect = np.linalg.norm(M @ d.reshape(-1)) / np.linalg.norm(b)
+    r = oracle.true_residual(dims, U, A, 0.13, x, b)
+    assert abs(r / expect - 1) < 1e-8
+    assert abs(oracle.true_residual(dims, U, A, 0.13, (2.5 - 1j) * x, (2.5 - 1j) * b) / r - 1) < 1e-12
+    assert oracle.true_residual(dims, U, A, 0.13, np.zeros_like(b), b) == 1.0
+    # the clover term is part of the operator it checks: without it the value differs
+    assert abs(oracle.true_residual(dims, U, None, 0.13, x, b) - r) > 1e-3
+
+
+def test_site_list_variants_match_full(rough):
+    """hop_sites and clover_sites (the per-site evaluations of the full-size
+    parity test) equal the full-lattice hop and clover at any site list,
+    including the boundary sites, both time boundary conditions and the
+    adjoint hop."""
+    dims, U, A, Ai = rough
+    V = int(np.prod(dims))
+    psi = gen.gaussian_spinor(dims, 51)[0]
+    rng = np.random.default_rng(5)
+    sites = np.concatenate([[0, V - 1, dims[0] - 1, V - dims[0]], rng.choice(V, 40, replace=False)])
+    for tbc in (0, 1):
+        for dag in (False, True):
+            full = oracle.hop(dims, U, psi, tbc, dagger=dag).reshape(V, 4, 3)
+            assert np.abs(oracle.hop_sites(dims, U, psi, sites, tbc, dagger=dag) - full[sites]).max() == 0
+    Af = oracle.clover(dims, U, KAPPA, 1.3)
+    assert np.abs(oracle.clover_sites(dims, U, KAPPA, 1.3, sites) - Af[sites]).max() == 0
+    assert np.abs(Af - A).max() == 0
