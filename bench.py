@@ -46,6 +46,13 @@ FLOPS = {"k2a": 1824, "k2b": 1872}
 PB = {"f64": 8, "df64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
 
+def bench_config(world: int) -> dict:
+    """The workload description both arms print (same keys, same values)."""
+    return {"workload": WORKLOAD, "lattice": list(DIMS), "prec": "f32", "recon": 12, "nrhs": 1,
+            "kappa": KAPPA, "c_sw": CSW, "eps": EPS, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2: each step streams ~1.2 GB (links 403 MB, clover 604 MB, spinors)"}
+
+
 def site_bytes(prec: str, recon: int, kernel: str) -> int:
     """Compulsory bytes per output site: 8 links, input spinor, output spinor,
     clover block pair (+ the local spinor for K2b); FP16/BF16 add a 4-byte
@@ -61,6 +68,17 @@ def site_bytes(prec: str, recon: int, kernel: str) -> int:
 
 def mhat_bytes(prec, recon):
     return site_bytes(prec, recon, "k2a") + site_bytes(prec, recon, "k2b")
+
+
+def mhat_bytes_per_rhs(prec, recon, nrhs):
+    """Compulsory bytes per output site and right-hand side of an nrhs-RHS Mhat:
+    links and clover once per site for all right-hand sides, spinors per RHS
+    (K2a: input and output; K2b: input, local and output)."""
+    b = PB[prec]
+    half = prec in ("f16", "bf16")
+    sp = 24 * b + (4 if half else 0)
+    lc = 8 * recon * b + 72 * b + (4 if half else 0)
+    return 2 * lc / nrhs + 5 * sp
 
 
 # ---------------------------------------------------------------------------
@@ -251,7 +269,7 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "prec": "f32", "recon": 12, "nrhs": 1},
+        "config": bench_config(args.gpus),
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample,
                          "sites_per_s": sites / dt},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -337,12 +355,17 @@ def solver_iteration(args):
     return 0
 
 
-def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
-    """FP64 CG vs mixed precision on the benchmark lattice, one Gaussian RHS."""
+SOLVE_SET = ("fp64", "mixed_f32", "mixed_f16", "mixed_bf16", "df64", "mixed_f16_df64", "bicgstab_fp64",
+             "bicgstab_mixed_f16", "bicgstab_mixed_f16_df64")
+
+
+def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi, dims=None, which=SOLVE_SET, src_seed=2003):
+    """FP64 CG vs mixed precision on one lattice, one Gaussian RHS."""
     import gen
-    b = gen.gaussian_spinor(DIMS, 2003)[0]
+    dims = tuple(dims or DIMS)
+    b = gen.gaussian_spinor(dims, src_seed)[0]
     bt = torch.from_numpy(b.view(np.float64).copy()).cuda()
-    res = {"lattice": list(DIMS), "kappa": KAPPA, "c_sw": CSW, "tol": 1e-10, "source": "Gaussian, seed 2003"}
+    res = {"lattice": list(dims), "kappa": KAPPA, "c_sw": CSW, "tol": 1e-10, "source": f"Gaussian, seed {src_seed}"}
     xs = {}
     cg, bi = L.LQCD_SOLVER_CGLS, L.LQCD_SOLVER_BICGSTAB
     for name, inner, outer, solver in (
@@ -351,6 +374,8 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
             ("df64", L.LQCD_DF64, L.LQCD_DF64, cg), ("mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, cg),
             ("bicgstab_fp64", L.LQCD_F64, L.LQCD_F64, bi), ("bicgstab_mixed_f16", L.LQCD_F16, L.LQCD_F64, bi),
             ("bicgstab_mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, bi)):
+        if name not in which:
+            continue
         xt = torch.zeros_like(bt)
         prm = L.solve_params(tol=1e-10, max_iter=40000 if solver == cg else 4000, inner=inner, delta=0.1, recon=18,
                              inner_recon=12, check_every=0, outer=outer, solver=solver)
@@ -364,12 +389,12 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
                      "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
         xs[name] = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
     # the headline pair: FP64 reliable updates against the FP64 CG
-    best = min((k for k in ("mixed_f32", "mixed_f16", "mixed_bf16") if res[k]["status"] == "ok"),
+    best = min((k for k in ("mixed_f32", "mixed_f16", "mixed_bf16") if k in res and res[k]["status"] == "ok"),
                key=lambda k: res[k]["seconds"], default=None)
     if best and res["fp64"]["status"] == "ok":
         res["best_mixed"] = best
         res["speedup_vs_fp64"] = res["fp64"]["seconds"] / res[best]["seconds"]
-    if res["df64"]["status"] == "ok" and res["fp64"]["status"] == "ok":
+    if "df64" in res and res["df64"]["status"] == "ok" and res["fp64"]["status"] == "ok":
         res["df64_cg_speedup_vs_fp64_cg"] = res["fp64"]["seconds"] / res["df64"]["seconds"]
     ok = [k for k in res if isinstance(res[k], dict) and res[k].get("status") == "ok" and k != "fp64"]
     if ok and res["fp64"]["status"] == "ok":
@@ -378,10 +403,48 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi):
         res["fastest_speedup_vs_fp64_cg"] = res["fp64"]["seconds"] / res[fastest]["seconds"]
     if want_oracle and oracle_AAi is not None:
         import oracle
-        A, _ = oracle_AAi
+        A = oracle_AAi[0]
         for name, x in xs.items():
-            res[name]["true_resid_oracle"] = oracle.true_residual(DIMS, U, A, KAPPA, x, b)
+            res[name]["true_resid_oracle"] = oracle.true_residual(dims, U, A, KAPPA, x, b)
     return res
+
+
+def headline(res):
+    """FP64 CGLS against the best mixed CGLS (FP64 updates) and the fastest
+    solve of any kind, with the oracle's residuals of those solves."""
+    if not res or res.get("fp64", {}).get("status") != "ok":
+        return None
+    h = {"lattice": res["lattice"], "fp64_cgls_s": res["fp64"]["seconds"]}
+    for key, name in (("best_mixed", res.get("best_mixed")), ("fastest", res.get("fastest"))):
+        if name:
+            h[key] = name
+            h[key + "_s"] = res[name]["seconds"]
+            h[key + "_speedup_vs_fp64_cgls"] = res["fp64"]["seconds"] / res[name]["seconds"]
+    ok = [k for k in res if isinstance(res[k], dict) and "true_resid_oracle" in res[k]]
+    if ok:
+        h["max_true_resid_oracle"] = max(res[k]["true_resid_oracle"] for k in ok)
+        h["oracle_checked_solves"] = len(ok)
+    return h
+
+
+def run_config3(L, torch, stream, want_oracle):
+    """Config 3: 48^3x96 (10.6 M sites), eps 0.2, c_sw 1.0, kappa 0.125, one
+    Gaussian RHS: plain FP64 CGLS against mixed FP16 CGLS (FP64 updates, and
+    DF64 updates) and mixed FP16 BiCGStab with DF64 updates, each to an
+    oracle-recomputed true residual of 1e-10."""
+    import gen
+    dims = (48, 48, 48, 96)
+    U = gen.gauge_field(dims, EPS, 1003)
+    AAi = None
+    if want_oracle:
+        import oracle
+        A = oracle.clover(dims, U, KAPPA, CSW)
+        AAi = (A, None)
+    with L.Lattice(dims, stream=stream) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(KAPPA, CSW)
+        return run_solves(L, torch, lat, U, 0, want_oracle, AAi, dims=dims,
+                          which=("fp64", "mixed_f16", "mixed_f16_df64", "bicgstab_mixed_f16_df64"), src_seed=2003)
 
 
 def run_multi_rhs(L, torch, lat, U, want_oracle, oracle_AAi):
@@ -417,8 +480,9 @@ def run_multi_rhs(L, torch, lat, U, want_oracle, oracle_AAi):
         if want_oracle and oracle_AAi is not None:
             import oracle
             x = xt.cpu().numpy().view(np.complex128).reshape(b.shape)
-            r["true_resid_oracle_rhs0_rhs11"] = [oracle.true_residual(DIMS, U, oracle_AAi[0], KAPPA, x[k], b[k])
-                                                 for k in (0, 11)]
+            rr = [oracle.true_residual(DIMS, U, oracle_AAi[0], KAPPA, x[k], b[k]) for k in range(12)]
+            r["true_resid_oracle"] = rr
+            r["max_true_resid_oracle"] = max(rr)
         if name == "cgls":
             res.update(r)
         else:
@@ -471,22 +535,26 @@ def run_schur_rough(L, torch, stream, want_oracle):
     return res
 
 
-def run_batch(L, torch, stream):
+def run_batch(L, torch, stream, want_oracle):
     """Config 4 (ii): 24 lattices of uneven volume (8 each of 16^3x32, 20^3x40,
     24^3x48; eps 0.2, kappa 0.125, c_sw 1.0), 4 Gaussian RHS each, mixed
-    precision, one graph-captured batched solve."""
+    precision, one graph-captured batched solve; every one of the 96 solutions
+    is checked by the oracle's full-lattice true residual."""
     import gen
     shapes = [(16, 16, 16, 32)] * 8 + [(20, 20, 20, 40)] * 8 + [(24, 24, 24, 48)] * 8
-    lats, bs, xs = [], [], []
+    lats, bs, xs, Us, bh = [], [], [], [], []
     for j, d in enumerate(shapes):
         U = gen.gauge_field(d, EPS, 3000 + j)
         lat = L.Lattice(d, stream=stream)
         lat.load_gauge(U.view(np.float64))
         lat.clover(KAPPA, CSW)
         lats.append(lat)
-        b = torch.from_numpy(gen.gaussian_spinor(d, 4000 + j, nrhs=4).view(np.float64).reshape(-1).copy()).cuda()
+        bnp = gen.gaussian_spinor(d, 4000 + j, nrhs=4)
+        b = torch.from_numpy(bnp.view(np.float64).reshape(-1).copy()).cuda()
         bs.append(b)
         xs.append(torch.zeros_like(b))
+        Us.append(U)
+        bh.append(bnp)
     sites = sum(int(np.prod(d)) for d in shapes)
     res = {"lattices": "8 x 16^3x32 + 8 x 20^3x40 + 8 x 24^3x48", "sites": sites, "rhs_per_lattice": 4,
            "inner": "f16", "tuning": "autotuner warmed by an untimed one-iteration batch per outer precision"}
@@ -494,6 +562,7 @@ def run_batch(L, torch, stream):
         prm = L.solve_params(tol=1e-10, max_iter=1, inner=L.LQCD_F16, delta=0.1, nrhs=4, recon=18, inner_recon=12,
                              check_every=0, outer=outer)
         L.lqcd_solve_batch([l.ctx for l in lats], [torch.zeros_like(b) for b in bs], bs, prm, raise_on_noconv=False)
+    sols = {}
     for name, outer in (("fp64_updates", L.LQCD_F64), ("df64_updates", L.LQCD_DF64)):
         for x in xs:
             x.zero_()
@@ -507,13 +576,56 @@ def run_batch(L, torch, stream):
         r = {"seconds": wall, "max_iters": max(i.iters for i in infos),
              "max_true_resid_gpu_fp64": max(max(i.true_resid[:4]) for i in infos),
              "status": "ok" if st == L.LQCD_OK else L.lqcd_last_error()}
+        sols[name] = [x.cpu().numpy().view(np.complex128).reshape(b.shape) for x, b in zip(xs, bh)]
         if name == "fp64_updates":
             res.update(r)
         else:
             res[name] = r
     for lat in lats:
         lat.close()
+    if want_oracle:
+        import oracle
+        worst = {k: 0.0 for k in sols}
+        n = 0
+        for j, d in enumerate(shapes):
+            A = oracle.clover(d, Us[j], KAPPA, CSW)
+            for k in range(4):
+                n += 1
+                for name in sols:
+                    r = oracle.true_residual(d, Us[j], A, KAPPA, sols[name][j][k], bh[j][k])
+                    worst[name] = max(worst[name], r)
+        res["max_true_resid_oracle"] = worst["fp64_updates"]
+        res["df64_updates"]["max_true_resid_oracle"] = worst["df64_updates"]
+        res["oracle_checked_rhs"] = n
     return res
+
+
+def mrhs_mhat(L, torch, ctx, psi, stream, steps):
+    """The many-right-hand-side Schur complement: 12 RHS against one, per
+    storage precision (autotuned kernel variant), with the per-RHS compulsory
+    bytes (links and clover read once for all right-hand sides)."""
+    out = {}
+    Vh = int(np.prod(DIMS)) // 2
+    for prec in ("f16", "bf16", "f32"):
+        P = L.PREC[prec]
+        r = {}
+        for n in (1, 12):
+            fx = L.lqcd_field_create(ctx, P, L.LQCD_ODD, n)
+            fy = L.lqcd_field_create(ctx, P, L.LQCD_EVEN, n)
+            fz = L.lqcd_field_create(ctx, P, L.LQCD_ODD, n)
+            L.lqcd_field_import(ctx, fx, np.ascontiguousarray(np.broadcast_to(psi, (n,) + psi.shape)))
+            f = lambda: L.lqcd_apply(ctx, L.LQCD_OP_MHAT, 12, fz, fx)
+            for _ in range(5):
+                f()
+            ms = time_ms(torch, f, max(10, steps // (4 * n)), stream)
+            for g in (fx, fy, fz):
+                L.lqcd_field_destroy(g)
+            bpr = mhat_bytes_per_rhs(prec, 12, n)
+            r[f"nrhs{n}"] = {"ms": ms, "ms_per_rhs": ms / n, "bytes_per_site_rhs": bpr,
+                             "GBps": n * Vh * bpr / (ms * 1e-3) / 1e9}
+        r["speedup_per_rhs"] = r["nrhs1"]["ms"] / r["nrhs12"]["ms_per_rhs"]
+        out[prec] = r
+    return out
 
 
 def run_solve_only(args):
@@ -687,13 +799,22 @@ def run_gpu(args, rank, world, local_rank):
     need_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
     oracle_AAi = oracle_setup(U) if need_oracle else None
     solve = None
+    mrhs = None
+    if world == 1:
+        mrhs = mrhs_mhat(L, torch, ctx, psi, stream, args.steps)
+    solve = None
+    solve_head = None
     if not args.no_solve and world == 1:
         solve = run_solves(L, torch, lat, U, rank, need_oracle, oracle_AAi)
         solve["schur_forms_rough_field"] = run_schur_rough(L, torch, stream, need_oracle)
+        solve_head = {"lattice_32x32x32x64": headline(solve)}
+        if not args.no_config3:
+            solve["lattice_48x48x48x96"] = run_config3(L, torch, stream, need_oracle)
+            solve_head["lattice_48x48x48x96"] = headline(solve["lattice_48x48x48x96"])
     multi = None
     if not args.no_batch and world == 1:
         multi = {"point_sources_32x32x32x64": run_multi_rhs(L, torch, lat, U, need_oracle, oracle_AAi),
-                 "batch_24_lattices": run_batch(L, torch, stream)}
+                 "batch_24_lattices": run_batch(L, torch, stream, need_oracle)}
     cpu = None
     if need_oracle:
         rate, nsl, dt = oracle_slab_rate(U, oracle_AAi[0], oracle_AAi[1], psi)
@@ -710,9 +831,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "prec": "f32", "recon": 12, "nrhs": 1,
-                   "kappa": KAPPA, "c_sw": CSW, "eps": EPS, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: each step streams ~1.2 GB (links 403 MB, clover 604 MB, spinors)"},
+        "config": bench_config(world),
         "pct_of_peak": 100.0 * gbs / world / peak,
         # the literature's "no-reuse" convention (8 neighbour spinors read per site; K2a 1536 B,
         # K2b 1632 B for FP32 12-real) and the flop rate, for comparison with published tables
@@ -729,6 +848,8 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "solve_headline": solve_head,
+        "multi_rhs_mhat_32x32x32x64": mrhs,
         "solve": solve,
         "multi_rhs_and_batch": multi,
     }
@@ -745,6 +866,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 48^3x96 solve comparison")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],

@@ -294,7 +294,9 @@ typedef struct {
   lqcd_prec high;    /* arithmetic of the FP64 parts (the low-mode filter once it leaves   */
                      /* FP32, the FP64 sign function and so D_ov, its CG and the mixed   */
                      /* CG's reliable updates): LQCD_F64 (0, the default) or LQCD_DF64;  */
-                     /* fields, projections and Gram matrices stay FP64 either way       */
+                     /* fields stay FP64 either way; Gram matrices, rotations and the    */
+                     /* sign function's low-mode projection accumulate in double-float  */
+                     /* (~2^-44 relative) in both cases                                  */
   int eig_method;    /* low-mode solver on H_W^2: LQCD_EIG_SUBSPACE (0, the default:      */
                      /* block subspace iteration with a Chebyshev filter; max_filter caps */
                      /* its sweeps) or LQCD_EIG_LANCZOS (thick-restart Lanczos, one      */
@@ -334,9 +336,16 @@ typedef enum {
  * Chebyshev filtering, or thick-restart Lanczos on H_W^2, per
  * params->eig_method; then Rayleigh-Ritz in H_W) and the Chebyshev
  * coefficients for the sign function, and keep them in the context.  Needs
- * the gauge field.  Blocks.  LQCD_ERR_NOCONV if the low modes do not reach
- * eig_tol within max_filter sweeps or restarts (info is filled either way);
- * LQCD_ERR_ARG for a lattice too small for the requested modes. */
+ * the gauge field.  Blocks.  The tolerance holds for H_W itself: after the
+ * final Rayleigh-Ritz step every returned mode's ||H_W v - lambda v|| is
+ * checked against eig_tol, and while one exceeds it the H_W^2 target is
+ * tightened and the block iteration continues (after the Lanczos method, on
+ * its Ritz vectors padded to a full block).  LQCD_ERR_NOCONV if the modes do
+ * not reach eig_tol within max_filter sweeps or restarts (info is filled
+ * either way); the context then holds no usable overlap state
+ * (lqcd_overlap and lqcd_overlap_lowmodes return LQCD_ERR_STATE until a
+ * set-up succeeds).  LQCD_ERR_ARG for a lattice too small for the requested
+ * modes. */
 lqcd_status lqcd_overlap_setup(lqcd_ctx *ctx, const lqcd_overlap_params *params, lqcd_overlap_info *info);
 
 /* Copy the n_low low-mode vectors (canonical, n_low fields back to back,

@@ -8,9 +8,10 @@
 //    orthonormalises the block by Cholesky QR (twice), and does a
 //    Rayleigh-Ritz step with H_W^2; once the wanted vectors have converged,
 //    a Rayleigh-Ritz step with H_W in their span fixes the signs of the
-//    eigenvalues.  The block inner products and rotations are plain GEMMs
-//    (cuBLAS ZGEMM); the m x m Hermitian eigenproblem (m <= 96) is solved on
-//    the host by cyclic Jacobi rotations.
+//    eigenvalues.  The block inner products (Gram matrices) and rotations are
+//    own tiled kernels accumulating in double-float on the FP32 pipes (GB300
+//    runs FP64 multiply-adds at 1/64 of its FP32 rate); the m x m Hermitian
+//    eigenproblem (m <= 96) is solved on the host by cyclic Jacobi rotations.
 //  * Sign function: exact low modes plus H_W P(H_W^2) on their complement,
 //    P the Chebyshev interpolant of 1/sqrt(y) on [a, b], evaluated by the
 //    Clenshaw recurrence b_k = c_k w + 2 T b_{k+1} - b_{k+2},
@@ -19,7 +20,6 @@
 //    adds the three-term update in its epilogue (MODE_CHEB).
 //  * D_ov(m) = f (1 + g5 eps) + m with f = (1 - m/(2 rho)) rho, and CG on its
 //    normal equations for the inverse.
-#include <cublas_v2.h>
 
 #include <algorithm>
 #include <chrono>
@@ -47,10 +47,11 @@ struct OverlapState {
   std::vector<double> coef32;  // the FP32 one inside the mixed CG: to max(sign_tol, 1e-6)
   double a = 0, b = 0;
   int degree = 0, degree32 = 0;
-  cublasHandle_t blas = nullptr;
   bool df = false;            // FP64 parts computed in double-float (prm.high == LQCD_DF64)
   double2 *dsmall = nullptr;  // device scratch for small matrices
   size_t dsmall_n = 0;
+  double *gpart = nullptr;  // per-chunk partials of the Gram kernel
+  size_t gpart_n = 0;
 };
 
 void overlap_free(lqcd_ctx *c) {
@@ -58,7 +59,7 @@ void overlap_free(lqcd_ctx *c) {
   if (!s) return;
   if (s->vecs) lqcd_field_destroy(s->vecs);
   if (s->vecs32) lqcd_field_destroy(s->vecs32);
-  if (s->blas) cublasDestroy(s->blas);
+  if (s->gpart) cudaFree(s->gpart);
   if (s->dsmall) cudaFree(s->dsmall);
   delete s;
   c->ov = nullptr;
@@ -69,6 +70,8 @@ namespace {
 constexpr int kT = 256;
 // accuracy of the FP32 sign function of the mixed overlap CG (its rounding level)
 constexpr double kInnerSignTol = 1e-6;
+// widest low-mode block (the rotation kernel holds this many rows of its matrix)
+constexpr int kOvMaxBlock = 96;
 // Low-mode block size m = max(want + 16, LQCD_OV_BLOCK_MULT * want), capped at
 // 96.  Measured on 16^3x32 (20 modes, |lambda| 0.509-0.510 clustered, DF64
 // sweeps): m = 40: 214 sweeps, 84 s; m = 60: 191 sweeps, 114 s; m = 96: 143
@@ -193,18 +196,8 @@ __global__ void scale_rows_kernel(C2 *m, int rows, int cols, const double *s) {
 
 // ---- host helpers ------------------------------------------------------------
 
-lqcd_status blas_ok(cublasStatus_t s, const char *what) {
-  return s == CUBLAS_STATUS_SUCCESS ? LQCD_OK : set_error(LQCD_ERR_CUDA, "%s failed (cuBLAS status %d)", what, (int)s);
-}
-
 lqcd_status ensure_state(lqcd_ctx *c) {
   if (!c->ov) c->ov = new OverlapState();
-  OverlapState &s = *c->ov;
-  if (!s.blas) {
-    if (cublasCreate(&s.blas) != CUBLAS_STATUS_SUCCESS) return set_error(LQCD_ERR_CUDA, "cublasCreate failed");
-  }
-  if (cublasSetStream(s.blas, c->stream) != CUBLAS_STATUS_SUCCESS)
-    return set_error(LQCD_ERR_CUDA, "cublasSetStream failed");
   return LQCD_OK;
 }
 
@@ -230,49 +223,203 @@ void *col(const lqcd_field *f, int p, int k) {
   return reinterpret_cast<char *>(f->data[p]) + (size_t)k * cwords(f) * celem(f);
 }
 
-// C(p x q) = X^H Y over both parities (X: first p RHS of fx, Y: first q RHS of
-// fy, same precision), C on the device as double2 (FP64) or float2 (FP32)
-lqcd_status gram(lqcd_ctx *c, const lqcd_field *fx, int p, const lqcd_field *fy, int q, void *C) {
-  OverlapState &s = *c->ov;
-  const int N = (int)cwords(fx);
-  for (int par = 0; par < 2; par++) {
-    if (fx->prec == LQCD_F64) {
-      const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
-      LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one,
-                                 (const cuDoubleComplex *)col(fx, par, 0), N, (const cuDoubleComplex *)col(fy, par, 0),
-                                 N, par ? &one : &zero, (cuDoubleComplex *)C, p),
-                     "ZGEMM (Gram)"));
-    } else {
-      const cuComplex one = make_cuComplex(1, 0), zero = make_cuComplex(0, 0);
-      LQ_TRY(blas_ok(cublasCgemm(s.blas, CUBLAS_OP_C, CUBLAS_OP_N, p, q, N, &one, (const cuComplex *)col(fx, par, 0), N,
-                                 (const cuComplex *)col(fy, par, 0), N, par ? &one : &zero, (cuComplex *)C, p),
-                     "CGEMM (Gram)"));
+// ---- block inner products and rotations ---------------------------------------
+// Own kernels for the two dense products of the low-mode solver and of the
+// sign function's projection: C = X^H Y (Gram) and Z = alpha X M + beta Z
+// (rotation), X, Y, Z columns of FULL fields (both parities; complex numbers
+// as double2 for FP64, float2 for FP32 fields).  Products accumulate in
+// double-float (compensated, ~2^-44 relative) on the FP32 pipes: an FP64
+// inner product would run at GB300's 1/64 FP64 rate.  Every input is
+// converted to double-float once per shared-memory tile or per rotation
+// column tile, not per product.
+struct cdf {
+  df re, im;
+};
+__device__ __forceinline__ cdf to_cdf(double2 v) { return cdf{df(v.x), df(v.y)}; }
+__device__ __forceinline__ cdf to_cdf(float2 v) { return cdf{df(v.x), df(v.y)}; }
+__device__ __forceinline__ void from_cdf(double2 &o, cdf a) { o = make_double2((double)a.re, (double)a.im); }
+__device__ __forceinline__ void from_cdf(float2 &o, cdf a) {
+  o = make_float2(__fadd_rn(a.re.hi, a.re.lo), __fadd_rn(a.im.hi, a.im.lo));
+}
+
+constexpr int kGT = 16;    // edge of the C tile of one Gram block
+constexpr int kGE = 32;    // elements per shared-memory step
+constexpr int kRQ = 16;    // Z columns per rotation thread
+constexpr int kRMaxP = 96; // rows of M a rotation block holds
+
+// partials of C = X^H Y: block (tile, chunk) sums elements [chunk * per, ...)
+// of both parities (e < n parity 0, e - n parity 1) for a kGT x kGT tile of C
+template <typename E>
+__global__ void __launch_bounds__(kGT * kGT) ov_gram_kernel(const E *X0, const E *X1, const E *Y0, const E *Y1, long ld,
+                                                             long n, int p, int q, int tiles_i, long per,
+                                                             double *part) {
+  __shared__ cdf sx[kGE][kGT], sy[kGE][kGT];
+  const int nch = gridDim.y, chunk = blockIdx.y;
+  const int i0 = (blockIdx.x % tiles_i) * kGT, j0 = (blockIdx.x / tiles_i) * kGT;
+  const int ti = threadIdx.x % kGT, tj = threadIdx.x / kGT;
+  const long e_beg = (long)chunk * per, e_end = min(2 * n, e_beg + per);
+  dfacc re{0.0f, 0.0f}, im{0.0f, 0.0f};
+  const cdf zero{df(0.0f, 0.0f), df(0.0f, 0.0f)};
+  for (long e0 = e_beg; e0 < e_end; e0 += kGE) {
+    for (int l = threadIdx.x; l < kGE * kGT; l += kGT * kGT) {
+      const int ee = l % kGE, cc = l / kGE;
+      const long e = e0 + ee;
+      cdf vx = zero, vy = zero;
+      if (e < e_end) {
+        const long off = e < n ? e : e - n;
+        if (i0 + cc < p) vx = to_cdf((e < n ? X0 : X1)[(long)(i0 + cc) * ld + off]);
+        if (j0 + cc < q) vy = to_cdf((e < n ? Y0 : Y1)[(long)(j0 + cc) * ld + off]);
+      }
+      sx[ee][cc] = vx;
+      sy[ee][cc] = vy;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ee = 0; ee < kGE; ee++) {
+      const cdf x = sx[ee][ti], y = sy[ee][tj];
+      dfacc_madd(re, x.re, y.re);  // conj(x) y
+      dfacc_madd(re, x.im, y.im);
+      dfacc_madd(im, x.re, y.im);
+      dfacc_madd(im, -x.im, y.re);
+    }
+    __syncthreads();
+  }
+  const int i = i0 + ti, j = j0 + tj;
+  if (i < p && j < q) {
+    const long k = (long)i + (long)p * j;
+    part[(2 * k) * nch + chunk] = (double)dfacc_value(re);
+    part[(2 * k + 1) * nch + chunk] = (double)dfacc_value(im);
+  }
+}
+
+// C[k] = the sum of its chunk partials, in chunk order (deterministic)
+template <typename CE> __global__ void ov_gram_finish_kernel(const double *part, int nch, int pq, CE *C) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= pq) return;
+  double re = 0.0, im = 0.0;
+  for (int ch = 0; ch < nch; ch++) {
+    re += part[(2L * k) * nch + ch];
+    im += part[(2L * k + 1) * nch + ch];
+  }
+  if constexpr (std::is_same<CE, double2>::value)
+    C[k] = make_double2(re, im);
+  else
+    C[k] = make_float2((float)re, (float)im);
+}
+
+// Z[:, q0 + c] = alpha sum_l X[:, l] M[l, q0 + c] + beta Z[:, q0 + c] for kRQ columns
+// per block row; grid (element chunks, column tiles), grid-stride over elements
+template <typename E>
+__global__ void __launch_bounds__(128) ov_rotate_kernel(const E *X0, const E *X1, long ld, long n, int p, const E *M,
+                                                         int q, E *Z0, E *Z1, double alpha, double beta) {
+  __shared__ cdf ms[kRMaxP][kRQ];
+  const int q0 = blockIdx.y * kRQ;
+  const cdf zero{df(0.0f, 0.0f), df(0.0f, 0.0f)};
+  for (int l = threadIdx.x; l < p * kRQ; l += blockDim.x) {
+    const int r = l / kRQ, cc = l % kRQ;
+    ms[r][cc] = q0 + cc < q ? to_cdf(M[r + (long)p * (q0 + cc)]) : zero;
+  }
+  __syncthreads();
+  const df al((float)alpha), be((float)beta);
+  const int nq = min(kRQ, q - q0);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += (long)gridDim.x * blockDim.x) {
+    const E *Xp = e < n ? X0 : X1;
+    E *Zp = e < n ? Z0 : Z1;
+    const long off = e < n ? e : e - n;
+    dfacc re[kRQ], im[kRQ];
+#pragma unroll
+    for (int cc = 0; cc < kRQ; cc++) re[cc] = im[cc] = dfacc{0.0f, 0.0f};
+    for (int l = 0; l < p; l++) {
+      const cdf x = to_cdf(Xp[(long)l * ld + off]);
+#pragma unroll
+      for (int cc = 0; cc < kRQ; cc++) {
+        const cdf m = ms[l][cc];
+        dfacc_madd(re[cc], x.re, m.re);
+        dfacc_madd(re[cc], -x.im, m.im);
+        dfacc_madd(im[cc], x.re, m.im);
+        dfacc_madd(im[cc], x.im, m.re);
+      }
+    }
+#pragma unroll
+    for (int cc = 0; cc < kRQ; cc++) {
+      if (cc >= nq) break;
+      E &z = Zp[(long)(q0 + cc) * ld + off];
+      cdf v{al * dfacc_value(re[cc]), al * dfacc_value(im[cc])};
+      if (beta != 0.0) {
+        const cdf zo = to_cdf(z);
+        v.re = fma(be, zo.re, v.re);
+        v.im = fma(be, zo.im, v.im);
+      }
+      from_cdf(z, v);
     }
   }
+}
+
+lqcd_status gram_partials(lqcd_ctx *c, size_t n, double **p) {
+  OverlapState &s = *c->ov;
+  if (s.gpart_n < n) {
+    if (s.gpart) {
+      LQ_CU(cudaStreamSynchronize(c->stream));
+      cudaFree(s.gpart);
+      s.gpart = nullptr;
+    }
+    LQ_CU(dev_malloc((void **)&s.gpart, n * sizeof(double)));
+    s.gpart_n = n;
+  }
+  *p = s.gpart;
   return LQCD_OK;
 }
 
-// Z = alpha X M + beta Z (X: N x p block of fx, M: p x q on the device, Z: N x q block of fz)
-lqcd_status rotate(lqcd_ctx *c, const lqcd_field *fx, int p, const void *M, int q, lqcd_field *fz, zc alpha,
-                   zc beta) {
-  OverlapState &s = *c->ov;
-  const int N = (int)cwords(fx);
-  for (int par = 0; par < 2; par++) {
-    if (fx->prec == LQCD_F64) {
-      const cuDoubleComplex al = make_cuDoubleComplex(alpha.real(), alpha.imag());
-      const cuDoubleComplex be = make_cuDoubleComplex(beta.real(), beta.imag());
-      LQ_TRY(blas_ok(cublasZgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al,
-                                 (const cuDoubleComplex *)col(fx, par, 0), N, (const cuDoubleComplex *)M, p, &be,
-                                 (cuDoubleComplex *)col(fz, par, 0), N),
-                     "ZGEMM (rotation)"));
-    } else {
-      const cuComplex al = make_cuComplex((float)alpha.real(), (float)alpha.imag());
-      const cuComplex be = make_cuComplex((float)beta.real(), (float)beta.imag());
-      LQ_TRY(blas_ok(cublasCgemm(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, N, q, p, &al, (const cuComplex *)col(fx, par, 0), N,
-                                 (const cuComplex *)M, p, &be, (cuComplex *)col(fz, par, 0), N),
-                     "CGEMM (rotation)"));
-    }
+// C(p x q) = X^H Y over both parities (X: first p RHS of fx, Y: first q RHS of
+// fy, same precision), C on the device as double2 (FP64) or float2 (FP32)
+lqcd_status gram(lqcd_ctx *c, const lqcd_field *fx, int p, const lqcd_field *fy, int q, void *C) {
+  if (fx->prec != fy->prec || (fx->prec != LQCD_F64 && fx->prec != LQCD_F32))
+    return set_error(LQCD_ERR_ARG, "Gram of fields of precisions %d, %d", (int)fx->prec, (int)fy->prec);
+  const long n = cwords(fx);
+  const int ti = (p + kGT - 1) / kGT, tq = (q + kGT - 1) / kGT;
+  // about four blocks per SM over all tiles, chunks of whole shared-memory steps
+  const int nch = (int)std::max<long>(1, std::min<long>(64, (4 * 152 + ti * tq - 1) / (ti * tq)));
+  const long per = ((2 * n + nch - 1) / nch + kGE - 1) / kGE * kGE;
+  double *part;
+  LQ_TRY(gram_partials(c, 2 * (size_t)p * q * nch, &part));
+  const dim3 grid((unsigned)(ti * tq), (unsigned)nch);
+  if (fx->prec == LQCD_F64) {
+    ov_gram_kernel<double2><<<grid, kGT * kGT, 0, c->stream>>>(
+        (const double2 *)fx->data[0], (const double2 *)fx->data[1], (const double2 *)fy->data[0],
+        (const double2 *)fy->data[1], n, n, p, q, ti, per, part);
+    LQ_CU(cudaGetLastError());
+    ov_gram_finish_kernel<double2><<<(p * q + 127) / 128, 128, 0, c->stream>>>(part, nch, p * q, (double2 *)C);
+  } else {
+    ov_gram_kernel<float2><<<grid, kGT * kGT, 0, c->stream>>>(
+        (const float2 *)fx->data[0], (const float2 *)fx->data[1], (const float2 *)fy->data[0],
+        (const float2 *)fy->data[1], n, n, p, q, ti, per, part);
+    LQ_CU(cudaGetLastError());
+    ov_gram_finish_kernel<float2><<<(p * q + 127) / 128, 128, 0, c->stream>>>(part, nch, p * q, (float2 *)C);
   }
+  LQ_CU(cudaGetLastError());
+  return LQCD_OK;
+}
+
+// Z = alpha X M + beta Z (X: N x p block of fx, M: p x q on the device, Z: N x q block of fz;
+// alpha, beta real, fz not overlapping fx)
+lqcd_status rotate(lqcd_ctx *c, const lqcd_field *fx, int p, const void *M, int q, lqcd_field *fz, double alpha,
+                   double beta) {
+  if (fx->prec != fz->prec || (fx->prec != LQCD_F64 && fx->prec != LQCD_F32))
+    return set_error(LQCD_ERR_ARG, "rotation of fields of precisions %d, %d", (int)fx->prec, (int)fz->prec);
+  if (p > kRMaxP) return set_error(LQCD_ERR_ARG, "rotation of %d > %d columns", p, kRMaxP);
+  const long n = cwords(fx);
+  const int tq = (q + kRQ - 1) / kRQ;
+  const long chunks = std::max<long>(1, std::min<long>((2 * n + 127) / 128, (8L * 152 + tq - 1) / tq));
+  const dim3 grid((unsigned)chunks, (unsigned)tq);
+  if (fx->prec == LQCD_F64)
+    ov_rotate_kernel<double2><<<grid, 128, 0, c->stream>>>(
+        (const double2 *)fx->data[0], (const double2 *)fx->data[1], n, n, p, (const double2 *)M, q,
+        (double2 *)fz->data[0], (double2 *)fz->data[1], alpha, beta);
+  else
+    ov_rotate_kernel<float2><<<grid, 128, 0, c->stream>>>((const float2 *)fx->data[0], (const float2 *)fx->data[1], n,
+                                                          n, p, (const float2 *)M, q, (float2 *)fz->data[0],
+                                                          (float2 *)fz->data[1], alpha, beta);
+  LQ_CU(cudaGetLastError());
   return LQCD_OK;
 }
 
@@ -1248,7 +1395,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   // the block holds the wanted modes plus a margin wide enough to contain a
   // near-degenerate cluster at the edge (smooth fields keep the free field's
   // 12-fold momentum multiplets almost degenerate)
-  int m = std::min<long>(std::max(want + 16, LQCD_OV_BLOCK_MULT * want), 96);
+  int m = std::min<long>(std::max(want + 16, LQCD_OV_BLOCK_MULT * want), kOvMaxBlock);
   if (m > N) m = (int)N;
   if (want >= m) return set_error(LQCD_ERR_ARG, "lattice too small for %d low modes", want);
   FieldGuard g;
@@ -1270,150 +1417,151 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   int sweep = 0, kneed = want;
   long applies = 0;  // H_W applications, one per right-hand side
   bool converged = false;
-  if (prm->eig_method == LQCD_EIG_LANCZOS) {
-    // restart size m (the block of the subspace method), basis of up to 2m
-    const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
-    if (mmax < m + 8) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", m + 8);
-    LanczosResult lr;
-    LQ_TRY(lowmodes_lanczos(c, prm, want, m, mmax, X, g, lr));
-    kneed = lr.kneed;
-    sweep = lr.cycles - 1;
-    applies = lr.applies;
-    converged = lr.converged;
-  } else {
-  {
-    const long nd = 2L * cwords(X) * m;  // doubles per parity block
-    for (int p = 0; p < 2; p++) {
-      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)X->data[p], nd,
-                                                                                   prm->seed * 2 + p + 1);
-      LQ_CU(cudaGetLastError());
-    }
-  }
-  LQ_TRY(orthonormalise(c, X, T, m));
   bool fp32_phase = true;
   int fp32_stall = 0;
   double prev_worst = 1e300;
   lqcd_field *Bs[4] = {nullptr, nullptr, nullptr, nullptr};  // FP32 filter block
   lqcd_field *Bd[4] = {nullptr, nullptr, nullptr, nullptr};  // double-float filter block
-  for (;; sweep++) {
-    // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
-    // extremal problem; Rayleigh-Ritz with H_W itself would be an interior one
-    // and produce spurious Ritz values near zero)
-    LQ_TRY(hw(c, m, HX, X));
-    LQ_TRY(small_scratch(c, (size_t)m * m, &d));
-    LQ_TRY(gram(c, HX, m, HX, m, d));
-    std::vector<zc> W, Q;
-    LQ_TRY(to_host(c, d, (size_t)m * m, W));
-    for (int j = 0; j < m; j++)  // symmetrise
-      for (int i = 0; i < j; i++) {
-        const zc avg = 0.5 * (W[i + (size_t)m * j] + std::conj(W[j + (size_t)m * i]));
-        W[i + (size_t)m * j] = avg;
-        W[j + (size_t)m * i] = std::conj(avg);
-      }
-    std::vector<double> mu;
-    jacobi_eigh(m, W, Q, mu);
-    // ascending order of mu
-    order.resize(m);
-    for (int i = 0; i < m; i++) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] < mu[y]; });
-    std::vector<zc> Qs((size_t)m * m);
-    std::vector<double> mus(m);
-    for (int jj = 0; jj < m; jj++) {
-      mus[jj] = mu[order[jj]];
-      for (int i = 0; i < m; i++) Qs[i + (size_t)m * jj] = Q[i + (size_t)m * order[jj]];
-    }
-    LQ_TRY(to_dev(c, Qs, d));
-    LQ_TRY(rotate(c, X, m, d, m, T, 1.0, 0.0));
-    LQ_TRY(rotate(c, HX, m, d, m, Y, 1.0, 0.0));
-    std::swap(X, T);
-    std::swap(HX, Y);
-    // residuals of H_W^2: || H_W (H_W x) - mu x ||
-    LQ_TRY(hw(c, m, Z, HX));
-    std::vector<double> neg(m), r2;
-    for (int i = 0; i < m; i++) neg[i] = -mus[i];
-    LQ_TRY(axpy_norms(c, Z, X, neg, m, r2));
-    applies += 2L * m;
-    // converge the wanted vectors and every vector nearly degenerate with the
-    // edge of the wanted set (a near-degenerate +-lambda partner left outside
-    // would stay mixed into a wanted vector)
-    kneed = want;
-    while (kneed < m - 4 && mus[kneed] <= 1.01 * mus[want - 1]) kneed++;
-    converged = true;
-    for (int i = 0; i < kneed; i++) converged &= std::sqrt(r2[i]) <= prm->eig_tol;
-    theta = mus;
-    if (converged || sweep + 1 >= prm->max_filter) break;
-    // Chebyshev filter of H_W^2 damping [mu_max, bmax], in FP32 while the
-    // residuals are far above the FP32 noise floor, in FP64 afterwards
-    double worst = 0;
-    for (int i = 0; i < kneed; i++) worst = std::max(worst, std::sqrt(r2[i]));
-    // FP32 filtering injects ~1e-7 relative noise: use it only while the
-    // residuals are large and still falling, FP64 from then on
-#if LQCD_OV_FP32_RULE == 0
-    if (fp32_phase && (worst < 1e-4 || worst > 0.5 * prev_worst)) fp32_phase = false;
-#else
-    // FP32 filtering injects ~1e-7 relative noise (a floor of ~1e-5 on the
-    // H_W^2 residuals, |H_W^2| ~ 42): keep it while the residuals are above
-    // 1e-4 and not stuck on that floor (three sweeps in a row without a 1 %
-    // drop end it; slow progress while an edge eigenvalue settles does not)
-    fp32_stall = worst > 0.99 * prev_worst ? fp32_stall + 1 : 0;
-    if (fp32_phase && (worst < 1e-4 || fp32_stall >= 3)) fp32_phase = false;
-#endif
-    if (kOvTrace)
-      std::fprintf(stderr, "lqcd overlap: sweep %d worst %.3e kneed %d mu[kneed-1] %.6f mu[m-1] %.6f %s\n", sweep,
-                   worst, kneed, mus[kneed - 1], mus[m - 1], fp32_phase ? "fp32" : (S.df ? "df64" : "fp64"));
-    prev_worst = worst;
-    const bool low = fp32_phase;
-    const double lo = std::min(std::max(mus[m - 1], 1.02 * mus[kneed - 1]), 0.9 * bmax), hi = bmax;
-    const double s2 = 2.0 / (hi - lo), s0 = -(hi + lo) / (hi - lo);
-    const int deg = 16;
-    // the filter runs on a copy of X in FP32 (early sweeps) or double-float
-    // (on request), in place in FP64 otherwise
-    const lqcd_prec fp = low ? LQCD_F32 : S.df ? LQCD_DF64 : LQCD_F64;
-    lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T;
-    if (fp != LQCD_F64) {
-      lqcd_field **blk = fp == LQCD_F32 ? Bs : Bd;
-      if (!blk[0]) {
-        for (int q = 0; q < 4; q++) {
-          LQ_TRY(lqcd_field_create(c, fp, LQCD_FULL, m, &blk[q]));
-          g.f.push_back(blk[q]);
+  // Block subspace sweeps on X (m orthonormal columns) until the kneed wanted
+  // (and edge-degenerate) vectors have H_W^2 residuals <= tol2, or the sweep
+  // budget is spent.  `cut` reports a near-degenerate cluster at the edge of
+  // the wanted set that fills the block up to its margin (and so may extend
+  // beyond it): the block must grow before the H_W Rayleigh-Ritz step, which
+  // is exact only on a union of whole clusters (an incomplete one is not
+  // H_W-invariant and gives spurious interior Ritz values).
+  bool cut = false;
+  auto sweeps = [&](double tol2) -> lqcd_status {
+    cut = false;
+    for (;; sweep++) {
+      // Rayleigh-Ritz with H_W^2 (the wanted eigenvalues are its smallest, an
+      // extremal problem; Rayleigh-Ritz with H_W itself would be an interior one
+      // and produce spurious Ritz values near zero)
+      LQ_TRY(hw(c, m, HX, X));
+      LQ_TRY(small_scratch(c, (size_t)m * m, &d));
+      LQ_TRY(gram(c, HX, m, HX, m, d));
+      std::vector<zc> W, Q;
+      LQ_TRY(to_host(c, d, (size_t)m * m, W));
+      for (int j = 0; j < m; j++)  // symmetrise
+        for (int i = 0; i < j; i++) {
+          const zc avg = 0.5 * (W[i + (size_t)m * j] + std::conj(W[j + (size_t)m * i]));
+          W[i + (size_t)m * j] = avg;
+          W[j + (size_t)m * i] = std::conj(avg);
         }
+      std::vector<double> mu;
+      jacobi_eigh(m, W, Q, mu);
+      // ascending order of mu
+      order.resize(m);
+      for (int i = 0; i < m; i++) order[i] = i;
+      std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] < mu[y]; });
+      std::vector<zc> Qs((size_t)m * m);
+      std::vector<double> mus(m);
+      for (int jj = 0; jj < m; jj++) {
+        mus[jj] = mu[order[jj]];
+        for (int i = 0; i < m; i++) Qs[i + (size_t)m * jj] = Q[i + (size_t)m * order[jj]];
       }
-      LQ_TRY(convert_full(c, blk[0], X, m));
-      fX = blk[0], fY = blk[1], fH = blk[2], fT = blk[3];
+      LQ_TRY(to_dev(c, Qs, d));
+      LQ_TRY(rotate(c, X, m, d, m, T, 1.0, 0.0));
+      LQ_TRY(rotate(c, HX, m, d, m, Y, 1.0, 0.0));
+      std::swap(X, T);
+      std::swap(HX, Y);
+      // residuals of H_W^2: || H_W (H_W x) - mu x ||
+      LQ_TRY(hw(c, m, Z, HX));
+      std::vector<double> neg(m), r2;
+      for (int i = 0; i < m; i++) neg[i] = -mus[i];
+      LQ_TRY(axpy_norms(c, Z, X, neg, m, r2));
+      applies += 2L * m;
+      // converge the wanted vectors and every vector nearly degenerate with the
+      // edge of the wanted set (a near-degenerate +-lambda partner left outside
+      // would stay mixed into a wanted vector)
+      kneed = want;
+      while (kneed < m - 4 && mus[kneed] <= 1.01 * mus[want - 1]) kneed++;
+      bool done = true;
+      for (int i = 0; i < kneed; i++) done &= std::sqrt(r2[i]) <= tol2;
+      theta = mus;
+      double worst = 0;
+      for (int i = 0; i < kneed; i++) worst = std::max(worst, std::sqrt(r2[i]));
+      // once the Ritz values mean something, a cluster reaching the margin
+      // asks for a wider block
+      if (m < kOvMaxBlock && kneed == m - 4 && mus[kneed] <= 1.01 * mus[want - 1] && worst < 1e-2) {
+        cut = true;
+        sweep++;
+        return LQCD_OK;
+      }
+      if (done || sweep + 1 >= prm->max_filter) {
+        sweep++;
+        return LQCD_OK;
+      }
+      // Chebyshev filter of H_W^2 damping [mu_max, bmax], in FP32 while the
+      // residuals are far above the FP32 noise floor, in FP64 afterwards
+      // FP32 filtering injects ~1e-7 relative noise: use it only while the
+      // residuals are large and still falling, FP64 from then on
+#if LQCD_OV_FP32_RULE == 0
+      if (fp32_phase && (worst < 1e-4 || worst > 0.5 * prev_worst)) fp32_phase = false;
+#else
+      // FP32 filtering injects ~1e-7 relative noise (a floor of ~1e-5 on the
+      // H_W^2 residuals, |H_W^2| ~ 42): keep it while the residuals are above
+      // 1e-4 and not stuck on that floor (three sweeps in a row without a 1 %
+      // drop end it; slow progress while an edge eigenvalue settles does not)
+      fp32_stall = worst > 0.99 * prev_worst ? fp32_stall + 1 : 0;
+      if (fp32_phase && (worst < 1e-4 || fp32_stall >= 3)) fp32_phase = false;
+#endif
+      if (kOvTrace)
+        std::fprintf(stderr, "lqcd overlap: sweep %d worst %.3e kneed %d mu[kneed-1] %.6f mu[m-1] %.6f %s\n", sweep,
+                     worst, kneed, mus[kneed - 1], mus[m - 1], fp32_phase ? "fp32" : (S.df ? "df64" : "fp64"));
+      prev_worst = worst;
+      const bool low = fp32_phase;
+      const double lo = std::min(std::max(mus[m - 1], 1.02 * mus[kneed - 1]), 0.9 * bmax), hi = bmax;
+      const double s2 = 2.0 / (hi - lo), s0 = -(hi + lo) / (hi - lo);
+      const int deg = 16;
+      // the filter runs on a copy of X in FP32 (early sweeps) or double-float
+      // (on request), in place in FP64 otherwise
+      const lqcd_prec fp = low ? LQCD_F32 : S.df ? LQCD_DF64 : LQCD_F64;
+      lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T;
+      if (fp != LQCD_F64) {
+        lqcd_field **blk = fp == LQCD_F32 ? Bs : Bd;
+        if (!blk[0]) {
+          for (int q = 0; q < 4; q++) {
+            LQ_TRY(lqcd_field_create(c, fp, LQCD_FULL, m, &blk[q]));
+            g.f.push_back(blk[q]);
+          }
+        }
+        LQ_TRY(convert_full(c, blk[0], X, m));
+        fX = blk[0], fY = blk[1], fH = blk[2], fT = blk[3];
+      }
+      // Y0 = X, Y1 = T(X), Y_{k+1} = 2 T(Y_k) - Y_{k-1} with T = s2 H^2 + s0: the
+      // second H_W of each step carries the update in its epilogue
+      LQ_TRY(hw(c, m, fT, fX));
+      LQ_TRY(hw_cheb(c, m, fY, fT, s2, fX, s0, nullptr, 0.0, nullptr, 0.0));
+      lqcd_field *prev = fX, *cur = fY, *nxt = fH;
+      for (int k = 1; k < deg; k++) {
+        LQ_TRY(hw(c, m, fT, cur));
+        LQ_TRY(hw_cheb(c, m, nxt, fT, 2.0 * s2, cur, 2.0 * s0, prev, -1.0, nullptr, 0.0));
+        lqcd_field *t = prev;
+        prev = cur;
+        cur = nxt;
+        nxt = t;
+      }
+      applies += 2L * deg * m;
+      if (fp != LQCD_F64) {
+        LQ_TRY(convert_full(c, X, cur, m));
+      } else if (cur != X) {  // the filtered block becomes X; the other two are scratch
+        lqcd_field *others[3] = {X, Y, HX};
+        lqcd_field *rest[2];
+        int r = 0;
+        for (auto *o : others)
+          if (o != cur) rest[r++] = o;
+        X = cur;
+        Y = rest[0];
+        HX = rest[1];
+      }
+      LQ_TRY(orthonormalise(c, X, T, m));
     }
-    // Y0 = X, Y1 = T(X), Y_{k+1} = 2 T(Y_k) - Y_{k-1} with T = s2 H^2 + s0: the
-    // second H_W of each step carries the update in its epilogue
-    LQ_TRY(hw(c, m, fT, fX));
-    LQ_TRY(hw_cheb(c, m, fY, fT, s2, fX, s0, nullptr, 0.0, nullptr, 0.0));
-    lqcd_field *prev = fX, *cur = fY, *nxt = fH;
-    for (int k = 1; k < deg; k++) {
-      LQ_TRY(hw(c, m, fT, cur));
-      LQ_TRY(hw_cheb(c, m, nxt, fT, 2.0 * s2, cur, 2.0 * s0, prev, -1.0, nullptr, 0.0));
-      lqcd_field *t = prev;
-      prev = cur;
-      cur = nxt;
-      nxt = t;
-    }
-    applies += 2L * deg * m;
-    if (fp != LQCD_F64) {
-      LQ_TRY(convert_full(c, X, cur, m));
-    } else if (cur != X) {  // the filtered block becomes X; the other two are scratch
-      lqcd_field *others[3] = {X, Y, HX};
-      lqcd_field *rest[2];
-      int r = 0;
-      for (auto *o : others)
-        if (o != cur) rest[r++] = o;
-      X = cur;
-      Y = rest[0];
-      HX = rest[1];
-    }
-    LQ_TRY(orthonormalise(c, X, T, m));
-  }
-  }
+  };
   // Rayleigh-Ritz with H_W in the span of the kneed converged vectors of
-  // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors; the
-  // `want` of smallest |lambda| are kept
-  {
+  // H_W^2 (an invariant subspace of H_W): signed eigenvalues and vectors and
+  // their H_W residuals ||H_W v - lambda v||; returns the largest residual of
+  // the `want` of smallest |lambda|
+  auto final_rr = [&](double &worst_wanted) -> lqcd_status {
     const int k = kneed;
     LQ_TRY(hw(c, k, HX, X));
     applies += k;
@@ -1431,8 +1579,14 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     LQ_TRY(to_dev(c, Q, d));
     LQ_TRY(rotate(c, X, k, d, k, T, 1.0, 0.0));
     LQ_TRY(rotate(c, HX, k, d, k, Y, 1.0, 0.0));
-    std::swap(X, T);
-    std::swap(HX, Y);
+    // the rotated Ritz vectors go back into the first k columns of X (the
+    // rest of the block is untouched, so X stays an orthonormal block)
+    for (int p = 0; p < 2; p++) {
+      LQ_CU(cudaMemcpyAsync(col(X, p, 0), col(T, p, 0), (size_t)k * cwords(X) * 16, cudaMemcpyDeviceToDevice,
+                            c->stream));
+      LQ_CU(cudaMemcpyAsync(col(HX, p, 0), col(Y, p, 0), (size_t)k * cwords(X) * 16, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    }
     std::vector<double> neg(k), r2;
     for (int i = 0; i < k; i++) neg[i] = -theta[i];
     LQ_TRY(axpy_norms(c, HX, X, neg, k, r2));
@@ -1441,7 +1595,97 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     order.resize(k);
     for (int i = 0; i < k; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int x, int y) { return std::fabs(theta[x]) < std::fabs(theta[y]); });
+    worst_wanted = 0;
+    for (int i = 0; i < want; i++) worst_wanted = std::max(worst_wanted, resid[order[i]]);
+    return LQCD_OK;
+  };
+  auto random_columns = [&](int from) -> lqcd_status {
+    if (from >= m) return LQCD_OK;
+    const long nd = 2L * cwords(X) * (m - from);  // doubles per parity
+    for (int p = 0; p < 2; p++) {
+      gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>(
+          (double *)col(X, p, from), nd, prm->seed * 2 + p + 1 + 1000003ULL * (unsigned long long)sweep);
+      LQ_CU(cudaGetLastError());
+    }
+    return LQCD_OK;
+  };
+  // widen the block to m2 columns: the current ones are kept, the new ones
+  // random, then the block is orthonormalised (Cholesky QR keeps the span of
+  // the leading columns)
+  auto grow = [&](int m2) -> lqcd_status {
+    lqcd_field *nf[5];
+    for (auto &f : nf) {
+      LQ_TRY(new_full(c, m2, &f));
+      g.f.push_back(f);
+    }
+    for (int p = 0; p < 2; p++)
+      LQ_CU(cudaMemcpyAsync(col(nf[0], p, 0), col(X, p, 0), (size_t)m * cwords(X) * 16, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    X = nf[0], T = nf[1], HX = nf[2], Y = nf[3], Z = nf[4];
+    for (int q = 0; q < 4; q++) Bs[q] = Bd[q] = nullptr;  // the filter blocks follow the new width
+    const int old = m;
+    m = m2;
+    if (kOvTrace) std::fprintf(stderr, "lqcd overlap: edge cluster fills the block, widening it %d -> %d\n", old, m);
+    LQ_TRY(random_columns(old));
+    return orthonormalise(c, X, T, m);
+  };
+  auto run_sweeps = [&](double tol2) -> lqcd_status {
+    for (;;) {
+      LQ_TRY(sweeps(tol2));
+      if (!cut || sweep >= prm->max_filter) return LQCD_OK;
+      LQ_TRY(grow((int)std::min<long>(std::min<long>(kOvMaxBlock, N), std::max(2 * m, m + 16))));
+    }
+  };
+  double tol2 = prm->eig_tol;
+  if (prm->eig_method == LQCD_EIG_LANCZOS) {
+    // restart size m (the block of the subspace method), basis of up to 2m
+    const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
+    if (mmax < m + 8) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", m + 8);
+    LanczosResult lr;
+    LQ_TRY(lowmodes_lanczos(c, prm, want, m, mmax, X, g, lr));
+    kneed = lr.kneed;
+    sweep = lr.cycles;
+    applies = lr.applies;
+    converged = lr.converged;
+    fp32_phase = false;
+  } else {
+    LQ_TRY(random_columns(0));
+    LQ_TRY(orthonormalise(c, X, T, m));
+    LQ_TRY(run_sweeps(tol2));
   }
+  // The contract is on H_W itself: ||H_W v - lambda v|| <= eig_tol for every
+  // returned mode.  An H_W^2 residual of eig_tol leaves an eigenvector error
+  // of about eig_tol / gap, gap the distance of the cluster's H_W^2 eigenvalue
+  // to the rest of the spectrum, so on a clustered spectrum the H_W residual
+  // can exceed eig_tol by the ratio |lambda| / gap.  The set-up therefore
+  // checks the H_W residuals after the final Rayleigh-Ritz step and, while
+  // they exceed eig_tol, tightens the H_W^2 target in proportion and sweeps
+  // on (the first time after the Lanczos method, on its Ritz vectors padded
+  // with random columns to a full block).
+  bool padded = prm->eig_method != LQCD_EIG_LANCZOS;
+  if (!padded && kneed >= m - 4) {  // Lanczos kept a cluster as wide as its restart block
+    LQ_TRY(random_columns(kneed));
+    LQ_TRY(orthonormalise(c, X, T, m));
+    padded = true;
+    LQ_TRY(run_sweeps(tol2));
+  }
+  double worst = 0;
+  LQ_TRY(final_rr(worst));
+  while (worst > prm->eig_tol && sweep < prm->max_filter) {
+    tol2 *= std::min(0.5, std::max(1e-3, 0.5 * prm->eig_tol / worst));
+    if (!padded) {
+      LQ_TRY(random_columns(kneed));
+      LQ_TRY(orthonormalise(c, X, T, m));
+      padded = true;
+    }
+    if (kOvTrace)
+      std::fprintf(stderr, "lqcd overlap: H_W residual %.3e > eig_tol, refining to H_W^2 residual %.3e\n", worst,
+                   tol2);
+    LQ_TRY(run_sweeps(tol2));
+    LQ_TRY(final_rr(worst));
+  }
+  converged = worst <= prm->eig_tol;
+  sweep--;  // inf->sweeps below counts sweep + 1
   inf->sweeps = sweep + 1;
   inf->hw_applies = (double)applies;
   // keep the `want` lowest (by |theta|), sorted
@@ -1480,8 +1724,12 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   inf->sign_error = sign_error(S.a, S.b, S.coef);
   LQ_CU(cudaStreamSynchronize(c->stream));
   inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // an unconverged set-up leaves the state unusable: the sign function would
+  // project with inexact eigenvectors
+  if (!converged)
+    return set_error(LQCD_ERR_NOCONV, "low modes not converged to ||H_W v - lambda v|| <= %.3g in %d sweeps",
+                     prm->eig_tol, prm->max_filter);
   S.ready = true;
-  if (!converged) return set_error(LQCD_ERR_NOCONV, "low modes not converged in %d sweeps", prm->max_filter);
   return LQCD_OK;
 }
 

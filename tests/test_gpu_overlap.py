@@ -113,6 +113,13 @@ def test_free_field_closed_form(lib, high):
     dims = (4, 4, 4, 4)
     U = gen.unit_gauge(dims)
     lat, info, lam, vecs = _setup(L, dims, U, 4, mass=0.05, high=high)
+    # the low modes: |lambda| = min_p N(p), the bottom of a 24-fold cluster
+    # (wider than the starting block, which must grow to hold it whole)
+    nmin = min(np.sqrt((4 - RHO - np.cos(p).sum()) ** 2 + (np.sin(p) ** 2).sum()) for p in all_momenta(dims, 1))
+    assert np.allclose(np.abs(lam), nmin, atol=1e-10)
+    assert max(info.resid[:4]) <= 1e-11
+    res, ortho = oracle.eigen_residuals(dims, U, RHO, lam, vecs)
+    assert res.max() <= 1e-10 and ortho < 1e-10
     g = [oracle.gamma(mu) for mu in range(4)]
     m = 0.05
     rng = np.random.default_rng(2)
@@ -189,4 +196,58 @@ def test_overlap_rejects_bad_eig_method(lib):
     with pytest.raises(L.LqcdError) as e:
         L.lqcd_overlap_setup(lat.ctx, prm)
     assert e.value.status == L.LQCD_ERR_ARG
+    lat.close()
+
+
+@pytest.mark.parametrize("high,method", [("f64", "subspace"), ("df64", "subspace"), ("f64", "lanczos"),
+                                         ("df64", "lanczos")])
+def test_twenty_mode_contract(lib, high, method):
+    """20 low modes on a smooth 8^3x16 field (a clustered spectrum, as on the
+    16^3x32 overlap workload): every returned mode meets eig_tol as an
+    eigenpair of H_W itself, recomputed by the oracle, not only its H_W^2
+    residual inside the solver."""
+    L = lib
+    dims = (8, 8, 8, 16)
+    U = gen.gauge_field(dims, 0.1, 1005)
+    eig_tol = 1e-10
+    lat = L.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    prm = L.overlap_params(rho=RHO, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=eig_tol, high=high,
+                           eig_method=method, max_filter=800)
+    st, info = L.lqcd_overlap_setup(lat.ctx, prm)
+    assert st == L.LQCD_OK
+    vecs = np.zeros((20,) + oracle.spinor_shape(dims), dtype=np.complex128)
+    L.lqcd_overlap_lowmodes(lat.ctx, vecs)
+    lam = np.array(info.lambda_[:20])
+    res, ortho = oracle.eigen_residuals(dims, U, RHO, lam, vecs)
+    assert res.max() <= eig_tol, res
+    assert max(info.resid[:20]) <= eig_tol
+    assert ortho < 1e-10
+    assert np.all(np.diff(np.abs(lam)) >= -1e-12)  # sorted by |lambda|
+    lat.close()
+
+
+def test_unconverged_setup_is_refused(lib):
+    """A set-up that returns NOCONV leaves no usable state: the overlap
+    operator and the low-mode export refuse to run on inexact eigenvectors."""
+    L = lib
+    dims = (4, 4, 4, 4)
+    U = gen.gauge_field(dims, 0.3, 23)
+    lat = L.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    prm = L.overlap_params(rho=RHO, n_low=8, sign_tol=1e-10, eig_tol=1e-13, max_filter=1)
+    st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
+    assert st == L.LQCD_ERR_NOCONV
+    psi = gen.gaussian_spinor(dims, 5)[0]
+    with pytest.raises(L.LqcdError) as e:
+        _ov(L, lat, psi, L.LQCD_OV_APPLY)
+    assert e.value.status == L.LQCD_ERR_STATE
+    with pytest.raises(L.LqcdError) as e:
+        L.lqcd_overlap_lowmodes(lat.ctx, np.zeros((8,) + oracle.spinor_shape(dims), dtype=np.complex128))
+    assert e.value.status == L.LQCD_ERR_STATE
+    # a converged set-up on the same context makes it usable again
+    prm = L.overlap_params(rho=RHO, n_low=8, sign_tol=1e-10, eig_tol=1e-11, max_filter=200)
+    st, info = L.lqcd_overlap_setup(lat.ctx, prm)
+    assert st == L.LQCD_OK
+    assert np.isfinite(_ov(L, lat, psi, L.LQCD_OV_APPLY)).all()
     lat.close()
