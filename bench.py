@@ -648,35 +648,38 @@ def run_solve_only(args):
     return 0
 
 
-def run_overlap(args):
+def overlap_workload(L, torch, high, eig, want_oracle, stream):
     """Config 5: overlap operator on 16^3x32 (eps 0.1, rho 1.5, m 0.05), 20
-    exact low modes, Chebyshev sign to 1e-10, 12 RHS, mixed-precision CG."""
-    import torch
+    exact low modes, Chebyshev sign to 1e-10, 12 RHS, mixed-precision CG; the
+    low modes and every right-hand side's true residual checked by the oracle
+    (its own FP64 sign function, with the returned modes and interval)."""
     import gen
-    import paper_2001_05706_gb300 as L
-    torch.cuda.set_device(0)
     dims = (16, 16, 16, 32)
     U = gen.gauge_field(dims, 0.1, 1005)
     b = gen.gaussian_spinor(dims, 2005, nrhs=12)
-    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10", "high": args.high,
-           "eig_method": args.eig, "config": {
+    out = {"high": high, "eig_method": eig, "config": {
         "workload": "overlap D_ov(m) = rho[1 + g5 sign(H_W)] + ..., 16^3x32, eps 0.1, rho 1.5, m 0.05, 20 low modes, "
                     "sign to 1e-10 (FP32 sign inside the CG to 1e-6), 12 Gaussian RHS, CG on the normal "
                     "equations with FP64 (or DF64) reliable updates every two decades (delta 0.01)"}}
-    with L.Lattice(dims, stream=torch.cuda.current_stream()) as lat:
+    with L.Lattice(dims, stream=stream) as lat:
         lat.load_gauge(U.view(np.float64))
-        prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-11, max_filter=400,
-                               high=args.high, eig_method=args.eig)
+        prm = L.overlap_params(rho=1.5, mass=0.05, n_low=20, sign_tol=1e-10, eig_tol=1e-10, max_filter=400,
+                               high=high, eig_method=eig)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, info = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
+        torch.cuda.synchronize()
         out["setup"] = {"seconds": time.perf_counter() - t0, "status": "ok" if st == 0 else L.lqcd_last_error(),
                         "sweeps_or_restarts": info.sweeps, "hw_applications": info.hw_applies,
                         "degree": info.degree, "degree_inner_fp32": info.degree_inner,
-                        "a": info.a, "b": info.b,
+                        "a": info.a, "b": info.b, "eig_tol": 1e-10,
                         "sign_error": info.sign_error, "max_eig_resid": max(info.resid[:20]),
                         "lambda_min_max": [min(abs(v) for v in info.lambda_[:20]),
                                            max(abs(v) for v in info.lambda_[:20])]}
+        if st != 0:
+            return out
         x = np.zeros_like(b)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         L.lqcd_overlap(lat.ctx, x, b, 12, L.LQCD_OV_APPLY)
         t_apply = time.perf_counter() - t0
@@ -690,7 +693,7 @@ def run_overlap(args):
         out["solve_mixed_12rhs"] = {"seconds": time.perf_counter() - t0, "iters": si.iters,
                                     "reliable_updates": si.reliable_updates, "status": "ok" if st == 0 else
                                     L.lqcd_last_error(), "max_true_resid_gpu_fp64": max(si.true_resid[:12])}
-        if not args.no_cpu_baseline:
+        if want_oracle:
             import oracle
             vecs = np.zeros((20,) + oracle.spinor_shape(dims), dtype=np.complex128)
             L.lqcd_overlap_lowmodes(lat.ctx, vecs)
@@ -699,8 +702,22 @@ def run_overlap(args):
             out["oracle_eig_resid_max"] = float(res.max())
             out["oracle_eig_ortho"] = float(ortho)
             n, c = oracle.cheb_degree(info.a, info.b, 1e-10)
-            r = b[0] - oracle.apply_overlap(dims, U, 1.5, 0.05, x[0], info.a, info.b, c, lam=lam, vecs=vecs)
-            out["oracle_true_resid_rhs0"] = float(np.linalg.norm(r) / np.linalg.norm(b[0]))
+            rr = []
+            for k in range(12):
+                r = b[k] - oracle.apply_overlap(dims, U, 1.5, 0.05, x[k], info.a, info.b, c, lam=lam, vecs=vecs)
+                rr.append(float(np.linalg.norm(r) / np.linalg.norm(b[k])))
+            out["oracle_true_resid"] = rr
+            out["max_true_resid_oracle"] = max(rr)
+    return out
+
+
+def run_overlap(args):
+    """Config 5 on its own (--overlap), either low-mode method and precision."""
+    import torch
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(0)
+    out = {"metric": "overlap set-up and mixed-precision 12-RHS solve time to 1e-10"}
+    out.update(overlap_workload(L, torch, args.high, args.eig, not args.no_cpu_baseline, torch.cuda.current_stream()))
     print(json.dumps(out))
     return 0
 
@@ -815,6 +832,9 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_batch and world == 1:
         multi = {"point_sources_32x32x32x64": run_multi_rhs(L, torch, lat, U, need_oracle, oracle_AAi),
                  "batch_24_lattices": run_batch(L, torch, stream, need_oracle)}
+    overlap = None
+    if not args.no_overlap and world == 1:
+        overlap = overlap_workload(L, torch, "df64", "lanczos", need_oracle, stream)
     cpu = None
     if need_oracle:
         rate, nsl, dt = oracle_slab_rate(U, oracle_AAi[0], oracle_AAi[1], psi)
@@ -852,6 +872,7 @@ def run_gpu(args, rank, world, local_rank):
         "multi_rhs_mhat_32x32x32x64": mrhs,
         "solve": solve,
         "multi_rhs_and_batch": multi,
+        "overlap_16x16x16x32": overlap,
     }
     print(json.dumps(line))
     return 0
@@ -867,11 +888,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-config3", action="store_true", help="skip the 48^3x96 solve comparison")
+    ap.add_argument("--no-overlap", action="store_true", help="skip the overlap workload in the default run")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
                     help="--overlap: arithmetic of the FP64 parts (FP64 or double-float)")
-    ap.add_argument("--eig", default="subspace", choices=["subspace", "lanczos"],
+    ap.add_argument("--eig", default="lanczos", choices=["subspace", "lanczos"],
                     help="--overlap: low-mode solver (block subspace iteration or thick-restart Lanczos)")
     ap.add_argument("--kernel-only", choices=["k2a", "k2b", "mhat"])
     ap.add_argument("--lattice", default="32,32,32,64")

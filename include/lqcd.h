@@ -375,11 +375,15 @@ lqcd_status lqcd_overlap(lqcd_ctx *ctx, double *out, const double *in, int nrhs,
  * latency-critical loops where cudaMalloc/cudaFree would synchronise the
  * device): its scratch -- at most 1024 x 64 partial sums (512 KiB) and a
  * counter -- is a static array of the library that every GPU loading it
- * holds until the process exits.  The first call on a device looks up that
+ * holds until the process exits.  The first call on a device (and on each
+ * new CUDA context of it, for example after cudaDeviceReset) looks up that
  * array's device address, so make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU (on
  * different streams, or from several threads) race and give wrong results.
- * nrhs > 64, n < 1 or n > 2^40 give LQCD_ERR_ARG; no context is needed. */
+ * nrhs > 64, n < 1 or n > 2^40, and x or result not device (or managed)
+ * memory of the current device give LQCD_ERR_ARG; the sizes of the arrays
+ * cannot be checked (x must hold n * nrhs doubles, result nrhs); no context
+ * is needed. */
 lqcd_status lqcd_norm2_noalloc(const double *x, long n, int nrhs, double *result, void *cuda_stream);
 
 #ifdef __cplusplus

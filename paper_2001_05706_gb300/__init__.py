@@ -256,12 +256,28 @@ def lqcd_solve_batch(ctxs, xs, bs, params, raise_on_noconv=True):
 
 def lqcd_norm2_noalloc(x, n, nrhs, result, stream=None):
     """result[k] = sum of squares of x[k*n:(k+1)*n] (device tensors of float64);
-    allocates nothing (static library scratch), asynchronous on `stream`."""
-    px, dx = _buf(x)
-    pr, dr = _buf(result)
-    if not (dx and dr):
-        raise ValueError("x and result must be CUDA tensors")
-    _check(_lib.lqcd_norm2_noalloc(px, int(n), int(nrhs), pr, _stream_ptr(stream)))
+    allocates nothing (static library scratch), asynchronous on `stream`.
+    The C side cannot see the tensors' sizes, so they are checked here: both
+    float64, contiguous, on the current CUDA device, x holding n * nrhs values
+    and result nrhs."""
+    import torch
+    for name, t in (("x", x), ("result", result)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not the current device cuda:{torch.cuda.current_device()}")
+    n, nrhs = int(n), int(nrhs)
+    if n >= 1 and nrhs >= 1 and x.numel() < n * nrhs:
+        raise ValueError(f"x holds {x.numel()} values, fewer than n * nrhs = {n * nrhs}")
+    if nrhs >= 1 and result.numel() < nrhs:
+        raise ValueError(f"result holds {result.numel()} values, fewer than nrhs = {nrhs}")
+    px, _ = _buf(x)
+    pr, _ = _buf(result)
+    _check(_lib.lqcd_norm2_noalloc(px, n, nrhs, pr, _stream_ptr(stream)))
 
 
 LQCD_EIG_SUBSPACE, LQCD_EIG_LANCZOS = 0, 1

@@ -9,6 +9,8 @@
 // per-block partial sums and the completion counter live in the arrays
 // below, which every GPU that loads the library holds until the process
 // exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -28,9 +30,41 @@ static __device__ __align__(256) unsigned int g_noalloc_counter[64];
 
 struct DeviceScratch {
   bool ready = false;
+  CUcontext ctx = nullptr;  // the context the addresses belong to
   double *partials = nullptr;
   unsigned int *counter = nullptr;
 };
+
+// the calling thread's current CUDA context (driver entry point looked up
+// through the runtime, so the library needs no link against libcuda);
+// nullptr if it cannot be found
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext *);
+  static Fn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<Fn>(f);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// x must be memory of the current device (device or managed memory)
+lqcd_status check_device_pointer(const void *p, int dev, const char *what) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ERR_ARG, "%s: not a CUDA pointer", what);
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+    return set_error(LQCD_ERR_ARG, "%s: must be device or managed memory of the current device %d", what, dev);
+  return LQCD_OK;
+}
 std::mutex g_noalloc_mu;
 DeviceScratch g_noalloc_dev[kNoAllocMaxDevices];
 
@@ -60,18 +94,24 @@ extern "C" lqcd_status lqcd_norm2_noalloc(const double *x, long n, int nrhs, dou
   int dev = 0;
   LQ_CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(LQCD_ERR_ARG, "device %d out of range", dev);
+  LQ_TRY(check_device_pointer(x, dev, "x"));
+  LQ_TRY(check_device_pointer(result, dev, "result"));
   DeviceScratch sc;
   {
-    // once per device, with that device current: the device addresses of the
-    // static arrays (their names in host code are host-side stand-ins)
+    // once per device and context, with that device current: the device
+    // addresses of the static arrays (their names in host code are host-side
+    // stand-ins); looked up again if the context changed (a cudaDeviceReset,
+    // or a caller on another driver-API context of the same device)
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     DeviceScratch &d = g_noalloc_dev[dev];
-    if (!d.ready) {
+    const CUcontext ctx = current_context();
+    if (!d.ready || d.ctx != ctx) {
       void *p = nullptr, *c = nullptr;
       LQ_CU(cudaGetSymbolAddress(&p, g_noalloc_partials));
       LQ_CU(cudaGetSymbolAddress(&c, g_noalloc_counter));
       d.partials = static_cast<double *>(p);
       d.counter = static_cast<unsigned int *>(c);
+      d.ctx = ctx;
       d.ready = true;
     }
     sc = d;

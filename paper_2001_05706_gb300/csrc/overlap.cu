@@ -1430,6 +1430,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   // is exact only on a union of whole clusters (an incomplete one is not
   // H_W-invariant and gives spurious interior Ritz values).
   bool cut = false;
+  bool refining = false;  // the refinement filters in FP64 (below double-float's noise floor)
   auto sweeps = [&](double tol2) -> lqcd_status {
     cut = false;
     for (;; sweep++) {
@@ -1515,7 +1516,7 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
       const int deg = 16;
       // the filter runs on a copy of X in FP32 (early sweeps) or double-float
       // (on request), in place in FP64 otherwise
-      const lqcd_prec fp = low ? LQCD_F32 : S.df ? LQCD_DF64 : LQCD_F64;
+      const lqcd_prec fp = low ? LQCD_F32 : (S.df && !refining) ? LQCD_DF64 : LQCD_F64;
       lqcd_field *fX = X, *fY = Y, *fH = HX, *fT = T;
       if (fp != LQCD_F64) {
         lqcd_field **blk = fp == LQCD_F32 ? Bs : Bd;
@@ -1641,8 +1642,13 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
     // restart size m (the block of the subspace method), basis of up to 2m
     const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
     if (mmax < m + 8) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", m + 8);
+    // the H_W residual of the result is about |lambda| / gap times its H_W^2
+    // residual: the Krylov method is asked for 1 % of eig_tol on H_W^2, cheap
+    // once it has converged
+    lqcd_overlap_params lprm = *prm;
+    lprm.eig_tol = std::max(1e-2 * prm->eig_tol, 1e-13);
     LanczosResult lr;
-    LQ_TRY(lowmodes_lanczos(c, prm, want, m, mmax, X, g, lr));
+    LQ_TRY(lowmodes_lanczos(c, &lprm, want, m, mmax, X, g, lr));
     kneed = lr.kneed;
     sweep = lr.cycles;
     applies = lr.applies;
@@ -1671,8 +1677,15 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   }
   double worst = 0;
   LQ_TRY(final_rr(worst));
-  while (worst > prm->eig_tol && sweep < prm->max_filter) {
-    tol2 *= std::min(0.5, std::max(1e-3, 0.5 * prm->eig_tol / worst));
+  // the H_W^2 residual the refinement can still resolve: its filter runs in
+  // FP64 (double-float filtering leaves ~3e-12 of noise); two rounds at the
+  // floor without meeting eig_tol end it (LQCD_ERR_NOCONV)
+  const double floor2 = 5e-14;
+  int at_floor = 0;
+  refining = true;
+  while (worst > prm->eig_tol && sweep < prm->max_filter && at_floor < 2) {
+    tol2 = std::max(floor2, tol2 * std::min(0.5, std::max(0.1, 0.5 * prm->eig_tol / worst)));
+    if (tol2 <= floor2) at_floor++;
     if (!padded) {
       LQ_TRY(random_columns(kneed));
       LQ_TRY(orthonormalise(c, X, T, m));

@@ -9,11 +9,15 @@ import pytest
 
 import gen
 import oracle
-from helpers import rel
+from helpers import rel, site_max_rel
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-5, "f16": 1e-2, "bf16": 1e-2}
+# the largest error of any single site, relative to that site (floored at a
+# tenth of the rms site norm): FP16 rounds each stored real to 2^-11, BF16 to
+# 2^-8 of its site's scale, accumulated over the eight neighbours
+SITE_TOL = {"f64": 1e-11, "df64": 1e-11, "f32": 1e-5, "f16": 1e-2, "bf16": 3e-2}
 KAPPA, CSW, RHO = 0.12, 1.0, 1.5
 
 
@@ -87,6 +91,7 @@ def test_ops_clover(clover_lattice, op, prec, recon):
     out = lat.dslash(psi, op, prec, recon)
     expect = _oracle_op(op, DIMS, U, A, Ai, psi)
     assert rel(out, expect) < TOL[prec], f"{op} {prec} r{recon}"
+    assert site_max_rel(out, expect) < SITE_TOL[prec], f"{op} {prec} r{recon} per site"
 
 
 @pytest.mark.parametrize("op", ["K2A", "MHAT", "MHAT_DAG", "M", "MHAT_SYM_DAG"])
@@ -97,7 +102,9 @@ def test_ops_wilson(lib, op, prec):
     psi = gen.gaussian_spinor(dims, 8)[0]
     recon = 18 if prec == "df64" else 12  # DF64 keeps all 18 reals of a link
     out = lat.dslash(psi, op, prec, recon)
-    assert rel(out, _oracle_op(op, dims, U, None, None, psi)) < TOL[prec]
+    expect = _oracle_op(op, dims, U, None, None, psi)
+    assert rel(out, expect) < TOL[prec]
+    assert site_max_rel(out, expect) < SITE_TOL[prec]
     lat.close()
 
 
@@ -108,7 +115,9 @@ def test_multi_rhs(clover_lattice, nrhs, prec):
     psi = gen.gaussian_spinor(DIMS, 3000 + nrhs, nrhs=nrhs)
     out = lat.dslash(psi, "MHAT", prec, 18 if prec == "df64" else 12)
     for k in range(nrhs):
-        assert rel(out[k], _oracle_op("MHAT", DIMS, U, A, Ai, psi[k])) < TOL[prec]
+        expect = _oracle_op("MHAT", DIMS, U, A, Ai, psi[k])
+        assert rel(out[k], expect) < TOL[prec]
+        assert site_max_rel(out[k], expect) < SITE_TOL[prec]
 
 
 @pytest.mark.parametrize("op", ["MHAT_SYM", "MHAT_SYM_DAG"])
@@ -303,6 +312,7 @@ def test_full_size_sampled(lib, prec, recon):
     expect = _mhat_at_sites(dims, U, kappa, csw, psi, sites)
     got = z.reshape(V, 12)[sites]
     assert rel(got, expect) < TOL[prec]
+    assert site_max_rel(got, expect) < SITE_TOL[prec]
 
 
 def test_df64_rejects_12_real_links(clover_lattice, lib):

@@ -64,10 +64,51 @@ def test_noalloc_norm2_matches_field_norm2_twice(lib):
 def test_noalloc_rejects_sizes_beyond_the_scratch(lib):
     import torch
     L = lib
-    x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    x = torch.zeros(16 * 65, dtype=torch.float64, device="cuda")
     r = torch.zeros(65, dtype=torch.float64, device="cuda")
     with pytest.raises(L.LqcdError) as e:
         L.lqcd_norm2_noalloc(x, 16, 65, r)
     assert e.value.status == L.LQCD_ERR_ARG and "64" in str(e.value)
     with pytest.raises(L.LqcdError):
         L.lqcd_norm2_noalloc(x, 0, 1, r)
+
+
+@pytest.mark.parametrize("n,nrhs", [(3_000_000, 2), (100, 64)])
+def test_noalloc_capped_grid_and_full_scratch(lib, n, nrhs):
+    """Beyond 2048 x 1024 values the grid is capped at 1024 blocks and the
+    kernel strides over the rest; 64 right-hand sides fill the static scratch.
+    Checked against numpy's FP64 sum of squares on the host and against the
+    existing entry point on canonical spinors, on two calls in a row."""
+    import torch
+    L = lib
+    rng = np.random.default_rng(n + nrhs)
+    for call in range(2):
+        xh = rng.standard_normal(n * nrhs) * (1.0 + call)
+        x = torch.from_numpy(xh).cuda()
+        res = torch.full((nrhs,), -1.0, dtype=torch.float64, device="cuda")
+        L.lqcd_norm2_noalloc(x, n, nrhs, res)
+        torch.cuda.synchronize()
+        expect = np.array([np.dot(xh[k * n:(k + 1) * n], xh[k * n:(k + 1) * n]) for k in range(nrhs)])
+        assert np.all(np.abs(res.cpu().numpy() - expect) <= 1e-12 * expect), call
+
+
+def test_noalloc_binding_checks_what_the_c_side_cannot(lib):
+    """The C entry point sees bare pointers: the binding rejects a wrong dtype,
+    too-short arrays and host tensors before any launch, and the C side
+    rejects a host pointer."""
+    import ctypes
+    import torch
+    L = lib
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    r = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        L.lqcd_norm2_noalloc(x.float(), 32, 2, r)
+    with pytest.raises(ValueError):
+        L.lqcd_norm2_noalloc(x, 33, 2, r)  # needs 66 values
+    with pytest.raises(ValueError):
+        L.lqcd_norm2_noalloc(x, 32, 3, r)  # result too short
+    with pytest.raises(ValueError):
+        L.lqcd_norm2_noalloc(x.cpu(), 32, 2, r)
+    host = np.zeros(64)
+    st = L._lib.lqcd_norm2_noalloc(host.ctypes.data_as(ctypes.c_void_p), 32, 2, ctypes.c_void_p(r.data_ptr()), None)
+    assert st == L.LQCD_ERR_ARG
