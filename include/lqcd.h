@@ -162,7 +162,7 @@ lqcd_status lqcd_dslash(lqcd_ctx *ctx, double *out, const double *in, int nrhs, 
 /* ---- device-resident fields -------------------------------------------- */
 
 /* Allocate a spinor field of nrhs right-hand sides on `subset` in storage
- * precision `prec`.  Contents are undefined until imported or written. */
+ * precision `prec`, zero-filled (asynchronously, on the context's stream). */
 lqcd_status lqcd_field_create(lqcd_ctx *ctx, lqcd_prec prec, lqcd_subset subset, int nrhs, lqcd_field **field);
 lqcd_status lqcd_field_destroy(lqcd_field *field);
 
@@ -363,6 +363,50 @@ lqcd_status lqcd_overlap_lowmodes(lqcd_ctx *ctx, double *vecs, int on_device);
  * final residuals.  Blocks. */
 lqcd_status lqcd_overlap(lqcd_ctx *ctx, double *out, const double *in, int nrhs, int on_device, lqcd_overlap_op op,
                          const lqcd_solve_params *cg, lqcd_solve_info *info);
+
+/* ---- domain decomposition along t: building blocks -------------------- */
+
+/* The paper's multi-GPU runs (Sec. 4: the clover solve on a 96^3 x 192 lattice
+ * over 324 GPUs, the overlap eigensystem over 4 GPUs) split the lattice
+ * between GPUs.  Here a domain is an ordinary context whose lattice is its
+ * share of the time slices plus `halo` ghost slices on either side (created
+ * with t_antiperiodic = 0: the global time boundary's sign travels with the
+ * ghost data instead).  Since t is the slowest site index, time slice t of a
+ * parity is a contiguous run of Vh / L3 sites in the global order, so these
+ * calls move and compute whole slices; the exchange between domains (NCCL,
+ * gloo, or copies between domains of one process) belongs to the caller
+ * (paper_2001_05706_gb300/domain.py drives it). */
+
+/* Copy time slices [t0, t1) of parity `parity` of field f (all its
+ * right-hand sides) to (to_field = 0) or from (to_field = 1) the device buffer
+ * buf, laid out [rhs][16-byte word][site of the slices], multiplying every
+ * real by factor (+1 or -1, exact).  FP64, FP32 and DF64 fields; buf holds
+ * nrhs * (24 * bytes per real / 16) * (t1 - t0) * Vh / L3 words of 16 bytes
+ * and must be device memory (LQCD_ERR_ARG otherwise).  Asynchronous on the
+ * context's stream. */
+lqcd_status lqcd_field_slices(lqcd_ctx *ctx, lqcd_field *f, int parity, int t0, int t1, void *buf, int to_field,
+                              double factor);
+
+/* The two kernels of the Schur complement (Table 2's D-slash with the clover
+ * term, see lqcd_apply_schur) on the output sites of time slices [t0, t1)
+ * only: y_e = A_ee^-1 D_eo x_o (dagger: with g5 on x), and
+ * z_o = A_oo x_o - kappa^2 D_oe y_e (dagger: g5 on the hop).  Sites outside
+ * the slices are not written.  lqcd_k2b_slices writes ||z_o||^2 over those
+ * slices per right-hand side to norm2 (host, nrhs doubles; NULL: none) and
+ * then blocks; otherwise asynchronous. */
+lqcd_status lqcd_k2a_slices(lqcd_ctx *ctx, lqcd_recon recon, int dagger, lqcd_field *y_even, const lqcd_field *x_odd,
+                            int t0, int t1);
+lqcd_status lqcd_k2b_slices(lqcd_ctx *ctx, lqcd_recon recon, int dagger, lqcd_field *z_odd, const lqcd_field *x_odd,
+                            const lqcd_field *y_even, int t0, int t1, double *norm2);
+
+/* y = a[k] x + b[k] y on right-hand side k (a, b host arrays of nrhs
+ * doubles), fields of one context with the same precision (FP64 or FP32),
+ * subset and nrhs (<= 128); blocks. */
+lqcd_status lqcd_field_axpby(lqcd_ctx *ctx, lqcd_field *y, const double *a, const double *b, const lqcd_field *x);
+
+/* out[k] = ||f_k||^2 (FP64 fixed-order sum over every site f holds) per
+ * right-hand side, host array of nrhs doubles (nrhs <= 256); blocks. */
+lqcd_status lqcd_field_norm2s(lqcd_ctx *ctx, const lqcd_field *f, double *out);
 
 /* ---- allocation-free reduction ---------------------------------------- */
 

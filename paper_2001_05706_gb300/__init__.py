@@ -93,6 +93,11 @@ _sig = {
     "lqcd_field_norm2": [_vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "lqcd_solve": [_vp, _vp, _vp, _ip, ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_norm2_noalloc": [_vp, ctypes.c_long, _ip, _vp, _vp],
+    "lqcd_field_slices": [_vp, _vp, _ip, _ip, _ip, _vp, _ip, ctypes.c_double],
+    "lqcd_k2a_slices": [_vp, _ip, _ip, _vp, _vp, _ip, _ip],
+    "lqcd_k2b_slices": [_vp, _ip, _ip, _vp, _vp, _vp, _ip, _ip, _vp],
+    "lqcd_field_axpby": [_vp, _vp, _vp, _vp, _vp],
+    "lqcd_field_norm2s": [_vp, _vp, _vp],
     "lqcd_solve_batch": [ctypes.POINTER(_vp), _ip, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip,
                          ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_overlap_setup": [_vp, ctypes.POINTER(lqcd_overlap_params), ctypes.POINTER(lqcd_overlap_info)],
@@ -219,6 +224,41 @@ def lqcd_field_norm2(ctx, field):
     r = ctypes.c_double(0)
     _check(_lib.lqcd_field_norm2(ctx, field, ctypes.byref(r)))
     return r.value
+
+
+def lqcd_field_slices(ctx, field, parity, t0, t1, buf, to_field, factor=1.0):
+    """Time slices [t0, t1) of one parity of a field to/from a device buffer (a CUDA tensor)."""
+    pb, dev = _buf(buf)
+    if not dev:
+        raise ValueError("buf must be a CUDA tensor")
+    _check(_lib.lqcd_field_slices(ctx, field, int(parity), int(t0), int(t1), pb, int(to_field), float(factor)))
+
+
+def lqcd_k2a_slices(ctx, recon, dagger, y_even, x_odd, t0, t1):
+    _check(_lib.lqcd_k2a_slices(ctx, int(recon), int(dagger), y_even, x_odd, int(t0), int(t1)))
+
+
+def lqcd_k2b_slices(ctx, recon, dagger, z_odd, x_odd, y_even, t0, t1, nrhs=None):
+    """z_o on time slices [t0, t1); returns the per-RHS ||z_o||^2 over them when nrhs is given."""
+    if nrhs is None:
+        _check(_lib.lqcd_k2b_slices(ctx, int(recon), int(dagger), z_odd, x_odd, y_even, int(t0), int(t1), None))
+        return None
+    out = (ctypes.c_double * int(nrhs))()
+    _check(_lib.lqcd_k2b_slices(ctx, int(recon), int(dagger), z_odd, x_odd, y_even, int(t0), int(t1), out))
+    return np.array(out[:])
+
+
+def lqcd_field_axpby(ctx, y, a, b, x):
+    """y = a[k] x + b[k] y per right-hand side."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    _check(_lib.lqcd_field_axpby(ctx, y, a.ctypes.data_as(_vp), b.ctypes.data_as(_vp), x))
+
+
+def lqcd_field_norm2s(ctx, field, nrhs):
+    out = (ctypes.c_double * int(nrhs))()
+    _check(_lib.lqcd_field_norm2s(ctx, field, out))
+    return np.array(out[:])
 
 
 def lqcd_solve(ctx, x, b, params: lqcd_solve_params, raise_on_noconv=True):

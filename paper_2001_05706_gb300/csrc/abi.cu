@@ -305,6 +305,13 @@ lqcd_status lqcd_field_create(lqcd_ctx *c, lqcd_prec prec, lqcd_subset subset, i
       k++;
     }
   }
+  // zero-filled on the context's stream (ordered before any use on it)
+  cudaError_t e = cudaMemsetAsync(f->alloc, 0, per * np, c->stream);
+  if (e == cudaSuccess && sper) e = cudaMemsetAsync(f->scale_alloc, 0, sper * np, c->stream);
+  if (e != cudaSuccess) {
+    lqcd_field_destroy(f);
+    return set_error(LQCD_ERR_CUDA, "zeroing a new field failed: %s", cudaGetErrorString(e));
+  }
   *field = f;
   return LQCD_OK;
 }
