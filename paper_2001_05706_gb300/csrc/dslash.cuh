@@ -91,20 +91,67 @@ template <typename S> __device__ __forceinline__ const void *rhs_base(const void
   return reinterpret_cast<const char *>(base) + (long)r * rhs_words * Wd::W;
 }
 
+// FP16/BF16 (re, im) pairs as one 32-bit word: unpacked and packed two
+// values per instruction (exact on the way in; round to nearest on the way
+// out, as the scalar conversions)
+template <typename S> struct PackedPair;
+template <> struct PackedPair<__half> {
+  using type = __half2;
+  static __device__ __forceinline__ type from(unsigned u) { return *reinterpret_cast<const type *>(&u); }
+  static __device__ __forceinline__ type make(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ float2 f2(type v) { return __half22float2(v); }
+};
+template <> struct PackedPair<__nv_bfloat16> {
+  using type = __nv_bfloat162;
+  static __device__ __forceinline__ type from(unsigned u) { return *reinterpret_cast<const type *>(&u); }
+  static __device__ __forceinline__ type make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  // a BF16 value is the upper half of an FP32: one shift or mask per value
+  static __device__ __forceinline__ float2 f2(type v) {
+    const unsigned u = *reinterpret_cast<const unsigned *>(&v);
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+  }
+};
+template <typename S> __device__ __forceinline__ unsigned pack_pair(float a, float b) {
+  const auto v = PackedPair<S>::make(a, b);
+  return *reinterpret_cast<const unsigned *>(&v);
+}
+template <typename S> __device__ __forceinline__ float2 unpack_pair(unsigned u) {
+  return PackedPair<S>::f2(PackedPair<S>::from(u));
+}
+
+// the twelve (re, im) pairs of one FP16/BF16 spinor (three 16-byte words)
+template <typename S, bool STREAM = false>
+__device__ __forceinline__ void load_pairs(const FieldRef &f, long Vh, int r, long i, unsigned (&u)[12]) {
+  static_assert(Words<S, 24>::W == 16, "FP16/BF16 spinors are three 16-byte words");
+  const uint4 *p = reinterpret_cast<const uint4 *>(rhs_base<S>(f.data, f.rhs_words, r));
+#pragma unroll
+  for (int w = 0; w < 3; w++) {
+    const uint4 v = STREAM ? ldcs_word(p + (long)w * Vh + i) : ldg_word(p + (long)w * Vh + i);
+    u[4 * w] = v.x;
+    u[4 * w + 1] = v.y;
+    u[4 * w + 2] = v.z;
+    u[4 * w + 3] = v.w;
+  }
+}
+
 template <typename S, bool STREAM = false>
 __device__ __forceinline__ void load_spinor(const FieldRef &f, long Vh, int r, long i,
                                             cx<typename Math<S>::T> (&psi)[4][3]) {
   using T = typename Math<S>::T;
-  S raw[24];
-  load_reals<S, 24, STREAM>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
   if constexpr (IsHalf<S>::value) {
+    unsigned u[12];
+    load_pairs<S, STREAM>(f, Vh, r, i, u);
     const T sc = (T)__ldg(f.scale + (long)r * Vh + i);
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-      for (int c = 0; c < 3; c++)
-        psi[a][c] = mk<T>(sc * (T)to_f(raw[6 * a + 2 * c]), sc * (T)to_f(raw[6 * a + 2 * c + 1]));
+      for (int c = 0; c < 3; c++) {
+        const float2 v = unpack_pair<S>(u[3 * a + c]);
+        psi[a][c] = mk<T>(sc * v.x, sc * v.y);
+      }
   } else {
+    S raw[24];
+    load_reals<S, 24, STREAM>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -118,14 +165,26 @@ template <typename S>
 __device__ __forceinline__ typename Math<S>::T load_spinor_raw(const FieldRef &f, long Vh, int r, long i,
                                                                cx<typename Math<S>::T> (&psi)[4][3]) {
   using T = typename Math<S>::T;
-  S raw[24];
-  load_reals<S, 24>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
   T sc = (T)1;
-  if constexpr (IsHalf<S>::value) sc = (T)__ldg(f.scale + (long)r * Vh + i);
+  if constexpr (IsHalf<S>::value) {
+    unsigned u[12];
+    load_pairs<S>(f, Vh, r, i, u);
+    sc = (T)__ldg(f.scale + (long)r * Vh + i);
 #pragma unroll
-  for (int a = 0; a < 4; a++)
+    for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+      for (int c = 0; c < 3; c++) {
+        const float2 v = unpack_pair<S>(u[3 * a + c]);
+        psi[a][c] = mk<T>(v.x, v.y);
+      }
+  } else {
+    S raw[24];
+    load_reals<S, 24>(rhs_base<S>(f.data, f.rhs_words, r), Vh, i, raw);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+  }
   return sc;
 }
 
@@ -143,6 +202,15 @@ __device__ __forceinline__ void store_spinor(void *base, float *scale, long rhs_
       for (int c = 0; c < 3; c++) m = fmax(m, fmax(fabs(psi[a][c].r), fabs(psi[a][c].i)));
     scale[(long)r * Vh + i] = (float)m;
     inv = m > (T)0 ? (T)1 / m : (T)0;
+    unsigned u[12];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) u[3 * a + c] = pack_pair<S>(psi[a][c].r * inv, psi[a][c].i * inv);
+    uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<char *>(base) + (long)r * rhs_words * 16);
+#pragma unroll
+    for (int w = 0; w < 3; w++) p[(long)w * Vh + i] = make_uint4(u[4 * w], u[4 * w + 1], u[4 * w + 2], u[4 * w + 3]);
+    return;
   }
 #pragma unroll
   for (int a = 0; a < 4; a++)
@@ -260,13 +328,27 @@ __device__ __forceinline__ typename Math<S>::T load_clover_block(const void *bas
                                                                  long i, int blk, typename Math<S>::T (&m)[36]) {
   using T = typename Math<S>::T;
   using Wd = Words<S, 36>;
-  S raw[36];
   const void *b = reinterpret_cast<const char *>(base) + (long)blk * Wd::NW * Vh * Wd::W;
-  load_reals<S, 36, true>(b, Vh, i, raw);
   T sc = (T)1;
-  if constexpr (IsHalf<S>::value) sc = (T)__ldg(scale + i);
+  if constexpr (IsHalf<S>::value) {
+    static_assert(Wd::W == 8 && Wd::NW == 9, "FP16/BF16 clover blocks are nine 8-byte words");
+    const uint2 *p = reinterpret_cast<const uint2 *>(b);
 #pragma unroll
-  for (int k = 0; k < 36; k++) m[k] = (T)to_f(raw[k]);
+    for (int w = 0; w < 9; w++) {
+      const uint2 v = ldcs_word(p + (long)w * Vh + i);
+      const float2 x = unpack_pair<S>(v.x), y = unpack_pair<S>(v.y);
+      m[4 * w] = x.x;
+      m[4 * w + 1] = x.y;
+      m[4 * w + 2] = y.x;
+      m[4 * w + 3] = y.y;
+    }
+    sc = (T)__ldg(scale + i);
+  } else {
+    S raw[36];
+    load_reals<S, 36, true>(b, Vh, i, raw);
+#pragma unroll
+    for (int k = 0; k < 36; k++) m[k] = (T)to_f(raw[k]);
+  }
   return sc;  // the FP16/BF16 scale, applied to the products by the caller
 }
 
@@ -321,6 +403,46 @@ __device__ __forceinline__ void project(int mu, T s, const cx<T> (&p)[4][3], cx<
         h[1][c] = p[1][c] + sgn_mul(s, p[3][c]);
         break;
     }
+  }
+}
+
+// The projection of FP16/BF16 spinors on their stored (normalised) pairs:
+// h = u + c l with c in {+-1, +-i} is one packed multiply-add per colour and
+// spin (the products by +-1 are exact, so each component is rounded once, at
+// the storage precision), and only the six projected colour components are
+// converted to FP32 instead of all twelve.  u[3 a + c] holds (re, im) of
+// psi[a][c]; s is the projection sign (with g5 on the input folded in).
+template <typename S>
+__device__ __forceinline__ void project_packed(int mu, float s, const unsigned (&u)[12], cx<float> (&h)[2][3]) {
+  using PP = PackedPair<S>;
+  using T2 = typename PP::type;
+  const T2 sp = PP::make(s, s), sm = PP::make(-s, -s);
+  const T2 ip = PP::make(-s, s), im = PP::make(s, -s);  // s i z = (-s z.im, s z.re)
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const T2 p0 = PP::from(u[c]), p1 = PP::from(u[3 + c]), p2 = PP::from(u[6 + c]), p3 = PP::from(u[9 + c]);
+    T2 r0, r1;
+    switch (mu) {
+      case 0:  // h0 = p0 + s i p3, h1 = p1 + s i p2
+        r0 = __hfma2(__lowhigh2highlow(p3), ip, p0);
+        r1 = __hfma2(__lowhigh2highlow(p2), ip, p1);
+        break;
+      case 1:  // h0 = p0 - s p3, h1 = p1 + s p2
+        r0 = __hfma2(p3, sm, p0);
+        r1 = __hfma2(p2, sp, p1);
+        break;
+      case 2:  // h0 = p0 + s i p2, h1 = p1 - s i p3
+        r0 = __hfma2(__lowhigh2highlow(p2), ip, p0);
+        r1 = __hfma2(__lowhigh2highlow(p3), im, p1);
+        break;
+      default:  // h0 = p0 + s p2, h1 = p1 + s p3
+        r0 = __hfma2(p2, sp, p0);
+        r1 = __hfma2(p3, sp, p1);
+        break;
+    }
+    const float2 a = PP::f2(r0), b = PP::f2(r1);
+    h[0][c] = mk<float>(a.x, a.y);
+    h[1][c] = mk<float>(b.x, b.y);
   }
 }
 
@@ -494,39 +616,56 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
     else
       cp_async_wait<0>();
     S raw[24];
+    unsigned uw[12];  // FP16/BF16: the spinor as its twelve stored (re, im) pairs
     unsigned dep = 0;
 #pragma unroll
     for (int w = 0; w < WS::NW; w++) {
       const auto v = st.sp[b][w][tid];
       dep |= first_bits(v);
-      const S *q = reinterpret_cast<const S *>(&v);
+      if constexpr (IsHalf<S>::value) {
+        static_assert(WS::W == 16, "FP16/BF16 spinors are three 16-byte words");
+        const unsigned *q = reinterpret_cast<const unsigned *>(&v);
 #pragma unroll
-      for (int j = 0; j < WS::PER; j++) raw[w * WS::PER + j] = q[j];
+        for (int j = 0; j < 4; j++) uw[w * 4 + j] = q[j];
+      } else {
+        const S *q = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int j = 0; j < WS::PER; j++) raw[w * WS::PER + j] = q[j];
+      }
     }
     S lraw[R];
+    unsigned lw[R / 2];  // FP16/BF16: the link's (re, im) pairs
 #pragma unroll
     for (int w = 0; w < WL::NW; w++) {
       const auto v = st.ln[b][w][tid];
       dep |= first_bits(v);
-      const S *q = reinterpret_cast<const S *>(&v);
+      if constexpr (IsHalf<S>::value) {
+        const unsigned *q = reinterpret_cast<const unsigned *>(&v);
 #pragma unroll
-      for (int j = 0; j < WL::PER; j++) lraw[w * WL::PER + j] = q[j];
+        for (int j = 0; j < WL::PER / 2; j++) lw[w * (WL::PER / 2) + j] = q[j];
+      } else {
+        const S *q = reinterpret_cast<const S *>(&v);
+#pragma unroll
+        for (int j = 0; j < WL::PER; j++) lraw[w * WL::PER + j] = q[j];
+      }
     }
     T f = (T)1;
     if constexpr (IsHalf<S>::value) {
       f = (T)st.sc[b][tid];
       dep |= __float_as_uint(f);
     }
-    cx<T> psi[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-      for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
     cx<T> U[3][3];
 #pragma unroll
     for (int r = 0; r < R / 6; r++)
 #pragma unroll
-      for (int c = 0; c < 3; c++) U[r][c] = mk<T>((T)to_f(lraw[6 * r + 2 * c]), (T)to_f(lraw[6 * r + 2 * c + 1]));
+      for (int c = 0; c < 3; c++) {
+        if constexpr (IsHalf<S>::value) {
+          const float2 e = unpack_pair<S>(lw[3 * r + c]);
+          U[r][c] = mk<T>(e.x, e.y);
+        } else {
+          U[r][c] = mk<T>((T)to_f(lraw[6 * r + 2 * c]), (T)to_f(lraw[6 * r + 2 * c + 1]));
+        }
+      }
     if (R == 12) {
 #pragma unroll
       for (int j = 0; j < 3; j++) {
@@ -540,16 +679,26 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
     if (k + 2 < 8) issue(k + 2, dep);
     const bool wrap = (mu == 3) && P.g.tbc && (dir > 0 ? xc.x[3] == P.g.L[3] - 1 : xc.x[3] == 0);
     if (wrap) f = -f;
-    if (P.g5_in) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        psi[2][c] = (T)-1 * psi[2][c];
-        psi[3][c] = (T)-1 * psi[3][c];
-      }
-    }
     const T s = dir > 0 ? (T)-1 : (T)1;
     cx<T> hh[2][3], uh[2][3];
-    project<T>(mu, s, psi, hh);
+    if constexpr (IsHalf<S>::value) {
+      // g5 on the input negates the lower spins: the projection sign flips
+      project_packed<S>(mu, P.g5_in ? -s : s, uw, hh);
+    } else {
+      cx<T> psi[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) psi[a][c] = mk<T>((T)to_f(raw[6 * a + 2 * c]), (T)to_f(raw[6 * a + 2 * c + 1]));
+      if (P.g5_in) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          psi[2][c] = (T)-1 * psi[2][c];
+          psi[3][c] = (T)-1 * psi[3][c];
+        }
+      }
+      project<T>(mu, s, psi, hh);
+    }
     link_mul(U, dir < 0, hh, uh);
     reconstruct(mu, s, f, uh, acc);
   }

@@ -437,18 +437,30 @@ __device__ __forceinline__ void mrhs_dir(const DslashParams &P, const MrhsSmem &
     cp_async_wait<D - 1>();
   const int tid = threadIdx.x;
   S ra[24], rb[24];
+  unsigned ua[12], ub[12];  // FP16/BF16: the stored (re, im) pairs
   unsigned dep = 0;
 #pragma unroll
   for (int w = 0; w < WS::NW; w++) {
     const auto va = st.sp[slot][0][w][tid];
     const auto vb = st.sp[slot][1][w][tid];
     dep |= first_bits(va) ^ first_bits(vb);
-    const S *xa = reinterpret_cast<const S *>(&va);
-    const S *xb = reinterpret_cast<const S *>(&vb);
+    if constexpr (IsHalf<S>::value) {
+      static_assert(WS::W == 16, "FP16/BF16 spinors are three 16-byte words");
+      const unsigned *xa = reinterpret_cast<const unsigned *>(&va);
+      const unsigned *xb = reinterpret_cast<const unsigned *>(&vb);
 #pragma unroll
-    for (int j = 0; j < WS::PER; j++) {
-      ra[w * WS::PER + j] = xa[j];
-      rb[w * WS::PER + j] = xb[j];
+      for (int j = 0; j < 4; j++) {
+        ua[w * 4 + j] = xa[j];
+        ub[w * 4 + j] = xb[j];
+      }
+    } else {
+      const S *xa = reinterpret_cast<const S *>(&va);
+      const S *xb = reinterpret_cast<const S *>(&vb);
+#pragma unroll
+      for (int j = 0; j < WS::PER; j++) {
+        ra[w * WS::PER + j] = xa[j];
+        rb[w * WS::PER + j] = xb[j];
+      }
     }
   }
   float sca = 1.0f, scb = 1.0f;
@@ -463,20 +475,32 @@ __device__ __forceinline__ void mrhs_dir(const DslashParams &P, const MrhsSmem &
   else
     mrhs_issue<S, NT>(P, st, g, slot, K + D - 8, true, dep);
   if (!g.ok) return;
-  c2 psi[4][3];
-#pragma unroll
-  for (int s = 0; s < 4; s++)
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-      psi[s][c] = {make_float2(to_f(ra[6 * s + 2 * c]), to_f(rb[6 * s + 2 * c])),
-                   make_float2(to_f(ra[6 * s + 2 * c + 1]), to_f(rb[6 * s + 2 * c + 1]))};
   const bool wrap = (MU == 3) && P.g.tbc && (DIR > 0 ? g.xc.x[3] == P.g.L[3] - 1 : g.xc.x[3] == 0);
   const float fw = wrap ? -fb : fb;
   const float2 f = make_float2(fw * sca, fw * scb);
   const float2 flo = mul2(bc2(S_ * g5h), f);
   const float2 spp = bc2(S_ * sp);
   c2 h[2][3];
-  project2<MU>(psi, spp, neg2(spp), h);
+  if constexpr (IsHalf<S>::value) {
+    // each right-hand side projected on its stored pairs (project_packed),
+    // then the two packed into FP32 pairs
+    cx<float> ha[2][3], hb[2][3];
+    project_packed<S>(MU, S_ * sp, ua, ha);
+    project_packed<S>(MU, S_ * sp, ub, hb);
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) h[a][c] = {make_float2(ha[a][c].r, hb[a][c].r), make_float2(ha[a][c].i, hb[a][c].i)};
+  } else {
+    c2 psi[4][3];
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+        psi[s][c] = {make_float2(to_f(ra[6 * s + 2 * c]), to_f(rb[6 * s + 2 * c])),
+                     make_float2(to_f(ra[6 * s + 2 * c + 1]), to_f(rb[6 * s + 2 * c + 1]))};
+    project2<MU>(psi, spp, neg2(spp), h);
+  }
   link_recon2<MU, (DIR < 0)>(sm, K, lane, h, f, flo, neg2(flo), acc);
 }
 

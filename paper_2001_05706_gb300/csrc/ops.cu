@@ -166,12 +166,17 @@ static int pick_variant(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int 
       if (x == v) return v;
   }
   if (cand.size() == 1) return cand[0];
-  const TuneKey key((int)prec, recon, mode, nrhs, c->Vh);
+  // keyed on the launch's site count: a launch over part of the parity (the
+  // host pipeline's chunks, a domain's slices) tunes apart from a whole one
+  const TuneKey key((int)prec, recon, mode, nrhs, P.h1 - P.h0);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_tune_loaded) tune_load();
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) return it->second;
+    if (it != g_tune.end()) {
+      for (int x : cand)  // a cached choice outside this launch's candidates is ignored
+        if (x == it->second) return x;
+    }
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
