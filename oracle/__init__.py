@@ -5,8 +5,10 @@ CPU-baseline leg of ``bench.py`` may import this package; the library under
 ``paper_2001_05706_gb300`` never does, and this package never imports it.
 
 The arithmetic is in ``oracle.c`` (plain C99 complex, FP64, full 4x4 spin
-matrices, Gauss-Jordan inverses, sequential reductions).  This wrapper only
-marshals numpy arrays.  The paper prints no formula; each function follows
+matrices, Gauss-Jordan inverses, sequential reductions).  This wrapper
+marshals numpy arrays; the overlap-eigensystem functions at its end compose
+oracle.c's H_W with numpy's dense Hermitian eigendecomposition (the exact
+sign function and the chirality-sector spectrum, small lattices only).  The paper prints no formula; each function follows
 the standard definition of the operator the paper names (Table 1:
 QUDA_DIRAC_WILSON, QUDA_DIRAC_CLOVER; the overlap inverter of Secs. 1, 3, 4).
 Conventions are listed at the top of ``oracle.c``.
@@ -478,3 +480,73 @@ def eigen_residuals(dims, U, rho, lam, vecs, tbc=1):
     Z = np.asarray(vecs).reshape(k, -1)
     ortho = np.abs(Z.conj() @ Z.T - np.eye(k)).max()
     return res, ortho
+
+
+# ---- overlap eigensystem (Sec. 4: the low eigenpairs of D_ov) ---------------
+#
+# D_ov(0) = rho (1 + g5 eps) is normal and g5-Hermitian, so D_ov(0)^dag D_ov(0)
+# commutes with g5: its eigenvectors can be taken chiral, and on the chirality
+# sector s (P_s = (1 + s g5)/2) it is 2 rho^2 P_s (1 + s eps) P_s.  A vector
+# chi of sector s with eigenvalue mu belongs to the pair of D_ov(0)
+# eigenvalues lambda = mu / (2 rho) +- i sqrt(mu - mu^2 / (4 rho^2)).
+
+def chirality_indices(dims, sector):
+    """Flattened canonical-spinor indices of chirality sector s: spins 0, 1
+    (s = +1) or 2, 3 (s = -1), g5 = diag(1, 1, -1, -1) in the DeGrand-Rossi
+    basis."""
+    V = int(np.prod(dims))
+    spin = np.tile(np.repeat(np.arange(4), 3), V)
+    return np.nonzero(spin < 2 if sector > 0 else spin >= 2)[0]
+
+
+def overlap_dense(dims, U, rho, m=0.0, tbc=1):
+    """The dense matrix of D_ov(m) = (1 - m/(2 rho)) rho (1 + g5 eps(H_W)) + m
+    with the exact sign function eps = Q sign(Lambda) Q^H of a dense
+    eigendecomposition of H_W (small lattices only)."""
+    H = hw_dense(dims, U, rho, tbc)
+    H = 0.5 * (H + H.conj().T)
+    lam, Q = np.linalg.eigh(H)
+    eps = (Q * np.sign(lam)) @ Q.conj().T
+    N = H.shape[0]
+    g5 = np.ones(N)
+    g5[chirality_indices(dims, -1)] = -1.0
+    return (1.0 - m / (2.0 * rho)) * rho * (np.eye(N) + g5[:, None] * eps) + m * np.eye(N)
+
+
+def overlap_sector_eigensystem(dims, U, rho, k, sector, tbc=1):
+    """The k lowest eigenpairs (mu_i, chi_i) of D_ov(0)^dag D_ov(0) on the
+    chirality-s subspace (dense Hermitian eigendecomposition of the restricted
+    matrix), ascending; chi_i returned as full spinors, zero in the other
+    chirality."""
+    D = overlap_dense(dims, U, rho, 0.0, tbc)
+    idx = chirality_indices(dims, sector)
+    M = (D.conj().T @ D)[np.ix_(idx, idx)]
+    M = 0.5 * (M + M.conj().T)
+    mu, W = np.linalg.eigh(M)
+    N = D.shape[0]
+    vecs = np.zeros((k, N), dtype=_c)
+    vecs[:, idx] = W[:, :k].T
+    return mu[:k], vecs.reshape((k,) + spinor_shape(dims))
+
+
+def apply_sector_normal(dims, U, rho, sector, chi, a, b, c, lam=(), vecs=(), tbc=1):
+    """P_s D_ov(0)^dag D_ov(0) P_s chi = 2 rho^2 P_s (chi + s eps chi), with the
+    polynomial sign function of apply_sign (the operator the GPU eigensolver
+    uses)."""
+    chi = np.array(chi, dtype=_c)
+    keep = spinor_shape(dims)[-2]  # 4 spins
+    mask = np.zeros(keep, dtype=bool)
+    mask[[0, 1] if sector > 0 else [2, 3]] = True
+    chi[..., ~mask, :] = 0
+    e = apply_sign(dims, U, rho, chi, a, b, c, lam=lam, vecs=vecs, tbc=tbc)
+    out = 2.0 * rho * rho * (chi + sector * e)
+    out[..., ~mask, :] = 0
+    return out
+
+
+def overlap_pair_eigenvalues(mu, rho):
+    """The eigenvalue pair lambda = re +- i im of D_ov(0) belonging to the
+    D_ov(0)^dag D_ov(0) eigenvalue mu (0 <= mu <= 4 rho^2)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    re = mu / (2.0 * rho)
+    return re, np.sqrt(np.maximum(mu - re * re, 0.0))

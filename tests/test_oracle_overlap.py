@@ -159,3 +159,74 @@ def test_ginsparg_wilson(interacting):
     Dd = oracle.apply_overlap(dims, U, RHO, 0.05, u, a, B_MAX, c, lam=lam, vecs=vecs, dagger=True)
     Dv = oracle.apply_overlap(dims, U, RHO, 0.05, v, a, B_MAX, c, lam=lam, vecs=vecs)
     assert abs(np.vdot(u, Dv) - np.vdot(Dd, v)) < 1e-9 * abs(np.vdot(u, Dv))
+
+
+# ---- the overlap eigensystem: chirality sectors of D_ov(0)^dag D_ov(0) -----
+
+def test_sector_spectrum_free_field_closed_form():
+    """Unit links: per momentum D_ov(p) = rho (1 + D_W(p)/N(p)) (colour
+    diagonal), so the sector-s spectrum is the union over p of the eigenvalues
+    of the spin-s block of D_ov(p)^dag D_ov(p), three times each."""
+    dims = (2, 2, 2, 4)
+    U = gen.unit_gauge(dims)
+    V = int(np.prod(dims))
+    g = [oracle.gamma(mu) for mu in range(4)]
+    for s in (+1, -1):
+        blk = [0, 1] if s > 0 else [2, 3]
+        expect = []
+        for p in all_momenta(dims, 1):
+            DW = (4 - RHO - np.cos(p).sum()) * np.eye(4) + 1j * sum(g[mu] * np.sin(p[mu]) for mu in range(4))
+            D = RHO * (np.eye(4) + DW / np.sqrt(_free_N2(p)))
+            M = (D.conj().T @ D)[np.ix_(blk, blk)]
+            expect += list(np.linalg.eigvalsh(0.5 * (M + M.conj().T))) * 3
+        mu, vecs = oracle.overlap_sector_eigensystem(dims, U, RHO, 6 * V, s)
+        assert np.allclose(mu, np.sort(expect), atol=1e-11)
+        # the vectors are chiral and orthonormal
+        Z = vecs.reshape(6 * V, -1)
+        assert np.abs(Z[:, oracle.chirality_indices(dims, -s)]).max() == 0
+        assert np.abs(Z.conj() @ Z.T - np.eye(6 * V)).max() < 1e-11
+
+
+def test_sector_spectra_pair_up_with_the_overlap_spectrum():
+    """Interacting field: D_ov(0)'s eigenvalues lie on the Ginsparg-Wilson
+    circle |lambda - rho| = rho, and the two sectors' spectra together are the
+    moduli |lambda|^2 (each pair lambda, lambda* gives one value per sector;
+    chiral zero modes and lambda = 2 rho only one)."""
+    dims = (2, 2, 2, 2)
+    U = gen.gauge_field(dims, 0.5, 41)
+    V = int(np.prod(dims))
+    D = oracle.overlap_dense(dims, U, RHO)
+    lam = np.linalg.eigvals(D)
+    assert np.abs(np.abs(lam - RHO) - RHO).max() < 1e-11
+    mp, _ = oracle.overlap_sector_eigensystem(dims, U, RHO, 6 * V, +1)
+    mm, _ = oracle.overlap_sector_eigensystem(dims, U, RHO, 6 * V, -1)
+    assert np.allclose(np.sort(np.concatenate([mp, mm])), np.sort(np.abs(lam) ** 2), atol=1e-10)
+    # away from 0 and 4 rho^2 the two sectors carry the same values
+    inner = lambda m: np.sort(m[(m > 1e-8) & (m < 4 * RHO**2 - 1e-8)])
+    assert np.allclose(inner(mp), inner(mm), atol=1e-10)
+    # the pair formula reproduces D_ov(0)'s eigenvalues with Im >= 0
+    re, im = oracle.overlap_pair_eigenvalues(mp, RHO)
+    up = lam[lam.imag >= -1e-12]
+    for r, i in zip(re[:20], im[:20]):
+        assert np.abs(up - (r + 1j * i)).min() < 1e-8
+
+
+def test_sector_vectors_against_the_polynomial_operator():
+    """The dense sector eigenvectors are eigenvectors of the operator the GPU
+    eigensolver applies, 2 rho^2 P_s (1 + s eps) P_s with the polynomial sign
+    function, to the polynomial's accuracy; and D_ov(0) maps a sector vector to
+    a D^dag D eigenvector of the same eigenvalue."""
+    dims = (2, 2, 2, 4)
+    U = gen.gauge_field(dims, 0.4, 43)
+    k = 10
+    lam_w, vecs_w = oracle.low_modes_dense(dims, U, RHO, 5)
+    a = lam_w[4] ** 2
+    n, c = oracle.cheb_degree(a, B_MAX, 1e-12)
+    D = oracle.overlap_dense(dims, U, RHO)
+    for s in (+1, -1):
+        mu, chi = oracle.overlap_sector_eigensystem(dims, U, RHO, k, s)
+        for i in range(k):
+            h = oracle.apply_sector_normal(dims, U, RHO, s, chi[i], a, B_MAX, c, lam=lam_w[:4], vecs=vecs_w[:4])
+            assert np.linalg.norm((h - mu[i] * chi[i]).ravel()) < 1e-9
+            w = D @ chi[i].ravel()
+            assert np.linalg.norm(D.conj().T @ (D @ w) - mu[i] * w) < 1e-9 * max(1.0, np.linalg.norm(w))
