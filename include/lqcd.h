@@ -329,7 +329,9 @@ typedef enum {
   LQCD_OV_APPLY = 0,      /* out = D_ov(m) in                                          */
   LQCD_OV_APPLY_DAG = 1,  /* out = D_ov(m)^dag in                                      */
   LQCD_OV_SIGN = 2,       /* out = eps(H_W) in                                         */
-  LQCD_OV_SOLVE = 3       /* out = D_ov(m)^-1 in by CG on the normal equations         */
+  LQCD_OV_SOLVE = 3,      /* out = D_ov(m)^-1 in by CG on the normal equations         */
+  LQCD_OV_SOLVE_DEFLATED = 4  /* the same CG started from the exact part of the solution */
+                          /* in the eigensystem of lqcd_overlap_eigen (deflation)      */
 } lqcd_overlap_op;
 
 /* Compute the low modes of H_W (block subspace iteration on H_W^2 with
@@ -363,6 +365,72 @@ lqcd_status lqcd_overlap_lowmodes(lqcd_ctx *ctx, double *vecs, int on_device);
  * final residuals.  Blocks. */
 lqcd_status lqcd_overlap(lqcd_ctx *ctx, double *out, const double *in, int nrhs, int on_device, lqcd_overlap_op op,
                          const lqcd_solve_params *cg, lqcd_solve_info *info);
+
+/* ---- the overlap eigensystem (Sec. 4: 200 pairs of the overlap eigensystem
+ * of a 24^3 x 64 lattice) and the deflated overlap CG ---------------------
+ *
+ * D_ov(0) = rho (1 + g5 eps) is normal and g5-Hermitian, so D_ov(0)^dag D_ov(0)
+ * commutes with g5 = diag(1, 1, -1, -1) (DeGrand-Rossi) and its eigenvectors
+ * can be taken chiral.  On the chirality sector s (P_s = (1 + s g5) / 2) it is
+ * H_s = 2 rho^2 P_s (1 + s eps) P_s, one sign-function application per vector.
+ * An eigenvalue mu of H_s (0 < mu < 4 rho^2) belongs to the eigenvalue pair
+ * lambda = mu / (2 rho) +- i sqrt(mu - mu^2 / (4 rho^2)) of D_ov(0), and its
+ * vector chi has a partner eta = P_-s eps chi / |P_-s eps chi| of the other
+ * sector with the same mu (chiral zero modes and mu = 4 rho^2 have none). */
+#define LQCD_OV_MAX_EV 256
+
+typedef struct {
+  int n_ev;                 /* eigenpairs of H_s wanted, 1..LQCD_OV_MAX_EV                   */
+  int sector;               /* s = +1 (spins 0, 1) or -1 (spins 2, 3)                        */
+  double tol;               /* contract: ||H_s chi - mu chi|| <= tol for every pair (|chi|=1) */
+  int basis;                /* Lanczos basis size; 0: min(max(3 n_ev, n_ev + 48), 511)        */
+  int max_restarts;         /* cap on Lanczos restart cycles                                 */
+  unsigned long long seed;  /* seed of the random start vector                               */
+} lqcd_overlap_eigen_params;
+
+typedef struct {
+  int n_ev;                         /* pairs kept (= params->n_ev on success)                */
+  int n_partners;                   /* of them with a partner in the other sector            */
+  double mu[LQCD_OV_MAX_EV];        /* eigenvalues of D_ov(0)^dag D_ov(0), ascending         */
+  double resid[LQCD_OV_MAX_EV];     /* ||H_s chi - mu chi||, recomputed after convergence    */
+  double lambda_re[LQCD_OV_MAX_EV]; /* the D_ov(0) eigenvalue pair lambda_re +- i lambda_im */
+  double lambda_im[LQCD_OV_MAX_EV];
+  int restarts;                     /* Lanczos restart cycles                                */
+  double sign_applies;              /* sign-function applications (one per vector)          */
+  double seconds;                   /* wall time                                             */
+} lqcd_overlap_eigen_info;
+
+/* The n_ev lowest eigenpairs of H_s for the sign function of the current
+ * lqcd_overlap_setup: thick-restart Lanczos on H_s (double-float basis,
+ * FP64 or double-float sign function per the set-up's `high`), then every
+ * pair's residual recomputed and its partner formed.  The context keeps the
+ * n_ev vectors and their partners (replacing an earlier eigensystem; a new
+ * lqcd_overlap_setup drops it) for LQCD_OV_SOLVE_DEFLATED.  LQCD_ERR_NOCONV if
+ * Lanczos does not converge within max_restarts or a recomputed residual
+ * exceeds tol (info filled either way; no eigensystem is kept);
+ * LQCD_ERR_STATE without an overlap set-up; LQCD_ERR_ARG for bad parameters
+ * or a lattice too small for the basis.  Blocks.  Device memory: the basis,
+ * 2 x (basis + 1) double-float vectors, during the solve; 2 n_ev FP64 vectors
+ * kept. */
+lqcd_status lqcd_overlap_eigen(lqcd_ctx *ctx, const lqcd_overlap_eigen_params *params,
+                               lqcd_overlap_eigen_info *info);
+
+/* Copy the kept eigenvectors (canonical full-lattice spinors, back to back,
+ * host or device): the n_ev sector vectors in the order of info->mu
+ * (partners = 0), or the n_partners partners (partners = 1), in the order of
+ * their sector vectors.  LQCD_ERR_STATE without an eigensystem. */
+lqcd_status lqcd_overlap_eigvecs(lqcd_ctx *ctx, double *vecs, int partners, int on_device);
+
+/* LQCD_OV_SOLVE_DEFLATED: the same mass serves every eigenvector, since
+ * D_ov(m)^dag D_ov(m) = (a^2 + a m / rho) D_ov(0)^dag D_ov(0) + m^2 with
+ * a = 1 - m / (2 rho).  With W the kept vectors and mu'_w their eigenvalues
+ * of D_ov(m)^dag D_ov(m), x0 = sum_w w <w, D_ov(m)^dag b> / mu'_w is the exact
+ * component of the solution in their span (D_ov maps each pair span{chi,
+ * eta} into itself, so this needs only inner products with W); the CG then
+ * solves D_ov(m) e = b - D_ov(m) x0 to the target ||b - D_ov(m) x|| <=
+ * tol ||b|| and returns x = x0 + e (info->iters counts its iterations).  The
+ * mixed CG (cg->inner = LQCD_F32) deflates again at each accepted reliable
+ * update.  A massless zero mode (mu' = 0) is not deflated. */
 
 /* ---- domain decomposition along t: building blocks -------------------- */
 

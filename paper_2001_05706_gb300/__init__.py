@@ -64,7 +64,20 @@ class lqcd_overlap_info(ctypes.Structure):
                 ("degree_inner", ctypes.c_int), ("hw_applies", ctypes.c_double)]
 
 
-LQCD_OV_APPLY, LQCD_OV_APPLY_DAG, LQCD_OV_SIGN, LQCD_OV_SOLVE = 0, 1, 2, 3
+LQCD_OV_APPLY, LQCD_OV_APPLY_DAG, LQCD_OV_SIGN, LQCD_OV_SOLVE, LQCD_OV_SOLVE_DEFLATED = 0, 1, 2, 3, 4
+LQCD_OV_MAX_EV = 256
+
+
+class lqcd_overlap_eigen_params(ctypes.Structure):
+    _fields_ = [("n_ev", ctypes.c_int), ("sector", ctypes.c_int), ("tol", ctypes.c_double), ("basis", ctypes.c_int),
+                ("max_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+class lqcd_overlap_eigen_info(ctypes.Structure):
+    _fields_ = [("n_ev", ctypes.c_int), ("n_partners", ctypes.c_int), ("mu", ctypes.c_double * LQCD_OV_MAX_EV),
+                ("resid", ctypes.c_double * LQCD_OV_MAX_EV), ("lambda_re", ctypes.c_double * LQCD_OV_MAX_EV),
+                ("lambda_im", ctypes.c_double * LQCD_OV_MAX_EV), ("restarts", ctypes.c_int),
+                ("sign_applies", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
 class lqcd_solve_info(ctypes.Structure):
@@ -102,6 +115,8 @@ _sig = {
                          ctypes.POINTER(lqcd_solve_params), ctypes.POINTER(lqcd_solve_info)],
     "lqcd_overlap_setup": [_vp, ctypes.POINTER(lqcd_overlap_params), ctypes.POINTER(lqcd_overlap_info)],
     "lqcd_overlap_lowmodes": [_vp, _vp, _ip],
+    "lqcd_overlap_eigen": [_vp, ctypes.POINTER(lqcd_overlap_eigen_params), ctypes.POINTER(lqcd_overlap_eigen_info)],
+    "lqcd_overlap_eigvecs": [_vp, _vp, _ip, _ip],
     "lqcd_overlap": [_vp, _vp, _vp, _ip, _ip, _ip, ctypes.POINTER(lqcd_solve_params),
                      ctypes.POINTER(lqcd_solve_info)],
 }
@@ -344,6 +359,25 @@ def lqcd_overlap_setup(ctx, params, raise_on_noconv=True):
 def lqcd_overlap_lowmodes(ctx, vecs):
     p, dev = _buf(vecs)
     _check(_lib.lqcd_overlap_lowmodes(ctx, p, dev))
+
+
+def overlap_eigen_params(n_ev=20, sector=1, tol=1e-9, basis=0, max_restarts=200, seed=11):
+    return lqcd_overlap_eigen_params(n_ev, sector, tol, basis, max_restarts, seed)
+
+
+def lqcd_overlap_eigen(ctx, params, raise_on_noconv=True):
+    """The n_ev lowest eigenpairs of D_ov(0)^dag D_ov(0) in one chirality
+    sector; returns (status, info)."""
+    info = lqcd_overlap_eigen_info()
+    st = _lib.lqcd_overlap_eigen(ctx, ctypes.byref(params), ctypes.byref(info))
+    if st != LQCD_OK and (raise_on_noconv or st != LQCD_ERR_NOCONV):
+        _check(st)
+    return st, info
+
+
+def lqcd_overlap_eigvecs(ctx, vecs, partners=False):
+    p, dev = _buf(vecs)
+    _check(_lib.lqcd_overlap_eigvecs(ctx, p, int(bool(partners)), dev))
 
 
 def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):

@@ -22,6 +22,7 @@
 //    normal equations for the inverse.
 
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -52,6 +53,14 @@ struct OverlapState {
   size_t dsmall_n = 0;
   double *gpart = nullptr;  // per-chunk partials of the Gram kernel
   size_t gpart_n = 0;
+  // eigensystem of D_ov(0)^dag D_ov(0) (lqcd_overlap_eigen): ev_n vectors of
+  // chirality ev_sector, then ev_np partners of the other chirality (FULL FP64)
+  lqcd_field *ev = nullptr;
+  int ev_n = 0, ev_np = 0, ev_sector = 0;
+  std::vector<double> ev_mu;    // eigenvalue of each column of ev
+  std::vector<double> ev_c;     // <chi_i, eps chi_i> of each sector vector
+  std::vector<double> ev_pn;    // |P_-s eps chi_i| (0: no partner)
+  std::vector<int> ev_partner;  // column of chi_i's partner in ev, or -1
 };
 
 void overlap_free(lqcd_ctx *c) {
@@ -59,6 +68,7 @@ void overlap_free(lqcd_ctx *c) {
   if (!s) return;
   if (s->vecs) lqcd_field_destroy(s->vecs);
   if (s->vecs32) lqcd_field_destroy(s->vecs32);
+  if (s->ev) lqcd_field_destroy(s->ev);
   if (s->gpart) cudaFree(s->gpart);
   if (s->dsmall) cudaFree(s->dsmall);
   delete s;
@@ -467,6 +477,139 @@ void jacobi_eigh(int m, std::vector<zc> &A, std::vector<zc> &V, std::vector<doub
   }
   w.resize(m);
   for (int i = 0; i < m; i++) w[i] = at(i, i).real();
+}
+
+// Hermitian eigendecomposition for larger projected matrices (the Lanczos
+// Rayleigh-Ritz step, where the cyclic Jacobi method's O(m^3) per sweep,
+// times ten sweeps, dominated a 511-column restart):
+// Householder reduction to Hermitian tridiagonal form, a diagonal phase
+// transformation to a real symmetric tridiagonal, and the implicit QL method
+// with Wilkinson shifts (Givens rotations accumulated into the eigenvectors).
+// A (column-major, destroyed), V the eigenvectors as columns, w the
+// eigenvalues (unsorted, as the Jacobi routine).  False if QL stalls.
+bool tridiag_eigh(int m, std::vector<zc> &A, std::vector<zc> &V, std::vector<double> &w) {
+  auto at = [&](int i, int j) -> zc & { return A[i + (size_t)m * j]; };
+  std::vector<zc> Q((size_t)m * m, zc(0, 0)), off(m, zc(0, 0)), v(m), p(m), q(m);
+  for (int i = 0; i < m; i++) Q[i + (size_t)m * i] = 1.0;
+  std::vector<double> d(m), e(m, 0.0);
+  // 1. A = Q T Q^H: for column k, H = I - 2 u u^H maps A[k+1:, k] to alpha e_1
+  for (int k = 0; k + 2 < m; k++) {
+    const int n = m - k - 1;  // length of the trailing block
+    double xn = 0;
+    for (int i = 0; i < n; i++) xn += std::norm(at(k + 1 + i, k));
+    xn = std::sqrt(xn);
+    if (xn == 0.0) continue;
+    const zc x0 = at(k + 1, k);
+    const zc ph = std::abs(x0) > 0 ? x0 / std::abs(x0) : zc(1, 0);
+    const zc alpha = -ph * xn;
+    for (int i = 0; i < n; i++) v[i] = at(k + 1 + i, k);
+    v[0] -= alpha;
+    double vn = 0;
+    for (int i = 0; i < n; i++) vn += std::norm(v[i]);
+    vn = std::sqrt(vn);
+    if (vn == 0.0) continue;
+    for (int i = 0; i < n; i++) v[i] /= vn;
+    // trailing block B <- H B H = B - 2 (v w^H + w v^H), w = B v - (v^H B v) v
+    for (int i = 0; i < n; i++) {
+      zc s = 0;
+      for (int j = 0; j < n; j++) s += at(k + 1 + i, k + 1 + j) * v[j];
+      p[i] = s;
+    }
+    zc vp = 0;
+    for (int i = 0; i < n; i++) vp += std::conj(v[i]) * p[i];
+    for (int i = 0; i < n; i++) q[i] = p[i] - vp.real() * v[i];
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < n; i++)
+        at(k + 1 + i, k + 1 + j) -= 2.0 * (v[i] * std::conj(q[j]) + q[i] * std::conj(v[j]));
+    // the column and row k: alpha below the diagonal, zeros under it
+    at(k + 1, k) = alpha;
+    at(k, k + 1) = std::conj(alpha);
+    for (int i = 1; i < n; i++) at(k + 1 + i, k) = at(k, k + 1 + i) = 0.0;
+    // Q <- Q H on columns k + 1 ..
+    for (int r = 0; r < m; r++) {
+      zc s = 0;
+      for (int j = 0; j < n; j++) s += Q[r + (size_t)m * (k + 1 + j)] * v[j];
+      for (int j = 0; j < n; j++) Q[r + (size_t)m * (k + 1 + j)] -= 2.0 * s * std::conj(v[j]);
+    }
+  }
+  // 2. T = D S D^H with S real: D_0 = 1, D_{k+1} = D_k t_k / |t_k| for the
+  //    subdiagonal t_k = T[k+1][k]; S has |t_k| below the diagonal
+  std::vector<zc> ph(m, zc(1, 0));
+  for (int k = 0; k < m; k++) d[k] = at(k, k).real();
+  for (int k = 0; k + 1 < m; k++) {
+    const zc t = at(k + 1, k);
+    e[k] = std::abs(t);
+    ph[k + 1] = e[k] > 0 ? ph[k] * (t / e[k]) : ph[k];
+  }
+  // 3. implicit QL on (d, e): Z accumulates the rotations, S = Z diag(d) Z^T
+  std::vector<double> Z((size_t)m * m, 0.0);
+  for (int i = 0; i < m; i++) Z[i + (size_t)m * i] = 1.0;
+  for (int l = 0; l < m; l++) {
+    for (int iter = 0;; iter++) {
+      int mm = l;
+      for (; mm + 1 < m; mm++) {  // first negligible subdiagonal entry at or after l
+        const double dd = std::fabs(d[mm]) + std::fabs(d[mm + 1]);
+        if (std::fabs(e[mm]) <= 1e-16 * dd) break;
+      }
+      if (mm == l) break;
+      if (iter == 100) return false;
+      // Wilkinson shift from the leading 2 x 2 block of the unreduced part
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      int i = mm - 1;
+      bool split = false;
+      for (; i >= l; i--) {  // chase the bulge from the bottom of the block up to l
+        const double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {  // the block split: deflate and restart on it
+          d[i + 1] -= pp;
+          e[mm] = 0.0;
+          split = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
+        for (int k = 0; k < m; k++) {
+          const double z1 = Z[k + (size_t)m * (i + 1)], z0 = Z[k + (size_t)m * i];
+          Z[k + (size_t)m * (i + 1)] = s * z0 + c * z1;
+          Z[k + (size_t)m * i] = c * z0 - s * z1;
+        }
+      }
+      if (split) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[mm] = 0.0;
+    }
+  }
+  // 4. eigenvectors of A: Q D Z
+  V.assign((size_t)m * m, zc(0, 0));
+  for (int j = 0; j < m; j++)
+    for (int k = 0; k < m; k++) {
+      const zc f = ph[k] * Z[k + (size_t)m * j];
+      if (f == zc(0, 0)) continue;
+      for (int r = 0; r < m; r++) V[r + (size_t)m * j] += Q[r + (size_t)m * k] * f;
+    }
+  w = d;
+  return true;
+}
+
+// the Hermitian eigensolver of the Lanczos Rayleigh-Ritz steps: cyclic Jacobi
+// up to 32 columns, Householder + QL beyond (x86 host: 0.013 s against 0.5 s at
+// 129 columns, 1.0 s against 40 s at 511; eigenvalues agree to ~1e-14 |A|)
+void herm_eigh(int m, std::vector<zc> &A, std::vector<zc> &V, std::vector<double> &w) {
+  if (m > 32) {
+    std::vector<zc> B = A;
+    if (tridiag_eigh(m, B, V, w)) return;
+  }
+  jacobi_eigh(m, A, V, w);
 }
 
 // Cholesky G = R^H R of a Hermitian positive definite m x m matrix and the
@@ -924,8 +1067,15 @@ lqcd_status copy_rhs(lqcd_ctx *c, lqcd_field *dst, const lqcd_field *src, int k)
   return LQCD_OK;
 }
 
+lqcd_status deflate(lqcd_ctx *c, int nrhs, lqcd_field *r, lqcd_field *x, bool x_zero, const std::vector<char> &mask);
+
+// deflate: with the context's eigensystem, each accepted reliable update also
+// adds the exact low-mode part of the correction for the new FP64 residual
+// (no operator application; the inner FP32 iteration restarts from that
+// residual, whose low modes its rounding and FP32 sign function would
+// otherwise bring back); the next update's FP64 residual checks it
 lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field *x, const lqcd_solve_params *cg,
-                          lqcd_solve_info *inf, const std::vector<double> &bn2) {
+                          lqcd_solve_info *inf, const std::vector<double> &bn2, bool deflated = false) {
   FieldGuard g;
   lqcd_field *r64, *t64, *xtry, *xlo, *r, *s, *p, *q;
   for (lqcd_field **f : {&r64, &t64, &xtry}) {
@@ -1030,6 +1180,11 @@ lqcd_status ov_cgls_mixed(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field
         parked[k] = 0;
       }
       if (done) break;
+      if (deflated) {
+        std::vector<char> mask(nrhs, 0);
+        for (int k = 0; k < nrhs; k++) mask[k] = active[k] && fr[k] > 0;
+        LQ_TRY(deflate(c, nrhs, r64, x, false, mask));
+      }
       LQ_TRY(scale_full(c, p, p, fp, nrhs));
       LQ_TRY(scale_full(c, r, r64, fr, nrhs));
       LQ_TRY(dov_apply(c, nrhs, r, s, 1));
@@ -1086,6 +1241,16 @@ struct LanczosResult {
   bool converged = false;
 };
 
+// dst columns kd .. kd + n - 1 = src columns ks .. (same precision)
+lqcd_status copy_col_range(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src, int ks, int n) {
+  const size_t bytes = (size_t)cwords(src) * celem(src);
+  for (int p = 0; p < 2; p++)
+    LQ_CU(cudaMemcpyAsync(static_cast<char *>(dst->data[p]) + bytes * kd,
+                          static_cast<const char *>(src->data[p]) + bytes * ks, bytes * n, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  return LQCD_OK;
+}
+
 // dst column kd = src column ks (same precision)
 lqcd_status copy_col(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src, int ks) {
   const size_t bytes = (size_t)cwords(src) * celem(src);
@@ -1104,7 +1269,7 @@ lqcd_status copy_col(lqcd_ctx *c, lqcd_field *dst, int kd, const lqcd_field *src
 // FP32 pipes they are bound by the basis' bytes.  Elements are indexed over
 // both parities: e < n is parity 0, e - n parity 1.
 constexpr int kLzT = 256;
-constexpr int kLzMaxP = 160;  // basis columns a kernel can take (mmax + 1 <= 129)
+constexpr int kLzMaxP = 512;  // basis columns a kernel can take (mmax + 1 <= 512)
 
 struct dfc {
   df re, im;
@@ -1223,25 +1388,38 @@ struct LzOps {
   }
 };
 
-// X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors of H_W^2
-lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int want, int kkeep, int mmax,
-                             lqcd_field *X, FieldGuard &g, LanczosResult &out) {
-  OverlapState &S = *c->ov;
+// A Hermitian operator for the thick-restart Lanczos: w = A x on single
+// double-float columns, `per_call` operator applications counted per call;
+// `start` (may be empty) maps the FP64 random start vector into the subspace
+// A acts on (a chirality sector, say) before it is normalised.
+struct LzSpec {
+  std::function<lqcd_status(lqcd_field *x, lqcd_field *w)> apply;
+  int per_call = 1;
+  std::function<lqcd_status(lqcd_field *x64)> start;
+  double tol = 1e-10;    // Ritz residual estimate beta_m |q_{m,i}| of each wanted pair
+  int max_cycles = 100;  // restart cycles
+  unsigned long long seed = 1;
+};
+
+// Thick-restart Lanczos for the lowest eigenpairs of a Hermitian operator:
+// X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors
+// (kneed >= want: a cluster straddling the want-th value is kept whole) and
+// ritz (may be NULL) their Ritz values.
+lqcd_status lanczos_lowest(lqcd_ctx *c, const LzSpec &sp, int want, int kkeep, int mmax, lqcd_field *X, FieldGuard &g,
+                           LanczosResult &out, std::vector<double> *ritz) {
   if (mmax + 1 > kLzMaxP) return set_error(LQCD_ERR_ARG, "Lanczos basis of %d vectors too large", mmax + 1);
-  // the basis and the vector H_W^2 acts on in double-float; FP64 copies for an FP64 H_W
-  lqcd_field *V, *V2, *xd, *td, *wd, *x64 = nullptr, *t64 = nullptr;
+  // the basis and the vector the operator acts on in double-float
+  lqcd_field *V, *V2, *xd, *wd, *x64 = nullptr;
   for (lqcd_field **f : {&V, &V2}) {
     LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, mmax + 1, f));
     g.f.push_back(*f);
   }
-  for (lqcd_field **f : {&xd, &td, &wd}) {
+  for (lqcd_field **f : {&xd, &wd}) {
     LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, 1, f));
     g.f.push_back(*f);
   }
   LQ_TRY(new_full(c, 1, &x64));
   g.f.push_back(x64);
-  LQ_TRY(new_full(c, 1, &t64));
-  g.f.push_back(t64);
   const long n = cwords(V);
   const long gx = std::min<long>((2 * n + kLzT - 1) / kLzT, (c->Vh + 31) / 32);
   LQ_TRY(ensure_partials(c, 2 * (mmax + 1)));
@@ -1251,9 +1429,10 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
     const long nd = 2L * n;
     for (int p = 0; p < 2; p++) {
       gauss_fill_kernel<<<(unsigned)((nd / 2 + kT - 1) / kT), kT, 0, c->stream>>>((double *)x64->data[p], nd,
-                                                                                   prm->seed * 2 + p + 1);
+                                                                                   sp.seed * 2 + p + 1);
       LQ_CU(cudaGetLastError());
     }
+    if (sp.start) LQ_TRY(sp.start(x64));
     std::vector<double> n2;
     LQ_TRY(field_norms(c, x64, 1, n2));
     LQ_TRY(convert_full(c, wd, x64, 1, 1.0 / std::sqrt(n2[0])));
@@ -1278,18 +1457,10 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
   int j0 = 0;
   for (;;) {
     for (int j = j0; j < mmax; j++) {
-      // w = H_W^2 v_j
+      // w = A v_j
       LQ_TRY(copy_col(c, xd, 0, V, j));
-      if (S.df) {
-        LQ_TRY(hw(c, 1, td, xd));
-        LQ_TRY(hw(c, 1, wd, td));
-      } else {
-        LQ_TRY(convert_full(c, x64, xd, 1));
-        LQ_TRY(hw(c, 1, t64, x64));
-        LQ_TRY(hw(c, 1, x64, t64));
-        LQ_TRY(convert_full(c, wd, x64, 1));
-      }
-      out.applies += 2;
+      LQ_TRY(sp.apply(xd, wd));
+      out.applies += sp.per_call;
       // two passes of classical Gram-Schmidt against v_0 .. v_j, then
       // v_{j+1} = w / |w|, all on the stream; the host reads the
       // coefficients and |w|^2 once
@@ -1322,7 +1493,7 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
         W[jj + (size_t)m * i] = std::conj(avg);
       }
     std::vector<double> mu;
-    jacobi_eigh(m, W, Q, mu);
+    herm_eigh(m, W, Q, mu);
     std::vector<int> order(m);
     for (int i = 0; i < m; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] < mu[y]; });
@@ -1340,17 +1511,18 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
     for (int i = 0; i < kneed; i++) {
       const double r = beta_m * std::abs(Qs[m - 1 + (size_t)m * i]);
       worst = std::max(worst, r);
-      conv &= r <= prm->eig_tol;
+      conv &= r <= sp.tol;
     }
     if (kOvTrace)
       std::fprintf(stderr, "lqcd overlap: Lanczos cycle %d worst %.3e kneed %d mu[kneed-1] %.6f mu[kkeep-1] %.6f\n",
                    out.cycles, worst, kneed, mus[kneed - 1], mus[kkeep - 1]);
     LQ_TRY(to_dev(c, Qs, d));
-    if (conv || out.cycles >= prm->max_filter) {
+    if (conv || out.cycles >= sp.max_cycles) {
       LQ_TRY(ops.rotate(V, m, d, kneed, V2));
       LQ_TRY(convert_full(c, X, V2, kneed));
       out.kneed = kneed;
       out.converged = conv;
+      if (ritz) ritz->assign(mus.begin(), mus.begin() + kneed);
       return LQCD_OK;
     }
     // thick restart: V2 = [V Q_k, v_m]; projected matrix diag(theta) bordered by beta_m Q_{m-1,i}
@@ -1364,6 +1536,131 @@ lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int wa
     }
     j0 = kkeep;
   }
+}
+
+// X (FP64 FULL, >= kkeep columns) receives the kneed lowest Ritz vectors of H_W^2
+lqcd_status lowmodes_lanczos(lqcd_ctx *c, const lqcd_overlap_params *prm, int want, int kkeep, int mmax,
+                             lqcd_field *X, FieldGuard &g, LanczosResult &out) {
+  OverlapState &S = *c->ov;
+  lqcd_field *td, *x64, *t64;
+  LQ_TRY(lqcd_field_create(c, LQCD_DF64, LQCD_FULL, 1, &td));
+  g.f.push_back(td);
+  LQ_TRY(new_full(c, 1, &x64));
+  g.f.push_back(x64);
+  LQ_TRY(new_full(c, 1, &t64));
+  g.f.push_back(t64);
+  LzSpec sp;
+  sp.per_call = 2;
+  sp.tol = prm->eig_tol;
+  sp.max_cycles = prm->max_filter;
+  sp.seed = prm->seed;
+  sp.apply = [&](lqcd_field *xd, lqcd_field *wd) -> lqcd_status {
+    if (S.df) {  // H_W in double-float
+      LQ_TRY(hw(c, 1, td, xd));
+      return hw(c, 1, wd, td);
+    }
+    LQ_TRY(convert_full(c, x64, xd, 1));
+    LQ_TRY(hw(c, 1, t64, x64));
+    LQ_TRY(hw(c, 1, x64, t64));
+    return convert_full(c, wd, x64, 1);
+  };
+  return lanczos_lowest(c, sp, want, kkeep, mmax, X, g, out, nullptr);
+}
+
+
+// ---- the overlap eigensystem and the deflated overlap CG -------------------
+
+// columns [k0, k0 + n) of a FULL field as a field of its own (no ownership)
+lqcd_field col_view(const lqcd_field *f, int k0, int n) {
+  lqcd_field v = *f;
+  for (int p = 0; p < 2; p++) v.data[p] = col(f, p, k0);
+  for (int p = 0; p < 2; p++) v.scale[p] = nullptr;
+  v.nrhs = n;
+  v.alloc = nullptr;
+  v.scale_alloc = nullptr;
+  return v;
+}
+
+// keep chirality sector s (g5 = diag(1, 1, -1, -1): s = +1 spins 0, 1, s = -1
+// spins 2, 3) of the first nrhs columns of a FULL FP64 or double-float field:
+// a column's spins 0, 1 are its complex words 0-5, spins 2, 3 words 6-11
+lqcd_status chiral_project(lqcd_ctx *c, lqcd_field *f, int nrhs, int sector) {
+  if (celem(f) != 16) return set_error(LQCD_ERR_ARG, "chiral projection of a field of precision %d", (int)f->prec);
+  const size_t half = 6 * (size_t)f->Vh * 16, colb = (size_t)cwords(f) * 16;
+  for (int p = 0; p < 2; p++)
+    LQ_CU(cudaMemset2DAsync(static_cast<char *>(f->data[p]) + (sector > 0 ? half : 0), colb, 0, half, nrhs,
+                            c->stream));
+  return LQCD_OK;
+}
+
+// Deflation with the kept eigensystem.  D_ov(0) maps each pair span{chi, eta}
+// into itself: with eps chi = c chi + n eta (c = <chi, eps chi>, n = |P_-s eps
+// chi|), g5 = s on chi's sector and -s on eta's,
+//   D_ov(0) chi = rho ((1 + s c) chi - s n eta),  D_ov(0) eta = rho (s n chi + (1 + s c) eta),
+// so D(m) = a D_ov(0) + m (a = 1 - m / (2 rho)) is the real 2 x 2 matrix
+// M = [[A, B], [-B, A]], A = a rho (1 + s c) + m, B = a rho s n, on it (1 x 1,
+// A, for an unpaired chi) and M^T M = mu' = A^2 + B^2.  For a residual r the
+// least-squares correction in the span is x_W = W M^T (W^H r) / mu' and
+// D(m) x_W = W (W^H r): x += x_W and r -= W (W^H r) need one Gram product and
+// two rotations, no operator application.  Columns k with mask[k] = 0 are left
+// alone; a massless zero mode (mu' = 0) is not deflated.
+lqcd_status deflate(lqcd_ctx *c, int nrhs, lqcd_field *r, lqcd_field *x, bool x_zero, const std::vector<char> &mask) {
+  OverlapState &S = *c->ov;
+  const int nw = S.ev_n + S.ev_np, sg = S.ev_sector;
+  const double rho = S.prm.rho, m = S.prm.mass, a = 1.0 - m / (2.0 * rho);
+  double2 *d;
+  LQ_TRY(small_scratch(c, (size_t)nw * nrhs, &d));
+  LQ_TRY(gram(c, S.ev, nw, r, nrhs, d));  // G = W^H r, nw x nrhs
+  std::vector<zc> G, Z((size_t)nw * nrhs, zc(0, 0));
+  LQ_TRY(to_host(c, d, (size_t)nw * nrhs, G));
+  for (int k = 0; k < nrhs; k++) {
+    zc *g = &G[(size_t)nw * k], *z = &Z[(size_t)nw * k];
+    if (!mask[k]) {
+      for (int w = 0; w < nw; w++) g[w] = 0;
+      continue;
+    }
+    for (int i = 0; i < S.ev_n; i++) {
+      const int j = S.ev_partner[i];
+      const double A = a * rho * (1.0 + sg * S.ev_c[i]) + m, B = j >= 0 ? a * rho * sg * S.ev_pn[i] : 0.0;
+      const double mu = A * A + B * B;
+      if (!(mu > 1e-14)) {  // a massless zero mode
+        g[i] = 0;
+        if (j >= 0) g[j] = 0;
+        continue;
+      }
+      if (j < 0) {
+        z[i] = g[i] * (A / mu);
+      } else {
+        z[i] = (A * g[i] - B * g[j]) / mu;
+        z[j] = (B * g[i] + A * g[j]) / mu;
+      }
+    }
+  }
+  // x (+)= W Z, r -= W G, in chunks of the rotation kernel's width
+  for (int pass = 0; pass < 2; pass++) {
+    const std::vector<zc> &C = pass == 0 ? Z : G;
+    lqcd_field *t = pass == 0 ? x : r;
+    for (int k0 = 0; k0 < nw; k0 += kRMaxP) {
+      const int pc = std::min(kRMaxP, nw - k0);
+      std::vector<zc> M((size_t)pc * nrhs);
+      for (int k = 0; k < nrhs; k++)
+        for (int w = 0; w < pc; w++) M[w + (size_t)pc * k] = C[k0 + w + (size_t)nw * k];
+      LQ_TRY(to_dev(c, M, d));
+      const lqcd_field Wv = col_view(S.ev, k0, pc);
+      const double beta = (pass == 0 && x_zero && k0 == 0) ? 0.0 : 1.0;
+      LQ_TRY(rotate(c, &Wv, pc, d, nrhs, t, pass == 0 ? 1.0 : -1.0, beta));
+    }
+  }
+  return LQCD_OK;
+}
+
+// the deflated start of the overlap CG: x0 = x_W of b, and r0 = b - D(m) x0
+// recomputed with the operator (so the CG's right-hand side is exact)
+lqcd_status deflation_guess(lqcd_ctx *c, int nrhs, const lqcd_field *b, lqcd_field *x0, lqcd_field *r0) {
+  LQ_TRY(copy_field(c, r0, b, nrhs));
+  LQ_TRY(deflate(c, nrhs, r0, x0, true, std::vector<char>(nrhs, 1)));
+  LQ_TRY(dov_apply(c, nrhs, x0, r0, 0));
+  return combine(c, nrhs, r0, b, r0, 1.0, -1.0, 0);
 }
 
 }  // namespace
@@ -1758,9 +2055,12 @@ extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, 
   if (!c || !out || !in) return set_error(LQCD_ERR_ARG, "NULL argument");
   if (!c->ov || !c->ov->ready) return set_error(LQCD_ERR_STATE, "overlap not set up (lqcd_overlap_setup)");
   if (nrhs < 1 || nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
-  if ((int)op < 0 || (int)op > 3) return set_error(LQCD_ERR_ARG, "bad overlap op");
-  if (op == LQCD_OV_SOLVE && (!cg || !(cg->tol > 0) || cg->max_iter < 1))
+  if ((int)op < 0 || (int)op > 4) return set_error(LQCD_ERR_ARG, "bad overlap op");
+  const bool solve = op == LQCD_OV_SOLVE || op == LQCD_OV_SOLVE_DEFLATED;
+  if (solve && (!cg || !(cg->tol > 0) || cg->max_iter < 1))
     return set_error(LQCD_ERR_ARG, "solve needs cg with tol > 0 and max_iter >= 1");
+  if (op == LQCD_OV_SOLVE_DEFLATED && !c->ov->ev)
+    return set_error(LQCD_ERR_STATE, "no overlap eigensystem to deflate with (lqcd_overlap_eigen)");
   LQ_TRY(ensure_state(c));
   const auto t0 = std::chrono::steady_clock::now();
   FieldGuard g;
@@ -1785,16 +2085,27 @@ extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, 
     for (int k = 0; k < nrhs; k++)
       if (!(bn2[k] > 0) || !std::isfinite(bn2[k]))
         return set_error(LQCD_ERR_ARG, "right-hand side %d is zero or not finite", k);
+    // deflated: the CG solves D e = r0 = b - D x0 from the eigensystem's
+    // exact low-mode part x0, to the same target |b - D x| <= tol |b|
+    lqcd_field *x0 = nullptr, *rhs = fin;
+    if (op == LQCD_OV_SOLVE_DEFLATED) {
+      LQ_TRY(new_full(c, nrhs, &x0));
+      g.f.push_back(x0);
+      LQ_TRY(new_full(c, nrhs, &rhs));
+      g.f.push_back(rhs);
+      LQ_TRY(deflation_guess(c, nrhs, fin, x0, rhs));
+    }
     if (cg->inner == LQCD_F64) {
-      LQ_TRY(ov_cgls_fp64(c, nrhs, fin, fout, cg, inf, bn2));
+      LQ_TRY(ov_cgls_fp64(c, nrhs, rhs, fout, cg, inf, bn2));
     } else {
       if (cg->inner != LQCD_F32) return set_error(LQCD_ERR_ARG, "overlap inner precision must be F64 or F32");
       if (c->ov->nlow > 0 && !c->ov->vecs32) {
         LQ_TRY(lqcd_field_create(c, LQCD_F32, LQCD_FULL, c->ov->nlow, &c->ov->vecs32));
         LQ_TRY(convert_full(c, c->ov->vecs32, c->ov->vecs, c->ov->nlow));
       }
-      LQ_TRY(ov_cgls_mixed(c, nrhs, fin, fout, cg, inf, bn2));
+      LQ_TRY(ov_cgls_mixed(c, nrhs, rhs, fout, cg, inf, bn2, op == LQCD_OV_SOLVE_DEFLATED));
     }
+    if (x0) LQ_TRY(axpy_full(c, fout, x0, std::vector<double>(nrhs, 1.0), nrhs));
     int it = inf->iters;
     lqcd_field *q;
     LQ_TRY(new_full(c, nrhs, &q));
@@ -1814,4 +2125,162 @@ extern "C" lqcd_status lqcd_overlap(lqcd_ctx *c, double *out, const double *in, 
   LQ_CU(cudaStreamSynchronize(c->stream));
   inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return result;
+}
+
+// The low eigenpairs of D_ov(0)^dag D_ov(0) in one chirality sector (Sec. 4's
+// overlap eigensystem).  On sector s, D_ov(0)^dag D_ov(0) = H_s = 2 rho^2 P_s
+// (1 + s eps) P_s: thick-restart Lanczos on H_s, one sign-function application
+// per Krylov vector; then, in batches, eps chi_i gives both the residual
+// ||H_s chi_i - mu_i chi_i|| = 2 rho^2 ||P_s eps chi_i - c_i chi_i|| (c_i =
+// <chi_i, eps chi_i>, mu_i = 2 rho^2 (1 + s c_i)) and the partner eta_i =
+// P_-s eps chi_i / |.| of the other sector with the same eigenvalue.
+extern "C" lqcd_status lqcd_overlap_eigen(lqcd_ctx *c, const lqcd_overlap_eigen_params *ep,
+                                          lqcd_overlap_eigen_info *info) {
+  using namespace lqcd;
+  NvtxRange nv("lqcd overlap eigensystem");
+  if (!c || !ep) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!c->ov || !c->ov->ready) return set_error(LQCD_ERR_STATE, "overlap not set up (lqcd_overlap_setup)");
+  if (ep->n_ev < 1 || ep->n_ev > LQCD_OV_MAX_EV) return set_error(LQCD_ERR_ARG, "n_ev must be in 1..%d", LQCD_OV_MAX_EV);
+  if (ep->sector != 1 && ep->sector != -1) return set_error(LQCD_ERR_ARG, "sector must be +1 or -1");
+  if (!(ep->tol > 0) || ep->max_restarts < 1) return set_error(LQCD_ERR_ARG, "need tol > 0 and max_restarts >= 1");
+  const int n_ev = ep->n_ev, s = ep->sector;
+  const long N = 6L * c->V;  // dimension of a chirality sector
+  // a basis of ~3 n_ev: thick restarts then converge in a few tens of cycles
+  // (16^3 x 32, 100 pairs: 40 cycles with 2 n_ev, 153 for 50 pairs)
+  int mmax = ep->basis > 0 ? ep->basis : std::min(std::max(3 * n_ev, n_ev + 48), kLzMaxP - 1);
+  if (mmax > kLzMaxP - 1 || mmax < n_ev + 16)
+    return set_error(LQCD_ERR_ARG, "Lanczos basis must be in n_ev + 16 .. %d", kLzMaxP - 1);
+  if (mmax >= N) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", mmax);
+  const int kkeep = std::min(mmax - 8, std::max(n_ev + 8, (n_ev + mmax) / 2));
+  const auto t0 = std::chrono::steady_clock::now();
+  lqcd_overlap_eigen_info local{};
+  lqcd_overlap_eigen_info *inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  OverlapState &S = *c->ov;
+  if (S.ev) {
+    lqcd_field_destroy(S.ev);
+    S.ev = nullptr;
+  }
+  S.ev_n = S.ev_np = 0;
+  S.ev_mu.clear();
+  const double rho = S.prm.rho, r2 = 2.0 * rho * rho;
+  FieldGuard g;
+  lqcd_field *X;
+  LQ_TRY(new_full(c, kkeep, &X));
+  g.f.push_back(X);
+  LanczosResult lr;
+  {
+    FieldGuard gl;  // the Lanczos basis is released before the vectors are post-processed
+    lqcd_field *x64, *e64;
+    LQ_TRY(new_full(c, 1, &x64));
+    gl.f.push_back(x64);
+    LQ_TRY(new_full(c, 1, &e64));
+    gl.f.push_back(e64);
+    LzSpec sp;
+    sp.per_call = 1;
+    sp.tol = 0.5 * ep->tol;
+    sp.max_cycles = ep->max_restarts;
+    sp.seed = ep->seed;
+    sp.start = [&](lqcd_field *x) { return chiral_project(c, x, 1, s); };
+    sp.apply = [&](lqcd_field *xd, lqcd_field *wd) -> lqcd_status {
+      LQ_TRY(convert_full(c, x64, xd, 1));
+      LQ_TRY(sign_apply(c, 1, x64, e64));
+      LQ_TRY(chiral_project(c, e64, 1, s));
+      LQ_TRY(combine(c, 1, e64, x64, e64, r2, r2 * s, 0));  // 2 rho^2 (x + s P_s eps x)
+      return convert_full(c, wd, e64, 1);
+    };
+    LQ_TRY(lanczos_lowest(c, sp, n_ev, kkeep, mmax, X, gl, lr, nullptr));
+  }
+  inf->restarts = lr.cycles;
+  inf->sign_applies = (double)lr.applies;
+  if (!lr.converged) {
+    inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return set_error(LQCD_ERR_NOCONV, "overlap eigensystem: Lanczos did not converge in %d restarts", lr.cycles);
+  }
+  // residuals, Rayleigh quotients and partners, 16 vectors at a time
+  lqcd_field *ev;
+  LQ_TRY(new_full(c, 2 * n_ev, &ev));
+  g.f.push_back(ev);
+  constexpr int kB = 16;
+  lqcd_field *E, *P;
+  LQ_TRY(new_full(c, kB, &E));
+  g.f.push_back(E);
+  LQ_TRY(new_full(c, kB, &P));
+  g.f.push_back(P);
+  std::vector<double> mu(n_ev), res(n_ev), pmu, cvec(n_ev), pnv(n_ev, 0.0);
+  std::vector<int> pidx, pcol(n_ev, -1);
+  double2 *d;
+  bool ok = true;
+  for (int k0 = 0; k0 < n_ev; k0 += kB) {
+    const int nb = std::min(kB, n_ev - k0);
+    const lqcd_field Xv = col_view(X, k0, nb);
+    LQ_TRY(sign_apply(c, nb, &Xv, E));
+    LQ_TRY(small_scratch(c, (size_t)nb * nb, &d));
+    LQ_TRY(gram(c, &Xv, nb, E, nb, d));
+    std::vector<zc> G;
+    LQ_TRY(to_host(c, d, (size_t)nb * nb, G));
+    std::vector<double> cc(nb), mc(nb), r2v, pn;
+    for (int i = 0; i < nb; i++) {
+      cc[i] = G[i + (size_t)nb * i].real();
+      mc[i] = -cc[i];
+      mu[k0 + i] = r2 * (1.0 + s * cc[i]);
+      cvec[k0 + i] = cc[i];
+    }
+    LQ_TRY(copy_field(c, P, E, nb));
+    LQ_TRY(chiral_project(c, P, nb, s));
+    LQ_TRY(axpy_norms(c, P, &Xv, mc, nb, r2v));  // |P_s eps chi - c chi|^2
+    for (int i = 0; i < nb; i++) {
+      res[k0 + i] = r2 * std::sqrt(std::max(r2v[i], 0.0));
+      ok &= res[k0 + i] <= ep->tol;
+    }
+    LQ_TRY(copy_col_range(c, ev, k0, X, k0, nb));
+    LQ_TRY(chiral_project(c, E, nb, -s));  // P_-s eps chi
+    LQ_TRY(field_norms(c, E, nb, pn));
+    for (int i = 0; i < nb; i++) {
+      if (!(pn[i] > 1e-10)) continue;  // a chiral zero mode, or mu = 4 rho^2: no partner
+      pidx.push_back(k0 + i);
+      pmu.push_back(mu[k0 + i]);
+      pcol[k0 + i] = n_ev + (int)pidx.size() - 1;
+      pnv[k0 + i] = std::sqrt(pn[i]);
+      // partners follow the n_ev sector vectors, in the order found
+      std::vector<double> f(1, 1.0 / std::sqrt(pn[i]));
+      const lqcd_field Ei = col_view(E, i, 1);
+      lqcd_field Ev = col_view(ev, n_ev + (int)pidx.size() - 1, 1);
+      LQ_TRY(scale_full(c, &Ev, &Ei, f, 1));
+    }
+  }
+  inf->sign_applies += n_ev;
+  inf->n_ev = n_ev;
+  inf->n_partners = (int)pidx.size();
+  for (int i = 0; i < n_ev; i++) {
+    inf->mu[i] = mu[i];
+    inf->resid[i] = res[i];
+    const double re = mu[i] / (2.0 * rho);
+    inf->lambda_re[i] = re;
+    inf->lambda_im[i] = std::sqrt(std::max(mu[i] - re * re, 0.0));
+  }
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (!ok) return set_error(LQCD_ERR_NOCONV, "overlap eigensystem: a residual is above tol");
+  S.ev = ev;
+  g.f.erase(std::find(g.f.begin(), g.f.end(), ev));
+  S.ev_n = n_ev;
+  S.ev_np = (int)pidx.size();
+  S.ev_sector = s;
+  S.ev_mu = mu;
+  S.ev_mu.insert(S.ev_mu.end(), pmu.begin(), pmu.end());
+  S.ev_c = cvec;
+  S.ev_pn = pnv;
+  S.ev_partner = pcol;
+  return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_overlap_eigvecs(lqcd_ctx *c, double *vecs, int partners, int on_device) {
+  using namespace lqcd;
+  if (!c || !vecs) return set_error(LQCD_ERR_ARG, "NULL argument");
+  if (!c->ov || !c->ov->ev) return set_error(LQCD_ERR_STATE, "no overlap eigensystem (lqcd_overlap_eigen)");
+  OverlapState &S = *c->ov;
+  const int k0 = partners ? S.ev_n : 0, n = partners ? S.ev_np : S.ev_n;
+  if (n == 0) return LQCD_OK;
+  const lqcd_field v = col_view(S.ev, k0, n);
+  return lqcd_field_export(c, &v, vecs, on_device);
 }

@@ -53,7 +53,9 @@ def test_struct_layouts_match_header(tmp_path):
     compiler's layout (sizes and the offset of every field)."""
     import paper_2001_05706_gb300 as L
     structs = {"lqcd_solve_params": L.lqcd_solve_params, "lqcd_solve_info": L.lqcd_solve_info,
-               "lqcd_overlap_params": L.lqcd_overlap_params, "lqcd_overlap_info": L.lqcd_overlap_info}
+               "lqcd_overlap_params": L.lqcd_overlap_params, "lqcd_overlap_info": L.lqcd_overlap_info,
+               "lqcd_overlap_eigen_params": L.lqcd_overlap_eigen_params,
+               "lqcd_overlap_eigen_info": L.lqcd_overlap_eigen_info}
     lines, expect = [], []
     for cname, py in structs.items():
         lines.append(f'printf("%zu\\n", sizeof({cname}));')
