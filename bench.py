@@ -711,6 +711,93 @@ def overlap_workload(L, torch, high, eig, want_oracle, stream):
     return out
 
 
+def overlap_eigen_workload(L, torch, dims, n_ev, want_oracle, stream, nrhs=2, basis=0):
+    """The overlap eigensystem (Sec. 4: 200 pairs on a 24^3x64 lattice; here a
+    synthetic stand-in, eps 0.1, rho 1.5, m 0.01): the n_ev lowest eigenpairs
+    of D_ov(0)^dag D_ov(0) in the + chirality sector (and their partners) by
+    thick-restart Lanczos, then the plain and the deflated mixed-precision
+    overlap CG on nrhs Gaussian sources.  The oracle recomputes three
+    eigenvectors' residuals (lowest, middle, highest) with its own sign
+    function on the returned low modes and interval, and every deflated
+    solve's true residual."""
+    import gen
+    U = gen.gauge_field(dims, 0.1, 1009)
+    b = gen.gaussian_spinor(dims, 2009, nrhs=nrhs)
+    name = "x".join(str(d) for d in dims)
+    out = {"config": {"workload": f"overlap eigensystem {name}, eps 0.1, rho 1.5, m 0.01, 20 H_W low modes, sign to "
+                                  f"1e-10 (double-float), {n_ev} eigenpairs of D_ov^dag D_ov in the + sector to "
+                                  f"1e-8, then {nrhs} Gaussian RHS by the mixed overlap CG to 1e-10 plain and "
+                                  f"deflated"}}
+    with L.Lattice(dims, stream=stream) as lat:
+        lat.load_gauge(U.view(np.float64))
+        prm = L.overlap_params(rho=1.5, mass=0.01, n_low=20, sign_tol=1e-10, eig_tol=1e-10, max_filter=400,
+                               high="df64", eig_method="lanczos")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, oinfo = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
+        out["setup_seconds"] = time.perf_counter() - t0
+        if st != 0:
+            out["status"] = L.lqcd_last_error()
+            return out
+        st, info = L.lqcd_overlap_eigen(lat.ctx, L.overlap_eigen_params(n_ev=n_ev, sector=1, tol=1e-8,
+                                                                        basis=basis, max_restarts=400),
+                                        raise_on_noconv=False)
+        mu = np.array(info.mu[:n_ev])
+        out["eigensystem"] = {"status": "ok" if st == 0 else L.lqcd_last_error(), "seconds": info.seconds,
+                              "restarts": info.restarts, "sign_applications": info.sign_applies,
+                              "pairs": n_ev, "partners": info.n_partners,
+                              "mu_min_max": [float(mu.min()), float(mu.max())],
+                              "lambda_min": [info.lambda_re[0], info.lambda_im[0]],
+                              "max_resid_gpu": max(info.resid[:n_ev])}
+        if st != 0:
+            return out
+        cg = L.solve_params(tol=1e-10, max_iter=8000, nrhs=nrhs, inner=L.LQCD_F32, delta=0.1)
+        xs = {}
+        for op, key in ((L.LQCD_OV_SOLVE, "solve_mixed"), (L.LQCD_OV_SOLVE_DEFLATED, "solve_mixed_deflated")):
+            x = np.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, si = L.lqcd_overlap(lat.ctx, x, b, nrhs, op, cg, raise_on_noconv=False)
+            out[key] = {"seconds": time.perf_counter() - t0, "iters": si.iters,
+                        "reliable_updates": si.reliable_updates, "status": "ok" if st == 0 else L.lqcd_last_error(),
+                        "max_true_resid_gpu_fp64": max(si.true_resid[:nrhs])}
+            xs[key] = x
+        out["deflation_speedup"] = out["solve_mixed"]["seconds"] / out["solve_mixed_deflated"]["seconds"]
+        if want_oracle:
+            import oracle
+            vecs = np.zeros((20,) + oracle.spinor_shape(dims), dtype=np.complex128)
+            L.lqcd_overlap_lowmodes(lat.ctx, vecs)
+            lam = np.array(oinfo.lambda_[:20])
+            n, c = oracle.cheb_degree(oinfo.a, oinfo.b, 1e-10)
+            chi = np.zeros((n_ev,) + oracle.spinor_shape(dims), dtype=np.complex128)
+            L.lqcd_overlap_eigvecs(lat.ctx, chi)
+            res = {}
+            for i in sorted({0, n_ev // 2, n_ev - 1}):
+                h = oracle.apply_sector_normal(dims, U, 1.5, 1, chi[i], oinfo.a, oinfo.b, c, lam=lam, vecs=vecs)
+                res[i] = float(np.linalg.norm((h - mu[i] * chi[i]).ravel()))
+            out["oracle_eig_resid_sampled"] = res
+            rr = []
+            for k in range(nrhs):
+                x = xs["solve_mixed_deflated"][k]
+                r = b[k] - oracle.apply_overlap(dims, U, 1.5, 0.01, x, oinfo.a, oinfo.b, c, lam=lam, vecs=vecs)
+                rr.append(float(np.linalg.norm(r) / np.linalg.norm(b[k])))
+            out["oracle_true_resid_deflated"] = rr
+    return out
+
+
+def run_ov_eigen(args):
+    """The overlap eigensystem on its own (--ov-eigen L0,L1,L2,L3 --n-ev N)."""
+    import torch
+    import paper_2001_05706_gb300 as L
+    torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.ov_eigen.split(","))
+    out = {"metric": "overlap eigensystem and deflated overlap solve time"}
+    out.update(overlap_eigen_workload(L, torch, dims, args.n_ev, not args.no_cpu_baseline,
+                                      torch.cuda.current_stream(), basis=args.ev_basis))
+    print(json.dumps(out))
+    return 0
+
+
 def run_overlap(args):
     """Config 5 on its own (--overlap), either low-mode method and precision."""
     import torch
@@ -835,6 +922,8 @@ def run_gpu(args, rank, world, local_rank):
     overlap = None
     if not args.no_overlap and world == 1:
         overlap = overlap_workload(L, torch, "df64", "lanczos", need_oracle, stream)
+        overlap["eigensystem_12x12x12x24"] = overlap_eigen_workload(L, torch, (12, 12, 12, 24), 50, need_oracle,
+                                                                    stream)
     cpu = None
     if need_oracle:
         rate, nsl, dt = oracle_slab_rate(U, oracle_AAi[0], oracle_AAi[1], psi)
@@ -889,6 +978,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-config3", action="store_true", help="skip the 48^3x96 solve comparison")
     ap.add_argument("--no-overlap", action="store_true", help="skip the overlap workload in the default run")
+    ap.add_argument("--ov-eigen", default=None, help="run only the overlap eigensystem on lattice L0,L1,L2,L3")
+    ap.add_argument("--n-ev", type=int, default=200, help="eigenpairs for --ov-eigen")
+    ap.add_argument("--ev-basis", type=int, default=0, help="Lanczos basis for --ov-eigen (0: automatic)")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
@@ -916,6 +1008,8 @@ def main():
         return solver_iteration(args) if rank == 0 else 0
     if args.overlap:
         return run_overlap(args) if rank == 0 else 0
+    if args.ov_eigen:
+        return run_ov_eigen(args) if rank == 0 else 0
     if args.solve_lattice:
         return run_solve_only(args) if rank == 0 else 0
     return run_gpu(args, rank, world, local_rank)
