@@ -356,7 +356,7 @@ def solver_iteration(args):
 
 
 SOLVE_SET = ("fp64", "mixed_f32", "mixed_f16", "mixed_bf16", "df64", "mixed_f16_df64", "bicgstab_fp64",
-             "bicgstab_mixed_f16", "bicgstab_mixed_f16_df64")
+             "bicgstab_mixed_f16", "bicgstab_mixed_f16_df64", "gcr_mixed_f16", "mixed_f16_r8")
 
 
 def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi, dims=None, which=SOLVE_SET, src_seed=2003):
@@ -367,18 +367,20 @@ def run_solves(L, torch, lat, U, rank, want_oracle, oracle_AAi, dims=None, which
     bt = torch.from_numpy(b.view(np.float64).copy()).cuda()
     res = {"lattice": list(dims), "kappa": KAPPA, "c_sw": CSW, "tol": 1e-10, "source": f"Gaussian, seed {src_seed}"}
     xs = {}
-    cg, bi = L.LQCD_SOLVER_CGLS, L.LQCD_SOLVER_BICGSTAB
+    cg, bi, gc = L.LQCD_SOLVER_CGLS, L.LQCD_SOLVER_BICGSTAB, L.LQCD_SOLVER_GCR
     for name, inner, outer, solver in (
             ("fp64", L.LQCD_F64, L.LQCD_F64, cg), ("mixed_f32", L.LQCD_F32, L.LQCD_F64, cg),
             ("mixed_f16", L.LQCD_F16, L.LQCD_F64, cg), ("mixed_bf16", L.LQCD_BF16, L.LQCD_F64, cg),
             ("df64", L.LQCD_DF64, L.LQCD_DF64, cg), ("mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, cg),
             ("bicgstab_fp64", L.LQCD_F64, L.LQCD_F64, bi), ("bicgstab_mixed_f16", L.LQCD_F16, L.LQCD_F64, bi),
-            ("bicgstab_mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, bi)):
+            ("bicgstab_mixed_f16_df64", L.LQCD_F16, L.LQCD_DF64, bi), ("gcr_mixed_f16", L.LQCD_F16, L.LQCD_F64, gc),
+            ("mixed_f16_r8", L.LQCD_F16, L.LQCD_F64, cg)):
         if name not in which:
             continue
         xt = torch.zeros_like(bt)
         prm = L.solve_params(tol=1e-10, max_iter=40000 if solver == cg else 4000, inner=inner, delta=0.1, recon=18,
-                             inner_recon=12, check_every=0, outer=outer, solver=solver)
+                             inner_recon=8 if name.endswith("_r8") else 12, check_every=0, outer=outer,
+                             solver=solver, gcr_nkrylov=8)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, info = L.lqcd_solve(lat.ctx, xt, bt, prm, raise_on_noconv=False)

@@ -75,8 +75,15 @@ typedef enum {
 typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3, LQCD_DF64 = 4 } lqcd_prec;
 
 /* Link storage: all 18 reals, or rows 0 and 1 only (12 reals) with row 2
- * rebuilt as conj(row0 x row1) in registers (Table 2's caption). */
-typedef enum { LQCD_RECON_18 = 18, LQCD_RECON_12 = 12 } lqcd_recon;
+ * rebuilt as conj(row0 x row1) in registers (Table 2's caption), or 8 reals
+ * (FP32/FP16 operators, one right-hand side per thread; BF16 would keep the
+ * two angles only to ~6e-3 rad and is refused): arg U00,
+ * arg U20, U01, U02, U10, the rest rebuilt from unitarity and det U = 1
+ * (|U00| and |U20| from the unit row 0 and column 0, U11 and U12 from a 2x2
+ * linear system of determinant 1 - |U00|^2, row 2 as the cross product).
+ * LQCD_ERR_ARG for the 8-real form on a field with a link of |U00| = 1 (unit
+ * links, the free field), where that determinant vanishes. */
+typedef enum { LQCD_RECON_18 = 18, LQCD_RECON_12 = 12, LQCD_RECON_8 = 8 } lqcd_recon;
 
 /* Which sites a device-resident field holds. */
 typedef enum { LQCD_EVEN = 0, LQCD_ODD = 1, LQCD_FULL = 2 } lqcd_subset;
@@ -197,7 +204,7 @@ lqcd_status lqcd_field_norm2(lqcd_ctx *ctx, const lqcd_field *field, double *res
  * with the same plain / mixed-precision-with-reliable-updates structure (no
  * counterpart in the paper's text; QUDA's inverter family, which the paper
  * ports, includes it).  lqcd_solve_batch runs CGLS only. */
-typedef enum { LQCD_SOLVER_CGLS = 0, LQCD_SOLVER_BICGSTAB = 1 } lqcd_solver;
+typedef enum { LQCD_SOLVER_CGLS = 0, LQCD_SOLVER_BICGSTAB = 1, LQCD_SOLVER_GCR = 2 } lqcd_solver;
 
 /* Even-odd reduced operator the recursion works on.  Both solve the same
  * system M x = b (same x_o):
@@ -228,9 +235,14 @@ typedef struct {
                        /* the accumulated solution, LQCD_F64 (0, the default) or  */
                        /* LQCD_DF64; the final residual check is FP64 either way  */
   int solver;          /* lqcd_solver: LQCD_SOLVER_CGLS (0, the default: CG on    */
-                       /* the normal equations) or LQCD_SOLVER_BICGSTAB           */
+                       /* the normal equations), LQCD_SOLVER_BICGSTAB or          */
+                       /* LQCD_SOLVER_GCR (restarted GCR(m) on the Schur         */
+                       /* operator; mixed: each cycle in the inner precision on   */
+                       /* the normalised residual, a reliable update after it,    */
+                       /* a cycle ending after m steps or a delta drop)           */
   int schur;           /* lqcd_schur: LQCD_SCHUR_ASYM (0, the default) or         */
                        /* LQCD_SCHUR_SYM; any solver, plain, mixed and batched    */
+  int gcr_nkrylov;     /* GCR: steps per cycle m, 1..64 (0: 8); 2m fields kept     */
 } lqcd_solve_params;
 
 typedef struct {

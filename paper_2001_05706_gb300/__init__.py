@@ -32,7 +32,7 @@ LQCD_OK = 0
 LQCD_ERR_ARG, LQCD_ERR_CUDA, LQCD_ERR_OOM, LQCD_ERR_NOCONV = -1, -2, -3, -4
 LQCD_ERR_TIMEOUT, LQCD_ERR_STATE, LQCD_ERR_NOT_SU3, LQCD_ERR_SINGULAR = -5, -6, -7, -8
 LQCD_F64, LQCD_F32, LQCD_F16, LQCD_BF16, LQCD_DF64 = 0, 1, 2, 3, 4
-LQCD_RECON_18, LQCD_RECON_12 = 18, 12
+LQCD_RECON_18, LQCD_RECON_12, LQCD_RECON_8 = 18, 12, 8
 LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
 (LQCD_OP_M, LQCD_OP_MHAT, LQCD_OP_MHAT_DAG, LQCD_OP_MHAT_NORMAL, LQCD_OP_HOP_EO, LQCD_OP_HOP_OE, LQCD_OP_HW,
  LQCD_OP_K2A, LQCD_OP_M_DAG, LQCD_OP_MHAT_SYM, LQCD_OP_MHAT_SYM_DAG) = range(11)
@@ -47,7 +47,8 @@ class lqcd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("use_x0", ctypes.c_int),
                 ("recon", ctypes.c_int), ("inner_recon", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("outer", ctypes.c_int), ("solver", ctypes.c_int), ("schur", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("solver", ctypes.c_int), ("schur", ctypes.c_int),
+                ("gcr_nkrylov", ctypes.c_int)]
 
 
 class lqcd_overlap_params(ctypes.Structure):
@@ -393,21 +394,21 @@ def lqcd_overlap(ctx, out, inp, nrhs, op, cg=None, raise_on_noconv=True):
     return st, info
 
 
-LQCD_SOLVER_CGLS, LQCD_SOLVER_BICGSTAB = 0, 1
-SOLVERS = {"cgls": LQCD_SOLVER_CGLS, "bicgstab": LQCD_SOLVER_BICGSTAB}
+LQCD_SOLVER_CGLS, LQCD_SOLVER_BICGSTAB, LQCD_SOLVER_GCR = 0, 1, 2
+SOLVERS = {"cgls": LQCD_SOLVER_CGLS, "bicgstab": LQCD_SOLVER_BICGSTAB, "gcr": LQCD_SOLVER_GCR}
 LQCD_SCHUR_ASYM, LQCD_SCHUR_SYM = 0, 1
 SCHUR = {"asym": LQCD_SCHUR_ASYM, "sym": LQCD_SCHUR_SYM}
 
 
 def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, use_x0=0, recon=LQCD_RECON_18,
                  inner_recon=LQCD_RECON_12, check_every=8, outer=LQCD_F64, solver=LQCD_SOLVER_CGLS,
-                 schur=LQCD_SCHUR_ASYM):
+                 schur=LQCD_SCHUR_ASYM, gcr_nkrylov=0):
     if isinstance(solver, str):
         solver = SOLVERS[solver]
     if isinstance(schur, str):
         schur = SCHUR[schur]
     return lqcd_solve_params(tol, max_iter, inner, delta, nrhs, use_x0, recon, inner_recon, check_every, outer,
-                             solver, schur)
+                             solver, schur, gcr_nkrylov)
 
 
 # ---- convenience ------------------------------------------------------------

@@ -201,6 +201,44 @@ cudaError_t bi_s(lqcd_prec pv, long Vh, int nrhs, MutField sv, FieldRef r, Field
   return cudaGetLastError();
 }
 
+// GCR: y_k += c_k x_k with a complex coefficient per right-hand side (c_k =
+// 0: right-hand side k untouched); y may be a wider type than x
+template <typename SY, typename SX>
+__global__ void __launch_bounds__(kBiThreads) gcr_caxpy_kernel(long Vh, MutField y, FieldRef x, const double2 *cf) {
+  using T = typename Math<SY>::T;
+  using TX = typename Math<SX>::T;
+  const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (h >= Vh || (cf[k].x == 0.0 && cf[k].y == 0.0)) return;
+  const cx<T> a = zc<T>(cf[k]);
+  cx<T> yv[4][3];
+  cx<TX> xv[4][3];
+  const FieldRef yr{y.data, y.scale, y.rhs_words};
+  load_spinor<SY>(yr, Vh, k, h, yv);
+  load_spinor<SX>(x, Vh, k, h, xv);
+#pragma unroll
+  for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) yv[sp][c] = cmadd(a, mk<T>((T)xv[sp][c].r, (T)xv[sp][c].i), yv[sp][c]);
+  store_spinor<SY>(y.data, y.scale, y.rhs_words, Vh, k, h, yv);
+}
+
+cudaError_t gcr_caxpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double2 *cf,
+                      cudaStream_t st) {
+  const dim3 g = bgrid(Vh, nrhs);
+  if (py == px) {
+    LQ_BI_DISPATCH(py, (gcr_caxpy_kernel<SV, SV><<<g, kBiThreads, 0, st>>>(Vh, y, x, cf)));
+  } else if (py == LQCD_F32 && (px == LQCD_F16 || px == LQCD_BF16)) {
+    if (px == LQCD_F16)
+      gcr_caxpy_kernel<float, __half><<<g, kBiThreads, 0, st>>>(Vh, y, x, cf);
+    else
+      gcr_caxpy_kernel<float, __nv_bfloat16><<<g, kBiThreads, 0, st>>>(Vh, y, x, cf);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, double *red,
                     cudaStream_t st) {
   const dim3 g = bgrid(Vh, nrhs);

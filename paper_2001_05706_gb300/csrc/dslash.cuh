@@ -251,6 +251,46 @@ template <> __device__ __forceinline__ void store_spinor<df>(void *base, float *
   store_reals<df, 24>(b, Vh, i, raw);
 }
 
+// The 8-real form (FP32/FP16 storage): v = (arg U00, arg U20, U01, U02,
+// U10) as (re, im) pairs.  |U00|^2 = 1 - |U01|^2 - |U02|^2 (row 0 is a unit
+// vector), |U20|^2 = 1 - |U00|^2 - |U10|^2 (so is column 0); U11 and U12 solve
+// the two linear conditions row 1 . conj(row 0) = 0 and conj(U20) = U01 U12 -
+// U02 U11 (row 2 = conj(row 0 x row 1) for det U = 1), whose determinant is
+// |U01|^2 + |U02|^2 = 1 - |U00|^2; row 2 is then that cross product.  The
+// library refuses the form for fields with a link where this determinant
+// nearly vanishes (U00 of modulus one, e.g. unit links).
+// sin and cos of a stored angle (|x| <= pi): the FP32 intrinsic, whose
+// absolute error there is below the angle's own FP32 rounding
+__device__ __forceinline__ void sincos_angle(float x, float *s, float *c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_angle(double x, double *s, double *c) { sincos(x, s, c); }
+
+template <typename T> __device__ __forceinline__ void rebuild_link8(const T (&v)[8], cx<T> (&U)[3][3]) {
+  const cx<T> u01 = mk<T>(v[2], v[3]), u02 = mk<T>(v[4], v[5]), u10 = mk<T>(v[6], v[7]);
+  const T d = u01.r * u01.r + u01.i * u01.i + u02.r * u02.r + u02.i * u02.i;  // 1 - |U00|^2
+  const T a00 = sqrt(fmax((T)1 - d, (T)0));
+  T s0, c0, s2, c2;
+  sincos_angle(v[0], &s0, &c0);
+  sincos_angle(v[1], &s2, &c2);
+  const cx<T> u00 = mk<T>(a00 * c0, a00 * s0);
+  const T a20 = sqrt(fmax(d - (u10.r * u10.r + u10.i * u10.i), (T)0));
+  const cx<T> u20 = mk<T>(a20 * c2, a20 * s2);
+  const T id = (T)1 / d;
+  const cx<T> e = (T)-1 * (u10 * conjg(u00));  // right-hand side of the orthogonality condition
+  const cx<T> f = conjg(u20);
+  // [[conj u01, conj u02], [-u02, u01]] (u11, u12) = (e, f)
+  const cx<T> u11 = id * (e * u01 - conjg(u02) * f);
+  const cx<T> u12 = id * (conjg(u01) * f + u02 * e);
+  U[0][0] = u00;
+  U[0][1] = u01;
+  U[0][2] = u02;
+  U[1][0] = u10;
+  U[1][1] = u11;
+  U[1][2] = u12;
+  U[2][0] = u20;
+  U[2][1] = conjg(u02 * u10 - u00 * u12);
+  U[2][2] = conjg(u00 * u11 - u01 * u10);
+}
+
 // Link U_mu at site i of one parity; 12-real form rebuilds row 2 = conj(row0 x row1).
 #ifndef LQCD_LINK_STREAM
 #define LQCD_LINK_STREAM true
@@ -260,6 +300,13 @@ __device__ __forceinline__ void load_link(const void *base, long Vh, long i, cx<
   using T = typename Math<S>::T;
   S raw[R];
   load_reals<S, R, LQCD_LINK_STREAM>(base, Vh, i, raw);
+  if constexpr (R == 8) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = (T)to_f(raw[k]);
+    rebuild_link8<T>(v, U);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < R / 6; k++)
 #pragma unroll
@@ -655,17 +702,33 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
       dep |= __float_as_uint(f);
     }
     cx<T> U[3][3];
+    if constexpr (R == 8) {
+      T v8[8];
 #pragma unroll
-    for (int r = 0; r < R / 6; r++)
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
+      for (int k = 0; k < 4; k++) {
         if constexpr (IsHalf<S>::value) {
-          const float2 e = unpack_pair<S>(lw[3 * r + c]);
-          U[r][c] = mk<T>(e.x, e.y);
+          const float2 e = unpack_pair<S>(lw[k]);
+          v8[2 * k] = e.x;
+          v8[2 * k + 1] = e.y;
         } else {
-          U[r][c] = mk<T>((T)to_f(lraw[6 * r + 2 * c]), (T)to_f(lraw[6 * r + 2 * c + 1]));
+          v8[2 * k] = (T)to_f(lraw[2 * k]);
+          v8[2 * k + 1] = (T)to_f(lraw[2 * k + 1]);
         }
       }
+      rebuild_link8<T>(v8, U);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R / 6; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          if constexpr (IsHalf<S>::value) {
+            const float2 e = unpack_pair<S>(lw[3 * r + c]);
+            U[r][c] = mk<T>(e.x, e.y);
+          } else {
+            U[r][c] = mk<T>((T)to_f(lraw[6 * r + 2 * c]), (T)to_f(lraw[6 * r + 2 * c + 1]));
+          }
+        }
+    }
     if (R == 12) {
 #pragma unroll
       for (int j = 0; j < 3; j++) {

@@ -21,7 +21,8 @@ static cudaError_t launch_one(const DslashParams &P, cudaStream_t st) {
 template <typename S, int R, int MODE>
 static cudaError_t launch_nr(const DslashParams &P, int nr, cudaStream_t st) {
   if (nr == 1) return launch_one<S, R, MODE, 1>(P, st);
-  if constexpr (MODE != MODE_FOLDED_AINV) {
+  if constexpr (R == 8) return cudaErrorInvalidValue;  // the 8-real form: one right-hand side per thread
+  if constexpr (R != 8 && MODE != MODE_FOLDED_AINV) {
     if (nr == 2) return launch_one<S, R, MODE, 2>(P, st);
     // double-float accumulators for four right-hand sides exceed the register file
     if constexpr (!std::is_same<S, df>::value)
@@ -47,9 +48,12 @@ static cudaError_t launch_mode(const DslashParams &P, int mode, int nr, cudaStre
   return cudaErrorInvalidValue;
 }
 
-template <typename S, bool WITH18, bool WITH12 = true>
+template <typename S, bool WITH18, bool WITH12 = true, bool WITH8 = false>
 static cudaError_t launch_dslash_impl(const DslashParams &P, int recon, int mode, int nr, cudaStream_t st) {
   if (P.nrhs % nr != 0) return cudaErrorInvalidValue;
+  if constexpr (WITH8) {
+    if (recon == 8) return launch_mode<S, 8>(P, mode, nr, st);
+  }
   if constexpr (WITH12) {
     if (recon == 12) return launch_mode<S, 12>(P, mode, nr, st);
   }

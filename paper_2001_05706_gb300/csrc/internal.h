@@ -39,6 +39,8 @@ cudaError_t convert_spinor(lqcd_prec pi, lqcd_prec po, long Vh, int nrhs, const 
                            void *out, float *os, long orw, double factor, cudaStream_t st);
 size_t link_bytes(lqcd_prec prec, int recon, long Vh);
 cudaError_t pack_links(lqcd_prec prec, const Geom &g, const double *U, int recon, void *out, cudaStream_t st);
+// min over the canonical links of 1 - |U00|^2 (the 8-real form's determinant)
+cudaError_t recon8_min_det(const double *U, long nlinks, unsigned long long *dev_word, double *out, cudaStream_t st);
 const void *link_ptr(const void *base, lqcd_prec prec, int recon, long Vh, int mu, int p);
 cudaError_t su3_check(const double *U, long nlinks, unsigned long long *worst, cudaStream_t st);
 size_t clover_bytes(lqcd_prec prec, long Vh);
@@ -83,6 +85,10 @@ cudaError_t bi_s(lqcd_prec pv, long Vh, int nrhs, MutField sv, FieldRef r, Field
 // red[3k..3k+2] = (a_k^H b_k) re, im, |a_k|^2  (red may be any of the slots)
 cudaError_t bi_dot3(lqcd_prec pv, long Vh, int nrhs, FieldRef a, FieldRef b, double *partials, double *red,
                     cudaStream_t st);
+// GCR: y_k += cf_k x_k, cf a complex coefficient per RHS on the device (0: skip);
+// py == px, or FP32 y with FP16/BF16 x
+cudaError_t gcr_caxpy(lqcd_prec py, lqcd_prec px, long Vh, int nrhs, MutField y, FieldRef x, const double2 *cf,
+                      cudaStream_t st);
 // x += alpha p + omega s; r = s - omega t; red = (rhat, r), |r|^2
 cudaError_t bi_xr(lqcd_prec px, lqcd_prec pv, long Vh, int nrhs, MutField x, FieldRef p, FieldRef sv, FieldRef t,
                   MutField r, FieldRef rhat, const BiScalars *s, double *partials, double *red, cudaStream_t st);

@@ -1,3 +1,5 @@
+#include <cstring>
+#include <algorithm>
 // Field layout conversions: canonical FP64 arrays <-> site-blocked
 // word-major fields of one parity in FP64/FP32/FP16/BF16, link packing into
 // the 18- and 12-real forms, clover packing, precision conversion, and the
@@ -172,8 +174,14 @@ __global__ void pack_links_kernel(Geom g, const double *__restrict__ U, void *ou
   const long s = lex_of(g, h, p);
   const double *u = U + (s * 4 + mu) * 18;
   S raw[R];
+  if constexpr (R == 8) {  // (arg U00, arg U20, U01, U02, U10)
+    const double p8[8] = {atan2(u[1], u[0]), atan2(u[13], u[12]), u[2], u[3], u[4], u[5], u[6], u[7]};
 #pragma unroll
-  for (int k = 0; k < R; k++) raw[k] = from_d<S>(u[k]);
+    for (int k = 0; k < 8; k++) raw[k] = from_d<S>(p8[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; k++) raw[k] = from_d<S>(u[k]);
+  }
   using Wd = Words<S, R>;
   char *base = reinterpret_cast<char *>(out) + (long)(mu * 2 + p) * Wd::NW * g.Vh * Wd::W;
   store_reals<S, R>(base, g.Vh, h, raw);
@@ -188,9 +196,35 @@ static cudaError_t pack_links_t(const Geom &g, const double *U, int recon, void 
   dim3 gr = grid2(g.Vh, 8, 128);
   if (recon == 12)
     pack_links_kernel<S, 12><<<gr, 128, 0, st>>>(g, U, out);
+  else if (recon == 8)
+    pack_links_kernel<S, 8><<<gr, 128, 0, st>>>(g, U, out);
   else
     pack_links_kernel<S, 18><<<gr, 128, 0, st>>>(g, U, out);
   return cudaGetLastError();
+}
+
+// min over links of |U01|^2 + |U02|^2 = 1 - |U00|^2, the determinant the
+// 8-real rebuild divides by, as a min of IEEE bit patterns of non-negative
+// doubles (order-independent); *out starts at all ones
+__global__ void recon8_det_kernel(const double *__restrict__ U, long nlinks, unsigned long long *out) {
+  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (long)gridDim.x * blockDim.x) {
+    const double *u = U + l * 18;
+    const double d = u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5];
+    atomicMin(out, (unsigned long long)__double_as_longlong(d));
+  }
+}
+
+cudaError_t recon8_min_det(const double *U, long nlinks, unsigned long long *dev_word, double *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(dev_word, 0xff, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  recon8_det_kernel<<<(unsigned)std::min<long>((nlinks + 255) / 256, 4096), 256, 0, st>>>(U, nlinks, dev_word);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  unsigned long long w = 0;
+  e = cudaMemcpyAsync(&w, dev_word, sizeof(w), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  std::memcpy(out, &w, sizeof(w));  // the bit pattern of a non-negative double
+  return e;
 }
 
 cudaError_t pack_links(lqcd_prec prec, const Geom &g, const double *U, int recon, void *out, cudaStream_t st) {

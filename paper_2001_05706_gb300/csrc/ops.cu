@@ -14,13 +14,29 @@ namespace lqcd {
 
 lqcd_status get_links(lqcd_ctx *c, lqcd_prec prec, int recon, const void **base) {
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
-  if (recon != 12 && recon != 18) return set_error(LQCD_ERR_ARG, "recon must be 12 or 18");
-  if (prec_half(prec) && recon != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 links are stored in 12-real form only");
+  if (recon != 12 && recon != 18 && recon != 8) return set_error(LQCD_ERR_ARG, "recon must be 8, 12 or 18");
+  if (prec_half(prec) && recon == 18) return set_error(LQCD_ERR_ARG, "FP16/BF16 links are stored in 12- or 8-real form");
+  // BF16's 8-bit mantissa would store the two angles only to ~6e-3 rad
+  if (recon == 8 && prec != LQCD_F32 && prec != LQCD_F16)
+    return set_error(LQCD_ERR_ARG, "the 8-real form is for FP32/FP16 links");
   const int key = 100 * (int)prec + recon;
   auto it = c->links.find(key);
   if (it != c->links.end()) {
     *base = it->second;
     return LQCD_OK;
+  }
+  if (recon == 8) {  // the rebuild divides by 1 - |U00|^2: refuse links where it vanishes (unit links)
+    unsigned long long *w = nullptr;
+    if (dev_malloc((void **)&w, sizeof(*w)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(LQCD_ERR_OOM, "cannot allocate a reduction word");
+    }
+    double dmin = 0;
+    const cudaError_t e = recon8_min_det(c->U64, 4L * c->V, w, &dmin, c->stream);
+    cudaFree(w);
+    LQ_CU(e);
+    if (!(dmin > 1e-10))
+      return set_error(LQCD_ERR_ARG, "8-real links need |U00| < 1 on every link (min 1 - |U00|^2 = %.3e)", dmin);
   }
   void *p = nullptr;
   if (dev_malloc(&p, link_bytes(prec, recon, c->Vh)) != cudaSuccess) {
@@ -129,8 +145,9 @@ static bool mrhs_ok(lqcd_prec prec, int mode, int nrhs) {
 }
 
 // every variant that can run this launch
-static std::vector<int> variants(lqcd_prec prec, int mode, int nrhs) {
+static std::vector<int> variants(lqcd_prec prec, int mode, int nrhs, int recon) {
   std::vector<int> v;
+  if (recon == 8) return {1};  // the 8-real form: dslash_kernel with one right-hand side per thread
   for (int nr : {1, 2, 4}) {
     if (nrhs % nr != 0) continue;
     if (nr > 1 && mode == MODE_FOLDED_AINV) continue;
@@ -159,7 +176,7 @@ static int default_variant(lqcd_prec prec, int mode, int nrhs) {
 }
 
 static int pick_variant(lqcd_ctx *c, const DslashParams &P, lqcd_prec prec, int recon, int mode, int nrhs) {
-  const std::vector<int> cand = variants(prec, mode, nrhs);
+  const std::vector<int> cand = variants(prec, mode, nrhs, recon);
   if (const char *f = std::getenv("LQCD_FORCE_VARIANT")) {
     const int v = std::atoi(f);
     for (int x : cand)
@@ -218,7 +235,7 @@ lqcd_status run_dslash(lqcd_ctx *c, lqcd_prec prec, int recon, int mode, int out
                        int g5_total, double *norm_result, int norm_stride, const FieldRef *zc, const double *cz,
                        long h0, long h1) {
   if (prec == LQCD_DF64 && recon != 18) return set_error(LQCD_ERR_ARG, "DF64 operators use 18-real links");
-  if (prec_half(prec) && recon != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 operators use 12-real links");
+  if (prec_half(prec) && recon == 18) return set_error(LQCD_ERR_ARG, "FP16/BF16 operators use 12- or 8-real links");
   DslashParams P{};
   P.g = c->geom;
   P.h0 = h0;

@@ -777,6 +777,201 @@ lqcd_status bicgstab(Work &W, bool mixed) {
   return nact == 0 ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "BiCGStab did not converge in %d iterations", W.max_iter);
 }
 
+// Restarted GCR(m) on the recursion's operator (Mhat, or A_oo^-1 Mhat).  Per
+// step: z = r, q = A z, q and z orthogonalised against the cycle's earlier
+// q_i (one classical Gram-Schmidt pass, the same coefficients on z), both
+// scaled to |q| = 1; then alpha = (q, r), x += alpha z, r -= alpha q, so |r|
+// falls monotonically (GCR minimises it over the cycle's Krylov space).
+// Plain: every step in precision hp, the cycle restarted from the true
+// residual after m steps.  Mixed: a cycle runs in the inner precision on the
+// residual normalised to 1 and ends after m steps, when every active |r|
+// dropped below delta, or when a right-hand side reached its target; the
+// FP64 (DF64) solution absorbs it and the true residual starts the next one.
+lqcd_status gcr(Work &W, bool mixed, int m) {
+  NvtxRange nv(mixed ? "lqcd GCR (mixed)" : "lqcd GCR (plain)");
+  lqcd_ctx *c = W.c;
+  const int n = W.nrhs;
+  const lqcd_prec L = mixed ? W.lo : W.hp;
+  const int rec = mixed ? W.recon_lo : W.recon64;
+  const lqcd_prec px = mixed ? LQCD_F32 : W.hp;  // the cycle's solution accumulates in FP32 when mixed
+  std::vector<lqcd_field *> z(m), q(m);
+  lqcd_field *r, *ye, *ye64, *xlo = nullptr;
+  for (int j = 0; j < m; j++) {
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 100 + j, &z[j]));
+    LQ_TRY(temp_field(c, L, LQCD_ODD, n, 200 + j, &q[j]));
+  }
+  LQ_TRY(temp_field(c, L, LQCD_ODD, n, 60, &r));
+  LQ_TRY(temp_field(c, L, LQCD_EVEN, n, 61, &ye));
+  LQ_TRY(temp_field(c, W.hp, LQCD_EVEN, n, 62, &ye64));
+  if (mixed) LQ_TRY(temp_field(c, LQCD_F32, LQCD_ODD, n, 63, &xlo));
+  LQ_TRY(ensure_partials(c, 3 * n * m));
+  struct Bufs {
+    double *red = nullptr, *hred = nullptr, *fac = nullptr, *hfac = nullptr;
+    double2 *cf = nullptr, *hcf = nullptr;
+    ~Bufs() {
+      if (red) cudaFree(red);
+      if (fac) cudaFree(fac);
+      if (cf) cudaFree(cf);
+      if (hred) cudaFreeHost(hred);
+      if (hfac) cudaFreeHost(hfac);
+      if (hcf) cudaFreeHost(hcf);
+    }
+  } b;
+  const size_t nred = 3 * (size_t)n * (m + 2);
+  if (dev_malloc((void **)&b.red, sizeof(double) * nred) != cudaSuccess ||
+      dev_malloc((void **)&b.fac, sizeof(double) * n) != cudaSuccess ||
+      dev_malloc((void **)&b.cf, sizeof(double2) * n * (size_t)(m + 1)) != cudaSuccess ||
+      cudaMallocHost(&b.hred, sizeof(double) * nred) != cudaSuccess ||
+      cudaMallocHost(&b.hfac, sizeof(double) * n) != cudaSuccess ||
+      cudaMallocHost(&b.hcf, sizeof(double2) * n * (size_t)(m + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ERR_OOM, "cannot allocate GCR state");
+  }
+  const size_t vbytes = (size_t)r->rhs_words() * 16 * n;
+  const size_t sbytes = r->scale[1] ? sizeof(float) * c->Vh * n : 0;
+  std::vector<double> target(n), sigma(n, 1.0), nrm(n), rr(n);
+  std::vector<char> active(n, 1);
+  for (int k = 0; k < n; k++) target[k] = 0.5 * W.tol * W.bnorm[k] / W.rscale;
+  auto sync_red = [&]() -> lqcd_status {
+    LQ_CU(cudaMemcpyAsync(b.hred, b.red, sizeof(double) * nred, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+  };
+  auto true_residual = [&]() -> lqcd_status {
+    LQ_TRY(residual_eo(W, W.r64->mut(1), W.x64->ref(1), ye64, c->results, 1));
+    LQ_CU(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    LQ_CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n; k++) nrm[k] = std::sqrt(c->h_results[k]);
+    W.info->mhat_applies += 1;
+    return LQCD_OK;
+  };
+  auto copy_vec = [&](lqcd_field *dst, const lqcd_field *src) -> lqcd_status {
+    LQ_CU(cudaMemcpyAsync(dst->data[1], src->data[1], vbytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (sbytes) LQ_CU(cudaMemcpyAsync(dst->scale[1], src->scale[1], sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LQCD_OK;
+  };
+  auto scale = [&](lqcd_field *f, const std::vector<double> &fv) -> lqcd_status {
+    std::memcpy(b.hfac, fv.data(), sizeof(double) * n);
+    LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    LQ_CU(blas_scale(L, L, c->Vh, n, f->mut(1), f->ref(1), b.fac, c->stream));
+    return LQCD_OK;
+  };
+  // the coefficient set `slot` of the cycle's device coefficient array
+  auto put_cf = [&](int slot) -> double2 * {
+    return b.cf + (size_t)n * slot;
+  };
+  auto upload_cf = [&](int slot) -> lqcd_status {
+    LQ_CU(cudaMemcpyAsync(put_cf(slot), b.hcf + (size_t)n * slot, sizeof(double2) * n, cudaMemcpyHostToDevice,
+                          c->stream));
+    return LQCD_OK;
+  };
+  LQ_TRY(true_residual());
+  int nact = 0;
+  for (int k = 0; k < n; k++) {
+    active[k] = nrm[k] > target[k];
+    nact += active[k];
+  }
+  lqcd_field *x = mixed ? xlo : W.x64;
+  int it = 0;
+  while (nact > 0 && it < W.max_iter) {
+    // the cycle's residual r: r64 (normalised when mixed)
+    std::vector<double> f(n, 0.0);
+    for (int k = 0; k < n; k++) {
+      if (mixed) sigma[k] = nrm[k] > 0 ? nrm[k] : 1.0;
+      f[k] = active[k] ? (mixed ? 1.0 / sigma[k] : 1.0) : 0.0;
+      rr[k] = (active[k] ? nrm[k] * f[k] : 0.0);
+      rr[k] *= rr[k];
+    }
+    std::memcpy(b.hfac, f.data(), sizeof(double) * n);
+    LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    LQ_CU(blas_scale(L, W.hp, c->Vh, n, r->mut(1), W.r64->ref(1), b.fac, c->stream));
+    if (mixed) LQ_CU(cudaMemsetAsync(xlo->data[1], 0, (size_t)xlo->rhs_words() * 16 * n, c->stream));
+    std::vector<char> on = active;  // right-hand sides this cycle still works on
+    const std::vector<double> rr0 = rr;
+    int j = 0;
+    for (; j < m && it < W.max_iter; j++, it++) {
+      LQ_TRY(copy_vec(z[j], r));
+      LQ_TRY(op_eo(W, L, rec, 0, q[j]->mut(1), z[j]->ref(1), ye, nullptr, 0));
+      W.info->mhat_applies += 1;
+      // beta_i = (q_i, q), all i < j at once (classical Gram-Schmidt)
+      for (int i = 0; i < j; i++)
+        LQ_CU(bi_dot3(L, c->Vh, n, q[i]->ref(1), q[j]->ref(1), c->partials, b.red + 3 * (size_t)n * i, c->stream));
+      if (j > 0) {
+        LQ_TRY(sync_red());
+        for (int i = 0; i < j; i++) {
+          for (int k = 0; k < n; k++) {
+            const double *d = b.hred + 3 * (size_t)n * i + 3 * k;
+            b.hcf[(size_t)n * i + k] = on[k] ? make_double2(-d[0], -d[1]) : make_double2(0.0, 0.0);
+          }
+          LQ_TRY(upload_cf(i));
+          LQ_CU(gcr_caxpy(L, L, c->Vh, n, q[j]->mut(1), q[i]->ref(1), put_cf(i), c->stream));
+          LQ_CU(gcr_caxpy(L, L, c->Vh, n, z[j]->mut(1), z[i]->ref(1), put_cf(i), c->stream));
+        }
+      }
+      // |q|, then q, z scaled to |q| = 1
+      LQ_CU(bi_dot3(L, c->Vh, n, q[j]->ref(1), q[j]->ref(1), c->partials, b.red, c->stream));
+      LQ_TRY(sync_red());
+      std::vector<double> inv(n, 0.0);
+      for (int k = 0; k < n; k++) {
+        const double qq = b.hred[3 * k + 2];
+        if (!std::isfinite(qq)) return set_error(LQCD_ERR_NOCONV, "GCR breakdown on RHS %d at iteration %d", k, it);
+        if (on[k] && qq > 0) inv[k] = 1.0 / std::sqrt(qq);
+        else on[k] = 0;
+      }
+      LQ_TRY(scale(q[j], inv));
+      LQ_TRY(scale(z[j], inv));
+      // alpha = (q, r): x += alpha z, r -= alpha q
+      LQ_CU(bi_dot3(L, c->Vh, n, q[j]->ref(1), r->ref(1), c->partials, b.red, c->stream));
+      LQ_TRY(sync_red());
+      for (int k = 0; k < n; k++) {
+        const double *d = b.hred + 3 * k;
+        b.hcf[(size_t)n * m + k] = on[k] ? make_double2(d[0], d[1]) : make_double2(0.0, 0.0);
+        if (on[k]) rr[k] = std::max(rr[k] - (d[0] * d[0] + d[1] * d[1]), 0.0);  // |r|^2 - |alpha|^2
+      }
+      LQ_TRY(upload_cf(m));
+      LQ_CU(gcr_caxpy(px, L, c->Vh, n, x->mut(1), z[j]->ref(1), put_cf(m), c->stream));
+      for (int k = 0; k < n; k++) b.hcf[(size_t)n * m + k] = make_double2(-b.hcf[(size_t)n * m + k].x,
+                                                                          -b.hcf[(size_t)n * m + k].y);
+      LQ_TRY(upload_cf(m));
+      LQ_CU(gcr_caxpy(L, L, c->Vh, n, r->mut(1), q[j]->ref(1), put_cf(m), c->stream));
+      // end the cycle early once every right-hand side reached its target, or
+      // (mixed) once every active residual fell by delta or one reached it
+      bool all_dropped = true, reached = false, all_reached = true;
+      for (int k = 0; k < n; k++) {
+        if (!on[k]) continue;
+        const bool rk = sigma[k] * std::sqrt(rr[k]) <= target[k];
+        reached |= rk;
+        all_reached &= rk;
+        if (rr[k] > W.delta * W.delta * rr0[k]) all_dropped = false;
+      }
+      if (all_reached || (mixed && (all_dropped || reached))) {
+        j++;
+        it++;
+        break;
+      }
+    }
+    if (mixed) {  // x64 += sigma x_lo
+      for (int k = 0; k < n; k++) b.hfac[k] = active[k] ? sigma[k] : 0.0;
+      LQ_CU(cudaMemcpyAsync(b.fac, b.hfac, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      LQ_CU(blas_axpy(W.hp, LQCD_F32, c->Vh, n, W.x64->mut(1), xlo->ref(1), b.fac, c->stream));
+      W.info->reliable_updates += 1;
+    }
+    LQ_TRY(true_residual());
+    nact = 0;
+    for (int k = 0; k < n; k++) {
+      if (!active[k]) continue;
+      if (!std::isfinite(nrm[k])) return set_error(LQCD_ERR_NOCONV, "residual of RHS %d is not finite", k);
+      if (nrm[k] <= target[k]) {
+        active[k] = 0;
+        continue;
+      }
+      nact++;
+    }
+  }
+  W.info->iters = it;
+  return nact == 0 ? LQCD_OK : set_error(LQCD_ERR_NOCONV, "GCR did not converge in %d iterations", W.max_iter);
+}
+
 // One solve: staging, even-odd source, the recursion, reconstruction and the
 // FP64 true residual.  Split so that a batch of lattices can share the loop.
 struct SolveJob {
@@ -805,8 +1000,10 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
   if (prm->max_iter < 1) return set_error(LQCD_ERR_ARG, "max_iter must be >= 1");
   if (prm->nrhs < 1 || prm->nrhs > 64) return set_error(LQCD_ERR_ARG, "nrhs must be in 1..64");
   if ((int)prm->inner < 0 || (int)prm->inner > 4) return set_error(LQCD_ERR_ARG, "bad inner precision");
-  if (prm->solver != LQCD_SOLVER_CGLS && prm->solver != LQCD_SOLVER_BICGSTAB)
+  if (prm->solver != LQCD_SOLVER_CGLS && prm->solver != LQCD_SOLVER_BICGSTAB && prm->solver != LQCD_SOLVER_GCR)
     return set_error(LQCD_ERR_ARG, "bad solver %d", prm->solver);
+  if (prm->solver == LQCD_SOLVER_GCR && (prm->gcr_nkrylov < 0 || prm->gcr_nkrylov > 64))
+    return set_error(LQCD_ERR_ARG, "gcr_nkrylov must be in 0..64");
   if (prm->schur != LQCD_SCHUR_ASYM && prm->schur != LQCD_SCHUR_SYM)
     return set_error(LQCD_ERR_ARG, "bad schur %d", prm->schur);
   if (prm->outer != LQCD_F64 && prm->outer != LQCD_DF64)
@@ -815,8 +1012,11 @@ lqcd_status check_params(lqcd_ctx *c, const lqcd_solve_params *prm) {
     return set_error(LQCD_ERR_ARG, "delta must be in (0, 1)");
   if (!c->have_gauge) return set_error(LQCD_ERR_STATE, "no gauge field loaded");
   if (!c->have_kappa) return set_error(LQCD_ERR_STATE, "kappa not set (call lqcd_clover)");
-  const int recon_lo = prm->inner_recon == 18 ? 18 : 12;
-  if (prec_half(prm->inner) && recon_lo != 12) return set_error(LQCD_ERR_ARG, "FP16/BF16 inner solves need 12-real links");
+  const int recon_lo = (prm->inner_recon == 18 ? 18 : prm->inner_recon == 8 ? 8 : 12);
+  if (prec_half(prm->inner) && recon_lo == 18)
+    return set_error(LQCD_ERR_ARG, "FP16/BF16 inner solves need 12- or 8-real links");
+  if (recon_lo == 8 && prm->inner != LQCD_F32 && prm->inner != LQCD_F16)
+    return set_error(LQCD_ERR_ARG, "8-real inner links need an FP32 or FP16 inner solve");
   return LQCD_OK;
 }
 
@@ -873,7 +1073,7 @@ lqcd_status job_prepare(SolveJob &J) {
   W.c = c;
   W.nrhs = n;
   W.recon64 = prm->recon == 12 ? 12 : 18;
-  W.recon_lo = prm->inner_recon == 18 ? 18 : 12;
+  W.recon_lo = (prm->inner_recon == 18 ? 18 : prm->inner_recon == 8 ? 8 : 12);
   W.lo = prm->inner;
   W.hp = prm->inner == LQCD_F64 ? LQCD_F64 : prm->inner == LQCD_DF64 ? LQCD_DF64 : prm->outer;
   W.tol = prm->tol;
@@ -993,7 +1193,9 @@ extern "C" lqcd_status lqcd_solve(lqcd_ctx *c, double *x, const double *b, int o
   J.prm = *prm;
   J.inf = info;
   LQ_TRY(job_prepare(J));
-  const lqcd_status st = prm->solver == LQCD_SOLVER_BICGSTAB ? bicgstab(J.W, !plain_cg(prm))
+  const lqcd_status st = prm->solver == LQCD_SOLVER_GCR
+                             ? gcr(J.W, !plain_cg(prm), prm->gcr_nkrylov > 0 ? prm->gcr_nkrylov : 8)
+                         : prm->solver == LQCD_SOLVER_BICGSTAB ? bicgstab(J.W, !plain_cg(prm))
                          : plain_cg(prm)                      ? cgls_plain(J.W, J.B)
                                                               : cgls_mixed(J.W, J.B);
   return job_finish(J, st);

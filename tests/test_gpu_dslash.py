@@ -84,7 +84,7 @@ def clover_lattice(lib):
 
 @pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("df64", 18), ("f32", 18), ("f32", 12), ("f16", 12),
-                                        ("bf16", 12)])
+                                        ("bf16", 12), ("f32", 8), ("f16", 8)])
 def test_ops_clover(clover_lattice, op, prec, recon):
     lat, U, A, Ai = clover_lattice
     psi = gen.gaussian_spinor(DIMS, 2001)[0]
@@ -334,3 +334,21 @@ def test_df64_beats_fp32_and_tracks_fp64(clover_lattice):
     edf = rel(lat.dslash(psi, "MHAT", "df64", 18), expect)
     assert edf < 1e-5 * e32
     assert edf < 1e-13 and e64 < 1e-14
+
+
+def test_eight_real_links_refused_for_unit_links(lib):
+    """The 8-real rebuild divides by 1 - |U00|^2: unit links (the free field)
+    are refused for it, and still run with 12 reals."""
+    dims = (4, 4, 4, 4)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(gen.unit_gauge(dims).view(np.float64))
+    lat.clover(KAPPA, CSW)
+    psi = gen.gaussian_spinor(dims, 5)[0]
+    with pytest.raises(lib.LqcdError) as e:
+        lat.dslash(psi, "MHAT", "f32", 8)
+    assert e.value.status == lib.LQCD_ERR_ARG
+    lat.dslash(psi, "MHAT", "f32", 12)
+    for prec in ("f64", "bf16"):  # no FP64 8-real form; BF16 cannot hold the angles
+        with pytest.raises(lib.LqcdError):
+            lat.dslash(psi, "MHAT", prec, 8)
+    lat.close()

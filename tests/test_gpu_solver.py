@@ -295,3 +295,73 @@ def test_symmetric_schur_solves(lib, solver, inner, outer, nrhs):
     if solver == "cgls" and inner == "f64":
         assert info.iters < infa.iters
     lat.close()
+
+
+@pytest.mark.parametrize("inner,outer,nrhs,nk", [("f64", "f64", 1, 8), ("df64", "df64", 1, 8), ("f32", "f64", 2, 8),
+                                                 ("f16", "f64", 2, 8), ("bf16", "f64", 1, 16),
+                                                 ("f16", "df64", 1, 4)])
+def test_gcr(lib, inner, outer, nrhs, nk):
+    """Restarted GCR(m) on Mhat, plain and mixed with a reliable update after
+    each cycle: every right-hand side to a true residual of 1e-10 (recomputed
+    by the oracle), and the FP64 CGLS solution."""
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003, nrhs=nrhs)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner=inner, outer=outer, delta=0.1, recon=18, inner_recon=12,
+                            solver="gcr", gcr_nkrylov=nk, max_iter=4000)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    for k in range(nrhs):
+        assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+        assert info.true_resid[k] <= 1e-10
+    xc, stc, _ = lat.solve(b, tol=1e-10, inner="f64", recon=18)
+    assert stc == lib.LQCD_OK
+    assert rel(x, xc) < 1e-8
+    if inner not in ("f64", "df64"):
+        assert info.reliable_updates >= 1
+    lat.close()
+
+
+@pytest.mark.parametrize("inner", ["f64", "f16"])
+def test_gcr_symmetric_schur_and_point_sources(lib, inner):
+    """GCR on A_oo^-1 Mhat (rough field) and on point sources (uneven
+    residuals), to the oracle's 1e-10; bad cycle lengths are refused."""
+    dims = (8, 8, 8, 8)
+    kappa, csw = 0.14, 2.0
+    U = gen.gauge_field(dims, 1.0, 1010)
+    b = gen.point_sources(dims)[:2]
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    A = oracle.clover(dims, U, kappa, csw)
+    for schur in ("asym", "sym"):
+        x, st, info = lat.solve(b, tol=1e-10, inner=inner, nrhs=2, solver="gcr", schur=schur, max_iter=6000)
+        assert st == lib.LQCD_OK, lib.lqcd_last_error()
+        for k in range(2):
+            assert oracle.true_residual(dims, U, A, kappa, x[k], b[k]) <= 1e-10
+    for bad in (-1, 65):
+        with pytest.raises(lib.LqcdError):
+            lat.solve(b[:1], tol=1e-10, solver="gcr", gcr_nkrylov=bad)
+    lat.close()
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_mixed_solve_with_eight_real_inner_links(lib, inner):
+    """The mixed CGLS with the 8-real form for the inner operator's links: the
+    oracle's true residual of 1e-10."""
+    dims = (8, 8, 8, 16)
+    kappa, csw = 0.125, 1.0
+    U = gen.gauge_field(dims, 0.2, 1003)
+    b = gen.gaussian_spinor(dims, 2003, nrhs=1)
+    lat = lib.Lattice(dims)
+    lat.load_gauge(U.view(np.float64))
+    lat.clover(kappa, csw)
+    x, st, info = lat.solve(b, tol=1e-10, inner=inner, recon=18, inner_recon=8)
+    assert st == lib.LQCD_OK, lib.lqcd_last_error()
+    A = oracle.clover(dims, U, kappa, csw)
+    assert oracle.true_residual(dims, U, A, kappa, x[0], b[0]) <= 1e-10
+    lat.close()
