@@ -713,7 +713,8 @@ def overlap_workload(L, torch, high, eig, want_oracle, stream):
     return out
 
 
-def overlap_eigen_workload(L, torch, dims, n_ev, want_oracle, stream, nrhs=2, basis=0):
+def overlap_eigen_workload(L, torch, dims, n_ev, want_oracle, stream, nrhs=2, basis=0, hw_eig_tol=1e-10,
+                           max_filter=400):
     """The overlap eigensystem (Sec. 4: 200 pairs on a 24^3x64 lattice; here a
     synthetic stand-in, eps 0.1, rho 1.5, m 0.01): the n_ev lowest eigenpairs
     of D_ov(0)^dag D_ov(0) in the + chirality sector (and their partners) by
@@ -726,14 +727,14 @@ def overlap_eigen_workload(L, torch, dims, n_ev, want_oracle, stream, nrhs=2, ba
     U = gen.gauge_field(dims, 0.1, 1009)
     b = gen.gaussian_spinor(dims, 2009, nrhs=nrhs)
     name = "x".join(str(d) for d in dims)
-    out = {"config": {"workload": f"overlap eigensystem {name}, eps 0.1, rho 1.5, m 0.01, 20 H_W low modes, sign to "
-                                  f"1e-10 (double-float), {n_ev} eigenpairs of D_ov^dag D_ov in the + sector to "
-                                  f"1e-8, then {nrhs} Gaussian RHS by the mixed overlap CG to 1e-10 plain and "
-                                  f"deflated"}}
+    out = {"config": {"workload": f"overlap eigensystem {name}, eps 0.1, rho 1.5, m 0.01, 20 H_W low modes to "
+                                  f"{hw_eig_tol:g}, sign to 1e-10 (double-float), {n_ev} eigenpairs of D_ov^dag D_ov "
+                                  f"in the + sector to 1e-8, then {nrhs} Gaussian RHS by the mixed overlap CG to "
+                                  f"1e-10 plain and deflated"}}
     with L.Lattice(dims, stream=stream) as lat:
         lat.load_gauge(U.view(np.float64))
-        prm = L.overlap_params(rho=1.5, mass=0.01, n_low=20, sign_tol=1e-10, eig_tol=1e-10, max_filter=400,
-                               high="df64", eig_method="lanczos")
+        prm = L.overlap_params(rho=1.5, mass=0.01, n_low=20, sign_tol=1e-10, eig_tol=hw_eig_tol,
+                               max_filter=max_filter, high="df64", eig_method="lanczos")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, oinfo = L.lqcd_overlap_setup(lat.ctx, prm, raise_on_noconv=False)
@@ -795,7 +796,8 @@ def run_ov_eigen(args):
     dims = tuple(int(v) for v in args.ov_eigen.split(","))
     out = {"metric": "overlap eigensystem and deflated overlap solve time"}
     out.update(overlap_eigen_workload(L, torch, dims, args.n_ev, not args.no_cpu_baseline,
-                                      torch.cuda.current_stream(), basis=args.ev_basis))
+                                      torch.cuda.current_stream(), basis=args.ev_basis, hw_eig_tol=args.hw_eig_tol,
+                                      max_filter=args.max_filter))
     print(json.dumps(out))
     return 0
 
@@ -983,6 +985,8 @@ def main():
     ap.add_argument("--ov-eigen", default=None, help="run only the overlap eigensystem on lattice L0,L1,L2,L3")
     ap.add_argument("--n-ev", type=int, default=200, help="eigenpairs for --ov-eigen")
     ap.add_argument("--ev-basis", type=int, default=0, help="Lanczos basis for --ov-eigen (0: automatic)")
+    ap.add_argument("--hw-eig-tol", type=float, default=1e-10, help="H_W low-mode tolerance for --ov-eigen")
+    ap.add_argument("--max-filter", type=int, default=400, help="H_W low-mode restart cap for --ov-eigen")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
