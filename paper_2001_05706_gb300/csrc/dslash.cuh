@@ -493,6 +493,70 @@ __device__ __forceinline__ void project_packed(int mu, float s, const unsigned (
   }
 }
 
+// FP16/BF16 hop in packed FP32x2 arithmetic (sm_100+ __ffma2_rn): the two
+// projected half-spinors h0, h1 sit in the two lanes of each float2 (real
+// parts together, imaginary parts together), so U h0 and U h1 take one
+// instruction per link-entry product (the entry broadcast to both lanes), and
+// the accumulators pair spins (0, 1) and (2, 3): f (U h) adds to the upper
+// pair as is, and to the lower pair as is (mu = 3) or lane-signed and
+// re/im-exchanged (mu = 2); mu = 0, 1 exchange the two spins, which packed
+// operands cannot, and stay scalar.  Each product sums the real-part terms
+// and the imaginary-part terms apart (A - B, C + D) where the scalar
+// link_mul interleaves them: the same products, another rounding order.
+__device__ __forceinline__ float2 pr_bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ void hop_pair_accumulate(int mu, bool dag, float s, float f, const cx<float> (&U)[3][3],
+                                                    const cx<float> (&h)[2][3], float2 (&aur)[3], float2 (&aui)[3],
+                                                    float2 (&alr)[3], float2 (&ali)[3]) {
+  float2 hr[3], hi[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    hr[c] = make_float2(h[0][c].r, h[1][c].r);
+    hi[c] = make_float2(h[0][c].i, h[1][c].i);
+  }
+  const float2 ff = pr_bc(f);
+  const float fs = f * s;
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    float2 A = pr_bc(0.0f), B = pr_bc(0.0f), C = pr_bc(0.0f), D = pr_bc(0.0f);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const cx<float> u = dag ? U[c][r] : U[r][c];
+      const float2 ur = pr_bc(u.r), ui = pr_bc(u.i);
+      A = __ffma2_rn(ur, hr[c], A);
+      B = __ffma2_rn(ui, hi[c], B);
+      C = __ffma2_rn(ur, hi[c], C);
+      D = __ffma2_rn(ui, hr[c], D);
+    }
+    // U h: (A - B, C + D); U^dag h (entries conj(U[c][r])): (A + B, C - D)
+    const float2 nB = make_float2(-B.x, -B.y), nD = make_float2(-D.x, -D.y);
+    const float2 tr = __fadd2_rn(A, dag ? B : nB), ti = __fadd2_rn(C, dag ? nD : D);
+    aur[r] = __ffma2_rn(ff, tr, aur[r]);
+    aui[r] = __ffma2_rn(ff, ti, aui[r]);
+    switch (mu) {
+      case 0:  // spin 2 += -i fs t1, spin 3 += -i fs t0
+        alr[r].x = fmaf(fs, ti.y, alr[r].x);
+        ali[r].x = fmaf(-fs, tr.y, ali[r].x);
+        alr[r].y = fmaf(fs, ti.x, alr[r].y);
+        ali[r].y = fmaf(-fs, tr.x, ali[r].y);
+        break;
+      case 1:  // spin 2 += fs t1, spin 3 -= fs t0
+        alr[r].x = fmaf(fs, tr.y, alr[r].x);
+        ali[r].x = fmaf(fs, ti.y, ali[r].x);
+        alr[r].y = fmaf(-fs, tr.x, alr[r].y);
+        ali[r].y = fmaf(-fs, ti.x, ali[r].y);
+        break;
+      case 2:  // spin 2 += -i fs t0, spin 3 += i fs t1
+        alr[r] = __ffma2_rn(make_float2(fs, -fs), ti, alr[r]);
+        ali[r] = __ffma2_rn(make_float2(-fs, fs), tr, ali[r]);
+        break;
+      default:  // spin 2 += fs t0, spin 3 += fs t1
+        alr[r] = __ffma2_rn(pr_bc(fs), tr, alr[r]);
+        ali[r] = __ffma2_rn(pr_bc(fs), ti, ali[r]);
+        break;
+    }
+  }
+}
+
 // acc += f * reconstruct(h): f folds the storage scale of the neighbour and
 // the boundary sign into the FMAs of the accumulation
 template <typename T>
@@ -655,6 +719,17 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
   };
   issue(0, 0u);
   issue(1, 0u);
+  // FP16/BF16: the accumulators paired over spins (0, 1) and (2, 3), see hop_pair_accumulate
+  float2 aur[3], aui[3], alr[3], ali[3];
+  if constexpr (IsHalf<S>::value) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      aur[c] = make_float2((float)acc[0][c].r, (float)acc[1][c].r);
+      aui[c] = make_float2((float)acc[0][c].i, (float)acc[1][c].i);
+      alr[c] = make_float2((float)acc[2][c].r, (float)acc[3][c].r);
+      ali[c] = make_float2((float)acc[2][c].i, (float)acc[3][c].i);
+    }
+  }
 #pragma unroll kPipeUnroll
   for (int k = 0; k < 8; k++) {
     const int mu = k >> 1, dir = (k & 1) ? -1 : +1, b = k & 1;
@@ -762,8 +837,21 @@ __device__ __forceinline__ void hop_pipelined(const DslashParams &P, long h, int
       }
       project<T>(mu, s, psi, hh);
     }
-    link_mul(U, dir < 0, hh, uh);
-    reconstruct(mu, s, f, uh, acc);
+    if constexpr (IsHalf<S>::value) {
+      hop_pair_accumulate(mu, dir < 0, s, f, U, hh, aur, aui, alr, ali);
+    } else {
+      link_mul(U, dir < 0, hh, uh);
+      reconstruct(mu, s, f, uh, acc);
+    }
+  }
+  if constexpr (IsHalf<S>::value) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      acc[0][c] = mk<T>(aur[c].x, aui[c].x);
+      acc[1][c] = mk<T>(aur[c].y, aui[c].y);
+      acc[2][c] = mk<T>(alr[c].x, ali[c].x);
+      acc[3][c] = mk<T>(alr[c].y, ali[c].y);
+    }
   }
 }
 
