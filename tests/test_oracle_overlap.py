@@ -230,3 +230,31 @@ def test_sector_vectors_against_the_polynomial_operator():
             assert np.linalg.norm((h - mu[i] * chi[i]).ravel()) < 1e-9
             w = D @ chi[i].ravel()
             assert np.linalg.norm(D.conj().T @ (D @ w) - mu[i] * w) < 1e-9 * max(1.0, np.linalg.norm(w))
+
+
+def test_overlap_acts_on_a_pair_as_a_two_by_two_matrix():
+    """The deflated CG's identity: for a sector-s eigenvector chi with
+    eps chi = c chi + n eta (eta of the other chirality, |eta| = 1),
+    D_ov(0) chi = rho ((1 + s c) chi - s n eta) and
+    D_ov(0) eta = rho (s n chi + (1 + s c) eta), checked on the dense D_ov."""
+    dims = (2, 2, 2, 4)
+    U = gen.gauge_field(dims, 0.4, 47)
+    D = oracle.overlap_dense(dims, U, RHO)
+    N = D.shape[0]
+    g5 = np.ones(N)
+    g5[oracle.chirality_indices(dims, -1)] = -1.0
+    eps = g5[:, None] * (D / RHO - np.eye(N))  # D = rho (1 + g5 eps)
+    for s in (+1, -1):
+        mu, chi = oracle.overlap_sector_eigensystem(dims, U, RHO, 6, s)
+        for i in range(6):
+            x = chi[i].ravel()
+            e = eps @ x
+            c = np.vdot(x, e).real
+            other = oracle.chirality_indices(dims, -s)
+            y = np.zeros(N, dtype=np.complex128)
+            y[other] = e[other]
+            n = np.linalg.norm(y)
+            eta = y / n
+            assert abs(mu[i] - 2 * RHO**2 * (1 + s * c)) < 1e-10
+            assert np.linalg.norm(D @ x - RHO * ((1 + s * c) * x - s * n * eta)) < 1e-10
+            assert np.linalg.norm(D @ eta - RHO * (s * n * x + (1 + s * c) * eta)) < 1e-10
