@@ -89,7 +89,7 @@ constexpr int kOvMaxBlock = 96;
 // pay for its cost per sweep.
 // Lanczos basis size (thick restart keeps the block size m of vectors)
 #ifndef LQCD_OV_LANCZOS_MMAX
-#define LQCD_OV_LANCZOS_MMAX 128
+#define LQCD_OV_LANCZOS_MMAX 256
 #endif
 #ifndef LQCD_OV_BLOCK_MULT
 #define LQCD_OV_BLOCK_MULT 2
@@ -1936,8 +1936,10 @@ extern "C" lqcd_status lqcd_overlap_setup(lqcd_ctx *c, const lqcd_overlap_params
   };
   double tol2 = prm->eig_tol;
   if (prm->eig_method == LQCD_EIG_LANCZOS) {
-    // restart size m (the block of the subspace method), basis of up to 2m
-    const int mmax = std::min<long>(std::min(2 * m, LQCD_OV_LANCZOS_MMAX), N - 1);
+    // restart size m (the block of the subspace method), basis of max(2m, m + 104): on a
+    // dense low spectrum (24^3 x 64, eps 0.1) a basis of 2m = 80 for 20 modes stalled for
+    // 1000 restarts; the thick restart needs room beyond the kept block
+    const int mmax = std::min<long>(std::min(std::max(2 * m, m + 104), LQCD_OV_LANCZOS_MMAX), N - 1);
     if (mmax < m + 8) return set_error(LQCD_ERR_ARG, "lattice too small for a Lanczos basis of %d vectors", m + 8);
     // the H_W residual of the result is about |lambda| / gap times its H_W^2
     // residual: the Krylov method is asked for 1 % of eig_tol on H_W^2, cheap
