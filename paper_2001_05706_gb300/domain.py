@@ -25,6 +25,15 @@ One exchange of 2 slices per side per application (24 reals per site),
 against the spin-projected single-slice faces (12 reals) of a two-exchange
 scheme: fewer synchronisation points, twice the bytes.
 
+With overlap=True the interior work runs while the halos are in flight:
+after the sends are posted, K2a runs on slices [HALO + 1, Lt + HALO - 1)
+(their t-neighbours of x_o are all interior) and K2b on
+[HALO + 2, Lt + HALO - 2) (their t-neighbours of y_e are those slices);
+once the ghosts have arrived K2a completes its two edge ranges and K2b the
+interior's edges.  Every output slice is still computed once, by the same
+kernel from the same values, so z is bit for bit the sequential result; the
+norms are the sums of the pieces' fixed-order sums.
+
 CG on the normal equations (CGLS) runs across domains with the global sums
 (||q||^2; then ||r||^2 and ||s||^2 together) reduced by the exchange's
 allreduce: two reductions and two halo exchanges per iteration.
@@ -65,6 +74,13 @@ class Partition:
         self.send_hi = (lt, lt + HALO)         # to the domain above (its lower ghosts)
         self.ghost_lo = (0, HALO)
         self.ghost_hi = (lt + HALO, lt + 2 * HALO)
+        # the overlapped schedule: what needs no ghost data, and the rest
+        a0, a1 = self.k2a_slices
+        self.k2a_inner = (HALO + 1, max(HALO + 1, lt + HALO - 1))
+        self.k2a_edges = _ranges((a0, self.k2a_inner[0]), (self.k2a_inner[1], a1))
+        b0, b1 = self.interior
+        self.k2b_inner = (HALO + 2, max(HALO + 2, lt + HALO - 2))
+        self.k2b_edges = _ranges((b0, min(self.k2b_inner[0], b1)), (max(self.k2b_inner[1], b0 + 2), b1))
         # ghost data arriving across the global time boundary carries its sign
         self.factor_lo = -1.0 if (self.tbc and rank == 0) else 1.0
         self.factor_hi = -1.0 if (self.tbc and rank == ndomains - 1) else 1.0
@@ -81,6 +97,19 @@ class Partition:
         return field_local[a:b]
 
 
+def _ranges(*rs):
+    """The non-empty ranges among rs, adjacent ones merged."""
+    out = []
+    for a, b in rs:
+        if b <= a:
+            continue
+        if out and out[-1][1] == a:
+            out[-1] = (out[-1][0], b)
+        else:
+            out.append((a, b))
+    return out
+
+
 class LocalExchange:
     """Halo routing and global sums between the domains held by one process
     (domain d's neighbours are d - 1 and d + 1, cyclically)."""
@@ -94,6 +123,15 @@ class LocalExchange:
         if len(sends) != self.n:
             raise ValueError("one send pair per domain")
         return [(sends[(d - 1) % self.n][1], sends[(d + 1) % self.n][0]) for d in range(self.n)]
+
+    def halo_start(self, sends):
+        """Post the exchange; halo_finish returns what halo() does.  Within one
+        process the routing is immediate (the send buffers are not written
+        again before the next exchange)."""
+        return self.halo(sends)
+
+    def halo_finish(self, pending):
+        return pending
 
     def allreduce(self, parts):
         """parts[d] = numpy array of domain d; the element-wise sum over domains."""
@@ -115,12 +153,20 @@ class DistExchange:
         self.size = dist.get_world_size(group)
 
     def halo(self, sends):
+        return self.halo_finish(self.halo_start(sends))
+
+    def halo_start(self, sends):
+        """Post the sends and receives and return without waiting.  With NCCL
+        they run on the communicator's stream, ordered after the work already
+        queued on torch's current stream (the domain's context stream must be
+        that stream, the default); halo_finish makes the current stream wait
+        for the receives."""
         import torch
         if len(sends) != 1:
             raise ValueError("one domain per rank")
         lo, hi = sends[0]
         if self.size == 1:
-            return [(hi.clone(), lo.clone())]
+            return [], [(hi.clone(), lo.clone())]
         down = (self.rank - 1) % self.size
         up = (self.rank + 1) % self.size
         recv_hi = torch.empty_like(lo)  # the domain above's lo
@@ -129,9 +175,13 @@ class DistExchange:
                self.dist.P2POp(self.dist.irecv, recv_hi, up, self.group),
                self.dist.P2POp(self.dist.isend, hi, up, self.group),
                self.dist.P2POp(self.dist.irecv, recv_lo, down, self.group)]
-        for req in self.dist.batch_isend_irecv(ops):
+        return self.dist.batch_isend_irecv(ops), [(recv_lo, recv_hi)]
+
+    def halo_finish(self, pending):
+        reqs, recvs = pending
+        for req in reqs:
             req.wait()
-        return [(recv_lo, recv_hi)]
+        return recvs
 
     def allreduce(self, parts):
         import torch
@@ -228,18 +278,22 @@ class GpuDomain:
         lqcd_field_slices(self.ctx, f, 1, *self.part.ghost_hi, z, 1)
 
     # ---- operators and BLAS -------------------------------------------------
-    def mhat(self, out, x, nrhs, dagger=False):
-        """out_o = Mhat x_o (or Mhat^dag x_o) on the interior, x's ghosts
-        already filled; returns the per-RHS ||out||^2 over the interior."""
-        from . import LQCD_EVEN, lqcd_field_create, lqcd_k2a_slices, lqcd_k2b_slices
+    def k2a(self, x, nrhs, t0, t1, dagger=False):
+        """y_e = A_ee^-1 D_eo x_o (dagger: with g5 on x) on slices [t0, t1) of
+        the domain's intermediate even field."""
+        from . import LQCD_EVEN, LQCD_F64, lqcd_field_create, lqcd_k2a_slices
         if self._y is None or self._ynrhs != nrhs:
             if self._y is not None:
                 self.free(self._y)
-            from . import LQCD_F64
             self._y = lqcd_field_create(self.ctx, LQCD_F64, LQCD_EVEN, nrhs)
             self._ynrhs = nrhs
-        lqcd_k2a_slices(self.ctx, self.recon, int(dagger), self._y, x, *self.part.k2a_slices)
-        return lqcd_k2b_slices(self.ctx, self.recon, int(dagger), out, x, self._y, *self.part.interior, nrhs=nrhs)
+        lqcd_k2a_slices(self.ctx, self.recon, int(dagger), self._y, x, t0, t1)
+
+    def k2b(self, out, x, nrhs, t0, t1, dagger=False):
+        """out_o = A_oo x_o - kappa^2 D_oe y_e (dagger: g5 on the hop) on slices
+        [t0, t1); returns the per-RHS ||out_o||^2 over them."""
+        from . import lqcd_k2b_slices
+        return lqcd_k2b_slices(self.ctx, self.recon, int(dagger), out, x, self._y, t0, t1, nrhs=nrhs)
 
     def axpby(self, y, a, b, x):
         from . import lqcd_field_axpby
@@ -254,25 +308,50 @@ class GpuDomain:
 # the distributed operator and solver (any domain objects with the methods above)
 # ---------------------------------------------------------------------------
 
-def dd_mhat(domains, exchange, outs, xs, nrhs, dagger=False):
+def _dd_apply(domains, exchange, outs, xs, nrhs, dagger, overlap):
     """outs[d] = Mhat xs[d] (or the adjoint) on each domain's interior, with one
-    halo exchange; x's ghost slices are cleared again afterwards.  Returns the
-    global per-RHS ||Mhat x||^2."""
+    halo exchange; x's ghost slices are cleared again afterwards.  Returns each
+    domain's per-RHS ||Mhat x||^2 over its interior (not yet reduced)."""
     sends = [d.pack(x, nrhs) for d, x in zip(domains, xs)]
+    parts = [np.zeros(nrhs) for _ in domains]
+    if overlap:
+        pending = exchange.halo_start(sends)
+        for i, (d, x, out) in enumerate(zip(domains, xs, outs)):
+            if d.part.k2a_inner[1] > d.part.k2a_inner[0]:
+                d.k2a(x, nrhs, *d.part.k2a_inner, dagger)
+            if d.part.k2b_inner[1] > d.part.k2b_inner[0]:
+                parts[i] = parts[i] + d.k2b(out, x, nrhs, *d.part.k2b_inner, dagger)
+        recvs = exchange.halo_finish(pending)
+        for i, (d, x, out, (rlo, rhi)) in enumerate(zip(domains, xs, outs, recvs)):
+            d.unpack(x, rlo, rhi)
+            for t0, t1 in d.part.k2a_edges:
+                d.k2a(x, nrhs, t0, t1, dagger)
+            for t0, t1 in d.part.k2b_edges:
+                parts[i] = parts[i] + d.k2b(out, x, nrhs, t0, t1, dagger)
+            d.clear_ghosts(x, nrhs)
+        return parts
     recvs = exchange.halo(sends)
-    parts = []
-    for d, x, out, (rlo, rhi) in zip(domains, xs, outs, recvs):
+    for i, (d, x, out, (rlo, rhi)) in enumerate(zip(domains, xs, outs, recvs)):
         d.unpack(x, rlo, rhi)
-        parts.append(d.mhat(out, x, nrhs, dagger))
+        d.k2a(x, nrhs, *d.part.k2a_slices, dagger)
+        parts[i] = d.k2b(out, x, nrhs, *d.part.interior, dagger)
         d.clear_ghosts(x, nrhs)
-    return exchange.allreduce(parts)
+    return parts
 
 
-def dd_cgls(domains, exchange, xs, bs, nrhs, tol=1e-10, max_iter=10000):
+def dd_mhat(domains, exchange, outs, xs, nrhs, dagger=False, overlap=False):
+    """outs[d] = Mhat xs[d] (or the adjoint) on each domain's interior, with one
+    halo exchange (overlapped with the interior work when overlap is set);
+    returns the global per-RHS ||Mhat x||^2."""
+    return exchange.allreduce(_dd_apply(domains, exchange, outs, xs, nrhs, dagger, overlap))
+
+
+def dd_cgls(domains, exchange, xs, bs, nrhs, tol=1e-10, max_iter=10000, overlap=False):
     """CG on the normal equations of Mhat x = b across domains (x starts at 0;
     every right-hand side its own recursion, parked once converged).  Stops
     when the recomputed ||b - Mhat x|| <= tol ||b|| for every right-hand side.
-    Returns (iterations, relative residuals)."""
+    overlap: every operator application overlaps its halo exchange with the
+    interior work.  Returns (iterations, relative residuals)."""
     D = list(zip(domains, xs, bs))
     one, zero = np.ones(nrhs), np.zeros(nrhs)
     mk = lambda: [d.new_field(nrhs) for d in domains]
@@ -283,7 +362,7 @@ def dd_cgls(domains, exchange, xs, bs, nrhs, tol=1e-10, max_iter=10000):
         for d, rr_, (_, _, b) in zip(domains, r, D):
             d.axpby(rr_, one, zero, b)
         bn2 = exchange.allreduce([d.norm2s(b, nrhs) for d, _, b in D])
-        gamma = dd_mhat(domains, exchange, s, r, nrhs, dagger=True)
+        gamma = dd_mhat(domains, exchange, s, r, nrhs, dagger=True, overlap=overlap)
         for d, pp, ss in zip(domains, p, s):
             d.axpby(pp, one, zero, ss)
         active = np.ones(nrhs, dtype=bool)
@@ -292,25 +371,19 @@ def dd_cgls(domains, exchange, xs, bs, nrhs, tol=1e-10, max_iter=10000):
         rel = np.ones(nrhs)
         while it < max_iter:
             it += 1
-            qq = dd_mhat(domains, exchange, q, p, nrhs)
+            qq = dd_mhat(domains, exchange, q, p, nrhs, overlap=overlap)
             alpha = np.where(active & (qq > 0), gamma / np.where(qq > 0, qq, 1.0), 0.0)
             for d, (_, x, _), pp, rr_, qv in zip(domains, D, p, r, q):
                 d.axpby(x, alpha, one, pp)
                 d.axpby(rr_, -alpha, one, qv)
             rparts = [d.norm2s(rr_, nrhs) for d, rr_ in zip(domains, r)]
-            gparts = []
             # s = Mhat^dag r, and the two sums reduced together
-            sends = [d.pack(rr_, nrhs) for d, rr_ in zip(domains, r)]
-            recvs = exchange.halo(sends)
-            for d, rr_, ss, (rlo, rhi) in zip(domains, r, s, recvs):
-                d.unpack(rr_, rlo, rhi)
-                gparts.append(d.mhat(ss, rr_, nrhs, dagger=True))
-                d.clear_ghosts(rr_, nrhs)
+            gparts = _dd_apply(domains, exchange, s, r, nrhs, True, overlap)
             both = exchange.allreduce([np.concatenate([a, b]) for a, b in zip(rparts, gparts)])
             rr, gnew = both[:nrhs], both[nrhs:]
             if np.all(~active | (rr <= target)):
                 # recompute the residual: q = b - Mhat x
-                dd_mhat(domains, exchange, q, xs, nrhs)
+                dd_mhat(domains, exchange, q, xs, nrhs, overlap=overlap)
                 for d, qv, (_, _, b) in zip(domains, q, D):
                     d.axpby(qv, one, -one, b)
                 rt = exchange.allreduce([d.norm2s(qv, nrhs) for d, qv in zip(domains, q)])

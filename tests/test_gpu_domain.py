@@ -38,9 +38,12 @@ def _domains(L, dims, ndom, U, tbc):
     return doms, LocalExchange(ndom)
 
 
-@pytest.mark.parametrize("ndom,tbc", [(2, 1), (4, 1), (2, 0), (1, 1)])
+@pytest.mark.parametrize("ndom,tbc,overlap", [(2, 1, False), (4, 1, False), (2, 0, False), (1, 1, False),
+                                              (2, 1, True), (4, 1, True), (1, 0, True)])
 @pytest.mark.parametrize("dagger", [False, True])
-def test_domains_reproduce_mhat_bitwise(lib, ndom, tbc, dagger):
+def test_domains_reproduce_mhat_bitwise(lib, ndom, tbc, overlap, dagger):
+    """Sequential and overlapped schedules (the interior slices computed
+    before the halo is unpacked) both give the single-domain operator."""
     from paper_2001_05706_gb300.domain import dd_mhat
     L = lib
     dims = (8, 6, 4, 16)
@@ -57,7 +60,7 @@ def test_domains_reproduce_mhat_bitwise(lib, ndom, tbc, dagger):
         zs = [d.new_field(2) for d in doms]
         for d, x in zip(doms, xs):
             d.import_global(x, psi)
-        n2 = dd_mhat(doms, ex, zs, xs, 2, dagger=dagger)
+        n2 = dd_mhat(doms, ex, zs, xs, 2, dagger=dagger, overlap=overlap)
         got = np.concatenate([d.export_interior(z, 2) for d, z in zip(doms, zs)], axis=1)
         odd = oracle.keep_parity(dims, np.ones(oracle.spinor_shape(dims)), 1) != 0
         assert np.array_equal(got[:, odd], full[:, odd])
@@ -72,7 +75,8 @@ def test_domains_reproduce_mhat_bitwise(lib, ndom, tbc, dagger):
             d.close()
 
 
-def test_domains_cgls_solves_the_schur_system(lib):
+@pytest.mark.parametrize("overlap", [False, True])
+def test_domains_cgls_solves_the_schur_system(lib, overlap):
     from paper_2001_05706_gb300.domain import dd_cgls
     L = lib
     dims = (8, 6, 4, 16)
@@ -84,7 +88,7 @@ def test_domains_cgls_solves_the_schur_system(lib):
         bs = [d.new_field(2) for d in doms]
         for d, bf in zip(doms, bs):
             d.import_global(bf, b)
-        it, res = dd_cgls(doms, ex, xs, bs, 2, tol=1e-10)
+        it, res = dd_cgls(doms, ex, xs, bs, 2, tol=1e-10, overlap=overlap)
         assert np.all(res <= 1e-10)
         x = np.concatenate([d.export_interior(xf, 2) for d, xf in zip(doms, xs)], axis=1)
         for d, xf, bf in zip(doms, xs, bs):
