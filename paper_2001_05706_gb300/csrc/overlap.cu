@@ -1234,7 +1234,7 @@ namespace {
 // fixed Chebyshev filter this adapts its polynomial to the spectrum and
 // applies H_W^2 to one vector per step instead of a whole block per filter
 // degree.  H_W^2 runs in FP64 or double-float; the basis, the Gram
-// coefficients and the rotations are FP64 (cuBLAS ZGEMM).
+// coefficients and the rotations are FP64 (the library's own Gram and rotation kernels).
 struct LanczosResult {
   int kneed = 0, cycles = 0;
   long applies = 0;

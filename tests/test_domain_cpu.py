@@ -211,11 +211,14 @@ def _worker(rank, world, port, tbc, dagger, overlap, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("tbc,dagger,overlap", [(1, False, False), (1, True, False), (1, True, True)])
-def test_two_gloo_ranks_match_the_oracle(tbc, dagger, overlap):
+@pytest.mark.parametrize("world,tbc,dagger,overlap", [(2, 1, False, False), (2, 1, True, False), (2, 1, True, True),
+                                                      (4, 1, False, True)])
+def test_gloo_ranks_match_the_oracle(world, tbc, dagger, overlap):
+    """Two ranks (both neighbours the same peer) and four (distinct peers
+    below and above) against the oracle on the whole lattice."""
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
-    world, port = 2, _free_port()
+    port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     procs = [ctx.Process(target=_worker, args=(r, world, port, tbc, dagger, overlap, q)) for r in range(world)]
