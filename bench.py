@@ -813,6 +813,62 @@ def run_overlap(args):
     return 0
 
 
+def run_multigrid(args):
+    """The 3-level multigrid solve on its own (--multigrid L0,L1,L2,L3): the
+    paper's aggregation layout, blocks (4,4,4,4) and then (2,2,2,2), with 24
+    near-null vectors per level, against the library's FP64 and mixed CGLS
+    on the same full-lattice system; the solution checked by the oracle."""
+    import torch
+    import gen
+    import paper_2001_05706_gb300 as L
+    from paper_2001_05706_gb300 import multigrid as gmg
+    torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.multigrid.split(","))
+    V = int(np.prod(dims))
+    kappa, csw, eps, nv = 0.1285, 1.0, 0.3, 24
+    blocks = [(4, 4, 4, 4), (2, 2, 2, 2)]
+    U = gen.gauge_field(dims, eps, 1011)
+    b = gen.gaussian_spinor(dims, 2011)
+    cfg = {"workload": f"Wilson-clover M x = b on {'x'.join(map(str, dims))}, eps {eps}, kappa {kappa}, c_sw {csw}, "
+                       f"Gaussian source, tol 1e-10; 3-level multigrid, blocks {blocks[0]} and {blocks[1]}, "
+                       f"{nv} near-null vectors per level (30 GCR steps each), K-cycle (0 pre / 4 post MR, coarse "
+                       "GCR to 0.25), outer flexible GCR(16)"}
+    out = {"metric": "multigrid set-up and solve time to 1e-10", "config": cfg}
+    with L.Lattice(dims, 1) as lat:
+        lat.load_gauge(U.view(np.float64))
+        lat.clover(kappa, csw)
+        starts = []
+        n, Vl = 12, V
+        for k, blk in enumerate(blocks):
+            starts.append(gen.gaussian(2 * nv * Vl * n, 2100 + k).view(np.complex128).reshape(nv, Vl, n))
+            Vl, n = Vl // int(np.prod(blk)), 2 * nv
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = gmg.fine_stencil(lat)
+        mg = gmg.Multigrid(st, blocks, starts, setup_iters=30)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        bd = torch.from_numpy(b.reshape(V, 12).copy()).to("cuda")
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        x, it, rel = mg.solve(bd, 1e-10, maxiter=300)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        xh = x.cpu().numpy().reshape(b.shape)
+        out["multigrid"] = {"setup_seconds": t1 - t0, "solve_seconds": t3 - t2, "outer_iters": it,
+                            "rel_resid_gpu": rel, "levels": [{"dims": list(op.dims), "n": op.n} for op in mg.ops]}
+        for name, inner in (("cgls_fp64", "f64"), ("cgls_mixed_f16", "f16")):
+            lat.solve(b, 1e-10, inner)  # warm the autotuner
+            xs, stt, info = lat.solve(b, 1e-10, inner)
+            out[name] = {"seconds": info.seconds, "iters": info.iters, "status": int(stt)}
+    if not args.no_cpu_baseline:  # the oracle's check of the solution, after the timed regions
+        import oracle
+        A = oracle.clover(dims, U, kappa, csw)
+        out["multigrid"]["oracle_true_resid"] = oracle.true_residual(dims, U, A, kappa, xh, b)
+    print(json.dumps(out))
+    return 0
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2001_05706_gb300 as L
@@ -988,6 +1044,7 @@ def main():
     ap.add_argument("--hw-eig-tol", type=float, default=1e-10, help="H_W low-mode tolerance for --ov-eigen")
     ap.add_argument("--max-filter", type=int, default=400, help="H_W low-mode restart cap for --ov-eigen")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
+    ap.add_argument("--multigrid", default=None, help="run only the multigrid solve on lattice L0,L1,L2,L3")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
                     help="--overlap: arithmetic of the FP64 parts (FP64 or double-float)")
@@ -1016,6 +1073,8 @@ def main():
         return run_overlap(args) if rank == 0 else 0
     if args.ov_eigen:
         return run_ov_eigen(args) if rank == 0 else 0
+    if args.multigrid:
+        return run_multigrid(args) if rank == 0 else 0
     if args.solve_lattice:
         return run_solve_only(args) if rank == 0 else 0
     return run_gpu(args, rank, world, local_rank)

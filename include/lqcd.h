@@ -488,6 +488,75 @@ lqcd_status lqcd_field_axpby(lqcd_ctx *ctx, lqcd_field *y, const double *a, cons
  * right-hand side, host array of nrhs doubles (nrhs <= 256); blocks. */
 lqcd_status lqcd_field_norm2s(lqcd_ctx *ctx, const lqcd_field *f, double *out);
 
+/* ---- adaptive multigrid: building blocks ------------------------------- */
+
+/* The paper's clover inverter at scale is QUDA's 3-level multigrid (Sec. 4:
+ * aggregation blocks (4,4,4,4) and then (2,2,2,2); Table 1: all parts a
+ * clover multigrid needs).  The paper gives no steps; these calls are those
+ * of standard adaptive aggregation multigrid, and the Krylov iteration and
+ * cycle around them are the caller's (paper_2001_05706_gb300/multigrid.py).
+ *
+ * Every level is a nearest-neighbour stencil on a periodic lattice dims[4]
+ * (x fastest, V sites), with n complex components per site (even, 2..64),
+ * the first n/2 of chirality +1 and the last n/2 of chirality -1:
+ *   D v(x) = X(x) v(x) + sum_mu F_mu(x) v(x + mu) + B_mu(x) v(x - mu).
+ * Arrays are the caller's device memory of the current device, complex FP64
+ * as interleaved (re, im) pairs, 16-byte aligned: fields (V, n), X (V, n, n),
+ * F and B (4, V, n, n) row-major, the prolongator P (V, n, nc) with
+ * nc = 2 nv coarse components per block.  A block of block[mu] sites per
+ * direction (dividing dims) is one coarse site; the coarse lattice is
+ * dims / block.  Errors: LQCD_ERR_ARG for NULL, misaligned or host pointers
+ * and sizes out of range; LQCD_ERR_CUDA for launch failures.  Asynchronous on
+ * the context's stream unless stated. */
+
+/* X, F, B of M = A - kappa D_W on the context's lattice: X = the clover term
+ * A (c_sw = 0: the identity), F_mu = -kappa (1 - gamma_mu) U_mu(x), B_mu =
+ * -kappa (1 + gamma_mu) U_mu(x - mu)^dag, with -1 on hops across the t
+ * boundary when the context is antiperiodic; n = 12 (index 3 spin + colour,
+ * DeGrand-Rossi, gamma5 = diag(1, 1, -1, -1)).  X holds V 144 complex, F and
+ * B 4 V 144.  LQCD_ERR_STATE without a gauge field or lqcd_clover. */
+lqcd_status lqcd_mg_fine_stencil(lqcd_ctx *ctx, void *X, void *F, void *B);
+
+/* out = D in for the stencil (X, F, B) on dims with n components; in and out
+ * distinct. */
+lqcd_status lqcd_mg_apply(lqcd_ctx *ctx, const int dims[4], int n, const void *X, const void *F, const void *B,
+                          const void *in, void *out);
+
+/* The prolongator P (V, n, 2 nv) of nv vectors vecs (nv, V, n): on each block
+ * and chirality the vectors restricted there, orthonormalised in their order
+ * by Gram-Schmidt (classical, applied twice; real positive diagonal), coarse
+ * components [chirality +1: nv, chirality -1: nv]; entries across
+ * chiralities zero.  nv <= 32 and <= the block's sites x n/2.  Blocks;
+ * LQCD_ERR_SINGULAR when a vector is dependent (within 1e-12) on the earlier
+ * ones on some block. */
+lqcd_status lqcd_mg_orthonormalize(lqcd_ctx *ctx, const int dims[4], int n, const int block[4], int nv,
+                                   const void *vecs, void *P);
+
+/* out (V, n) = P w for a coarse field w (dims / block sites, nc components). */
+lqcd_status lqcd_mg_prolong(lqcd_ctx *ctx, const int dims[4], int n, const int block[4], int nc, const void *P,
+                            const void *w, void *out);
+
+/* out (coarse sites, nc) = P^H v for a fine field v (V, n). */
+lqcd_status lqcd_mg_restrict(lqcd_ctx *ctx, const int dims[4], int n, const int block[4], int nc, const void *P,
+                             const void *v, void *out);
+
+/* The coarse stencil (Xc, Fc, Bc) of P^H D P on dims / block with nc
+ * components: hops inside a block go to Xc, hops across its forward and
+ * backward face in mu to Fc[mu] and Bc[mu]; sums in a fixed order. */
+lqcd_status lqcd_mg_coarsen(lqcd_ctx *ctx, const int dims[4], int n, const int block[4], int nc, const void *X,
+                            const void *F, const void *B, const void *P, void *Xc, void *Fc, void *Bc);
+
+/* out[j] = <X_j, y> = sum_i conj(X_j[i]) y[i] for the k <= 64 vectors X_j of
+ * len complex numbers stored one after the other; out is a host array of k
+ * complex (2 k doubles).  Fixed-order sums; blocks. */
+lqcd_status lqcd_mg_dots(lqcd_ctx *ctx, long len, int k, const void *X, const void *y, double *out);
+
+/* y += sum_j coef[j] X_j for k <= 64 vectors (coef: host, k complex). */
+lqcd_status lqcd_mg_axpys(lqcd_ctx *ctx, long len, int k, const double *coef, const void *X, void *y);
+
+/* y = a x + b y (a, b: host complex; x may be y). */
+lqcd_status lqcd_mg_axpby(lqcd_ctx *ctx, long len, const double a[2], const void *x, const double b[2], void *y);
+
 /* ---- allocation-free reduction ---------------------------------------- */
 
 /* The paper has no counterpart of this call.  result[k] = sum_i x[k*n + i]^2

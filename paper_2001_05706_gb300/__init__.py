@@ -120,6 +120,16 @@ _sig = {
     "lqcd_overlap_eigvecs": [_vp, _vp, _ip, _ip],
     "lqcd_overlap": [_vp, _vp, _vp, _ip, _ip, _ip, ctypes.POINTER(lqcd_solve_params),
                      ctypes.POINTER(lqcd_solve_info)],
+    "lqcd_mg_fine_stencil": [_vp, _vp, _vp, _vp],
+    "lqcd_mg_apply": [_vp, ctypes.POINTER(ctypes.c_int), _ip, _vp, _vp, _vp, _vp, _vp],
+    "lqcd_mg_orthonormalize": [_vp, ctypes.POINTER(ctypes.c_int), _ip, ctypes.POINTER(ctypes.c_int), _ip, _vp, _vp],
+    "lqcd_mg_prolong": [_vp, ctypes.POINTER(ctypes.c_int), _ip, ctypes.POINTER(ctypes.c_int), _ip, _vp, _vp, _vp],
+    "lqcd_mg_restrict": [_vp, ctypes.POINTER(ctypes.c_int), _ip, ctypes.POINTER(ctypes.c_int), _ip, _vp, _vp, _vp],
+    "lqcd_mg_coarsen": [_vp, ctypes.POINTER(ctypes.c_int), _ip, ctypes.POINTER(ctypes.c_int), _ip, _vp, _vp, _vp,
+                        _vp, _vp, _vp, _vp],
+    "lqcd_mg_dots": [_vp, ctypes.c_long, _ip, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
+    "lqcd_mg_axpys": [_vp, ctypes.c_long, _ip, ctypes.POINTER(ctypes.c_double), _vp, _vp],
+    "lqcd_mg_axpby": [_vp, ctypes.c_long, ctypes.POINTER(ctypes.c_double), _vp, ctypes.POINTER(ctypes.c_double), _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -412,6 +422,100 @@ def solve_params(tol=1e-10, max_iter=20000, inner=LQCD_F64, delta=0.1, nrhs=1, u
 
 
 # ---- convenience ------------------------------------------------------------
+
+# ---- adaptive multigrid building blocks (complex128 CUDA tensors) -------------
+
+def _mg_ptr(t, numel, name):
+    """The device pointer of a contiguous complex128 CUDA tensor holding at
+    least numel values (the C side cannot see sizes)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.complex128:
+        raise ValueError(f"{name} must be complex128, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} values, fewer than {numel}")
+    return _vp(t.data_ptr())
+
+
+def _i4(v):
+    v = [int(x) for x in v]
+    if len(v) != 4:
+        raise ValueError("four entries expected")
+    return (ctypes.c_int * 4)(*v)
+
+
+def _coarse(dims, block):
+    if any(int(b) < 1 or int(d) % int(b) for d, b in zip(dims, block)):
+        raise ValueError(f"blocks {tuple(block)} do not tile {tuple(dims)}")
+    return tuple(int(d) // int(b) for d, b in zip(dims, block))
+
+
+def lqcd_mg_fine_stencil(ctx, V, X, F, B):
+    """X (V,12,12), F and B (4,V,12,12) of M = A - kappa D_W on the context's lattice."""
+    _check(_lib.lqcd_mg_fine_stencil(ctx, _mg_ptr(X, V * 144, "X"), _mg_ptr(F, 4 * V * 144, "F"),
+                                     _mg_ptr(B, 4 * V * 144, "B")))
+
+
+def lqcd_mg_apply(ctx, dims, n, X, F, B, v, out):
+    V = int(np.prod(dims))
+    _check(_lib.lqcd_mg_apply(ctx, _i4(dims), int(n), _mg_ptr(X, V * n * n, "X"), _mg_ptr(F, 4 * V * n * n, "F"),
+                              _mg_ptr(B, 4 * V * n * n, "B"), _mg_ptr(v, V * n, "in"), _mg_ptr(out, V * n, "out")))
+
+
+def lqcd_mg_orthonormalize(ctx, dims, n, block, nv, vecs, P):
+    V = int(np.prod(dims))
+    _check(_lib.lqcd_mg_orthonormalize(ctx, _i4(dims), int(n), _i4(block), int(nv), _mg_ptr(vecs, nv * V * n, "vecs"),
+                                       _mg_ptr(P, V * n * 2 * nv, "P")))
+
+
+def lqcd_mg_prolong(ctx, dims, n, block, nc, P, w, out):
+    V, Vc = int(np.prod(dims)), int(np.prod(_coarse(dims, block)))
+    _check(_lib.lqcd_mg_prolong(ctx, _i4(dims), int(n), _i4(block), int(nc), _mg_ptr(P, V * n * nc, "P"),
+                                _mg_ptr(w, Vc * nc, "w"), _mg_ptr(out, V * n, "out")))
+
+
+def lqcd_mg_restrict(ctx, dims, n, block, nc, P, v, out):
+    V, Vc = int(np.prod(dims)), int(np.prod(_coarse(dims, block)))
+    _check(_lib.lqcd_mg_restrict(ctx, _i4(dims), int(n), _i4(block), int(nc), _mg_ptr(P, V * n * nc, "P"),
+                                 _mg_ptr(v, V * n, "v"), _mg_ptr(out, Vc * nc, "out")))
+
+
+def lqcd_mg_coarsen(ctx, dims, n, block, nc, X, F, B, P, Xc, Fc, Bc):
+    V, Vc = int(np.prod(dims)), int(np.prod(_coarse(dims, block)))
+    _check(_lib.lqcd_mg_coarsen(ctx, _i4(dims), int(n), _i4(block), int(nc), _mg_ptr(X, V * n * n, "X"),
+                                _mg_ptr(F, 4 * V * n * n, "F"), _mg_ptr(B, 4 * V * n * n, "B"),
+                                _mg_ptr(P, V * n * nc, "P"), _mg_ptr(Xc, Vc * nc * nc, "Xc"),
+                                _mg_ptr(Fc, 4 * Vc * nc * nc, "Fc"), _mg_ptr(Bc, 4 * Vc * nc * nc, "Bc")))
+
+
+def lqcd_mg_dots(ctx, k, Xv, y):
+    """[<X_j, y> for j < k] (complex), X_j the first k rows of Xv (each y.numel() long)."""
+    n = y.numel()
+    out = (ctypes.c_double * (2 * int(k)))()
+    _check(_lib.lqcd_mg_dots(ctx, n, int(k), _mg_ptr(Xv, k * n, "X"), _mg_ptr(y, n, "y"), out))
+    a = np.array(out[:])
+    return a[0::2] + 1j * a[1::2]
+
+
+def lqcd_mg_axpys(ctx, coef, Xv, y):
+    """y += sum_j coef[j] X_j."""
+    coef = np.asarray(coef, dtype=np.complex128).reshape(-1)
+    k, n = len(coef), y.numel()
+    c = np.ascontiguousarray(coef.view(np.float64))
+    _check(_lib.lqcd_mg_axpys(ctx, n, k, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _mg_ptr(Xv, k * n, "X"),
+                              _mg_ptr(y, n, "y")))
+
+
+def lqcd_mg_axpby(ctx, a, x, b, y):
+    """y = a x + b y (complex scalars)."""
+    n = y.numel()
+    ca = (ctypes.c_double * 2)(complex(a).real, complex(a).imag)
+    cb = (ctypes.c_double * 2)(complex(b).real, complex(b).imag)
+    _check(_lib.lqcd_mg_axpby(ctx, n, ca, _mg_ptr(x, n, "x"), cb, _mg_ptr(y, n, "y")))
+
 
 class Lattice:
     """One context: geometry, gauge field, clover term (thin wrapper)."""
