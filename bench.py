@@ -857,6 +857,47 @@ def run_multigrid(args):
         xh = x.cpu().numpy().reshape(b.shape)
         out["multigrid"] = {"setup_seconds": t1 - t0, "solve_seconds": t3 - t2, "outer_iters": it,
                             "rel_resid_gpu": rel, "levels": [{"dims": list(op.dims), "n": op.n} for op in mg.ops]}
+        # roofline of the stencil application at each level (CUDA events on the
+        # launching stream): algorithmic bytes per site = 9 n^2 matrix entries
+        # + n read + n written, 16 B each
+        peak, _ = load_peaks()
+        roof = []
+        for op in mg.ops:
+            v = op.new()
+            w = op.new()
+            for _ in range(3):
+                op.apply(v, w)
+            reps = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                op.apply(v, w)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            nbytes = op.V * (9 * op.n * op.n + 2 * op.n) * 16
+            roof.append({"dims": list(op.dims), "n": op.n, "ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
+                         "frac": nbytes / ms / 1e6 / peak, "l2_resident": nbytes < 120e6})
+        out["multigrid"]["apply_roofline"] = roof
+        if args.kernel_shares:
+            # device time per kernel over a second set-up and solve, from
+            # CUPTI activity records (torch.profiler): shares, not bench values
+            from torch.profiler import ProfilerActivity, profile
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                mg2 = gmg.Multigrid(st, blocks, starts, setup_iters=30)
+                mg2.solve(bd, 1e-10, maxiter=300)
+                torch.cuda.synchronize()
+            tot = {}
+            for ev in prof.events():
+                if getattr(ev.device_type, "name", "") == "CUDA":
+                    name = ev.name.replace("(anonymous namespace)::", "").replace("lqcd::", "")
+                    name = name.replace("void ", "").split("(")[0].split("<")[0]
+                    c, t = tot.get(name, (0, 0.0))
+                    tot[name] = (c + 1, t + ev.time_range.elapsed_us())
+            all_us = sum(t for _, t in tot.values()) or 1.0
+            out["kernel_shares"] = sorted(({"kernel": k, "launches": c, "total_ms": t / 1e3, "share": t / all_us}
+                                           for k, (c, t) in tot.items()), key=lambda r: -r["total_ms"])
         for name, inner in (("cgls_fp64", "f64"), ("cgls_mixed_f16", "f16")):
             lat.solve(b, 1e-10, inner)  # warm the autotuner
             xs, stt, info = lat.solve(b, 1e-10, inner)
@@ -1045,6 +1086,8 @@ def main():
     ap.add_argument("--max-filter", type=int, default=400, help="H_W low-mode restart cap for --ov-eigen")
     ap.add_argument("--overlap", action="store_true", help="run the overlap workload (16^3x32) instead")
     ap.add_argument("--multigrid", default=None, help="run only the multigrid solve on lattice L0,L1,L2,L3")
+    ap.add_argument("--kernel-shares", action="store_true",
+                    help="with --multigrid: device time per kernel of a second set-up and solve (CUPTI records)")
     ap.add_argument("--solve-lattice", default=None, help="run only the solve comparison on this lattice")
     ap.add_argument("--high", default="f64", choices=["f64", "df64"],
                     help="--overlap: arithmetic of the FP64 parts (FP64 or double-float)")
