@@ -85,3 +85,26 @@ def test_enum_values_match_header(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [getattr(L, n) for n in names], names
+
+
+def test_multigrid_entry_points_refuse_a_null_context():
+    """Every lqcd_mg_* call checks its context before any CUDA call."""
+    import ctypes
+    import paper_2001_05706_gb300 as L
+    d = (ctypes.c_int * 4)(4, 4, 4, 4)
+    p = ctypes.c_void_p(16)
+    two = (ctypes.c_double * 2)(1.0, 0.0)
+    calls = {
+        "lqcd_mg_fine_stencil": (None, p, p, p),
+        "lqcd_mg_apply": (None, d, 12, p, p, p, p, p),
+        "lqcd_mg_orthonormalize": (None, d, 12, d, 4, p, p),
+        "lqcd_mg_prolong": (None, d, 12, d, 8, p, p, p),
+        "lqcd_mg_restrict": (None, d, 12, d, 8, p, p, p),
+        "lqcd_mg_coarsen": (None, d, 12, d, 8, p, p, p, p, p, p, p),
+        "lqcd_mg_dots": (None, 16, 1, p, p, (ctypes.c_double * 2)()),
+        "lqcd_mg_axpys": (None, 16, 1, two, p, p),
+        "lqcd_mg_axpby": (None, 16, two, p, two, p),
+    }
+    for name, args in calls.items():
+        assert getattr(L._lib, name)(*args) == L.LQCD_ERR_ARG, name
+        assert b"context" in L._lib.lqcd_last_error(), name
