@@ -217,3 +217,21 @@ def test_aggregation_rejects_bad_arguments():
     v = _starts(1, V, 12, 1)
     with pytest.raises(ValueError):
         mg.Prolongator(st, (2, 2, 1, 2), np.concatenate([v, 2 * v]))  # dependent vectors
+
+
+def test_single_site_coarse_lattice_is_the_galerkin_product():
+    """Blocks spanning the whole lattice: one coarse site, every hop across
+    a block face wraps to the same block, and the coarse stencil's X + sum
+    (F + B) must equal the dense P^H M P."""
+    dims = SMALL
+    V = int(np.prod(dims))
+    U = gen.gauge_field(dims, 0.5, 71)
+    st = mg.wilson_clover_stencil(dims, U, KAPPA, CSW, 1)
+    P = mg.Prolongator(st, dims, mg.near_null_vectors(st, _starts(5, V, 12, 72), 15))
+    D = mg.coarsen(st, P)
+    assert D.dims == (1, 1, 1, 1) and D.n == 10
+    Pd = _dense_P(P)
+    G = Pd.conj().T @ _dense_M(dims, U, KAPPA, CSW, 1) @ Pd
+    assert np.abs(D.dense() - G).max() <= 1e-13 * np.abs(G).max()
+    # the t hops across the antiperiodic boundary keep their sign inside the single block
+    assert np.abs(D.F[3]).max() > 0 and np.abs(D.B[3]).max() > 0
