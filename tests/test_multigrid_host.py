@@ -127,7 +127,7 @@ def test_gcr_and_mr_on_block_diagonal_operators(gmg):
 
 
 def test_host_driver_follows_the_oracle_solver(gmg):
-    """Three levels on 8x8x4x8 near the critical kappa: the driver's set-up
+    """Three levels on 8x8x4x8 near the critical kappa: the host code's set-up
     gives the oracle's coarse operators, and its solve the oracle's step count
     and a true residual <= 1e-10 recomputed by the C oracle."""
     dims, kappa = (8, 8, 4, 8), 0.1285
